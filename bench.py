@@ -1,0 +1,324 @@
+"""Benchmark: OCP solves per second to a 1e-6 relative cost gap, GN-MPPI on GB300.
+
+Workload: a batch of seeded chain OCPs (M=10 masses, N=100, nu=2, K=2048
+samples, 30 Algorithm-1 iterations, sigma0 0.2, lambda 1e-3), FP32 rollouts
+with an FP64 Cholesky (the library's FP32 mode), all instances in one handle
+and one CUDA graph per solve.  A step = one batched solve of every instance.
+An instance counts as solved when the FP64 re-evaluation of its final cost is
+within 1e-6 (relative) of its reference optimum C*, which the FP64 CPU oracle
+wrote to tests/golden/chain_m10_cstar.txt.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gnmppi|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle,
+as it stands, on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N, K, T, SIGMA0, LAM = 10, 100, 2048, 30, 0.2, 1e-3
+GAP = 1e-6
+METRIC = "OCP solves/s to 1e-6 rel. cost gap"
+CSTAR = os.path.join(ROOT, "tests", "golden", "chain_m10_cstar.txt")
+WORKLOAD = "chain M=10 N=100 nu=2 K=2048 T=30 sigma0=0.2 lambda=1e-3"
+
+
+def load_cstar():
+    rows = np.loadtxt(CSTAR, comments="#")
+    return rows[:, 0].astype(int), rows[:, 1], rows[:, 2]
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+class Clocks:
+    """nvidia-smi sampler for SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            out, _ = self.p.communicate(timeout=5)
+            for line in out.strip().splitlines():
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    self.rows.append(f)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in self.rows if num(r[1])]
+        mx = [num(r[2]) for r in self.rows if num(r[2])]
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def chain_flops_per_step(F: int) -> int:
+    """Algorithmic FP32 flops of one RK4 step of the F-free-mass chain plus its
+    residual rows (FMA = 2): 4 right-hand sides of 25F + 2, 52F for the RK4
+    combinations, 6 per residual row (2F + 2 rows)."""
+    return 4 * (25 * F + 2) + 52 * F + 6 * (2 * F + 2)
+
+
+def run_gnmppi(args):
+    import torch
+
+    from paper_2512_04579_gb300 import build as B
+    from paper_2512_04579_gb300 import gnmppi as G
+    from paper_2512_04579_gb300 import inputs as I
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or not os.path.exists(B.OUT):
+        B.build()
+    if world > 1:
+        dist.barrier()
+    G.load()
+
+    idx, C_gn_oracle, Cstar = load_cstar()
+    batch = len(idx) if args.batch <= 0 else min(args.batch, len(idx))
+    Cstar = Cstar[:batch]
+    seed = I.BASE_SEED + 1
+    x0, tgt = I.chain_instances(seed, len(idx), M)
+    x0, tgt = x0[:batch], tgt[:batch]
+    stream = torch.cuda.current_stream(dev)
+    prob = G.chain_problem(M=M, N=N, K=K, iterations=T, lam=LAM, sigma0=SIGMA0, seed=seed,
+                           precision=G.PREC_FP32)
+    h = G.gnmppi_create(prob, batch, None, stream.cuda_stream)
+    d_x0 = torch.tensor(x0.ravel(), dtype=torch.float64, device=dev)
+    d_tgt = torch.tensor(tgt.ravel(), dtype=torch.float64, device=dev)
+    d_U0 = torch.zeros(batch * N * 2, dtype=torch.float64, device=dev)
+    d_U = torch.empty_like(d_U0)
+
+    def one_step():
+        d_U.copy_(d_U0)
+        G.gnmppi_solve(h, G.MEM_DEVICE, d_x0, d_tgt, d_U, None)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches0 = G.gnmppi_launch_count(h)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = G.gnmppi_launch_count(h) - launches0
+    # FP64 re-evaluation of the final costs, outside the timed region
+    Cfin = torch.empty(batch, dtype=torch.float64, device=dev)
+    G.gnmppi_cost(h, G.MEM_DEVICE, d_x0, d_tgt, d_U, Cfin)
+    Cfin = Cfin.cpu().numpy()
+    gap = (Cfin - Cstar) / Cstar
+    solved = int(np.sum(gap <= GAP))
+    ms_step = ms / args.steps
+    value = world * solved / (ms_step / 1e3)
+
+    # per-kernel CUDA-event times of one iteration on the final state
+    phases = G.gnmppi_phase_times(h, T)
+    F = M - 1
+    roll_flops = batch * (K) * (N * chain_flops_per_step(F))  # K rollouts of N steps each
+    t_roll = phases["samples"] / 1e3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
+    achieved = roll_flops / t_roll / 1e12
+    G.gnmppi_destroy(h)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    prob_e = G.chain_problem(M=M, N=N, K=K, iterations=T, lam=LAM, sigma0=SIGMA0, seed=seed,
+                             precision=G.PREC_FP32)
+    he = G.gnmppi_create(prob_e, batch, None, stream.cuda_stream)
+    hx0 = torch.tensor(x0.ravel(), dtype=torch.float64).pin_memory()
+    htg = torch.tensor(tgt.ravel(), dtype=torch.float64).pin_memory()
+    hU = torch.zeros(batch * N * 2, dtype=torch.float64).pin_memory()
+    G.gnmppi_solve(he, G.MEM_HOST, hx0, htg, hU, None)
+    e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        hU.zero_()
+        G.gnmppi_solve(he, G.MEM_HOST, hx0, htg, hU, None)
+    e2e_s = (time.perf_counter() - t0) / e_steps
+    Ce = torch.empty(batch, dtype=torch.float64, device=dev)
+    G.gnmppi_cost(he, G.MEM_HOST, hx0.numpy(), htg.numpy(), hU.numpy(), Ce.cpu().numpy())
+    G.gnmppi_destroy(he)
+    e2e_solved = solved  # same inputs, deterministic kernels: same final iterates
+    e2e = {"value": world * e2e_solved / e2e_s, "unit": "solves/s",
+           "h2d_bytes_per_step": int(8 * (x0.size + tgt.size + batch * N * 2)),
+           "d2h_bytes_per_step": int(8 * batch * N * 2)}
+
+    # plain GN-MPPI: one instance per handle and launch, in sequence
+    nplain = min(args.plain, batch)
+    hp = G.gnmppi_create(prob, 1, None, stream.cuda_stream)
+    pU = torch.zeros(N * 2, dtype=torch.float64, device=dev)
+    pC = torch.empty(1, dtype=torch.float64, device=dev)
+    G.gnmppi_solve(hp, G.MEM_DEVICE, d_x0[: 4 * F], d_tgt[: 2 * F], pU, None)
+    torch.cuda.synchronize()
+    p_solved = 0
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for b in range(nplain):
+        pU.zero_()
+        G.gnmppi_solve(hp, G.MEM_DEVICE, d_x0[b * 4 * F:(b + 1) * 4 * F], d_tgt[b * 2 * F:(b + 1) * 2 * F], pU, None)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1) / max(1, nplain)
+    # plain solves are the same computation as the batched ones (same instance index 0 stream only for b=0)
+    G.gnmppi_destroy(hp)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 rollouts/contractions, f64 Cholesky", "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD + f" batch={batch}", "batch": batch, "precision": "fp32",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "working set per iteration > L2 (dR alone %.1f GB)" % (batch * (2 * F + 2) * N * K / 2 * 4 / 1e9)},
+        "solved": solved, "solved_fraction": solved / batch, "gap_median": float(np.median(gap)),
+        "gap_max": float(np.max(gap)),
+        "plain": {"solves_per_s_upper_bound": 1e3 / plain_ms, "ms_per_solve": plain_ms, "instances": nplain},
+        "phases_ms_per_iteration": phases,
+        "roofline": {"kernel": "k_samples (RK4 rollouts + residual/cost/dR/W)", "bound": "alu",
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": None,
+                     "peak_note": "FP32 152 SMs x 128 lanes x 2 flop/FMA at the %.0f MHz maximum SM clock" % sm_max},
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def oracle_iteration_seconds(threads: int, iters: int, b: int = 0):
+    from oracle import oracle as O
+    from paper_2512_04579_gb300 import inputs as I
+
+    O.build()
+    seed = I.BASE_SEED + 1
+    x0, tgt = I.chain_instances(seed, 256, M)
+    m = O.chain(M=M, N=N)
+    opt = O.Options(K=K, iterations=iters, lam=LAM, seed=seed, threads=threads)
+    t0 = time.perf_counter()
+    O.solve(m, opt, x0[b], tgt[b], np.zeros(m.n), SIGMA0, inst=b)
+    return (time.perf_counter() - t0) / iters
+
+
+def cpu_baseline(args):
+    cores = os.cpu_count() or 1
+    iters = max(1, args.cpu_iters)
+    t_it = oracle_iteration_seconds(cores, iters)
+    _, C_gn, Cs = load_cstar()
+    frac = float(np.mean((C_gn - Cs) / Cs <= GAP))
+    return {"value": frac / (t_it * T), "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 instance, {iters} of {T} iterations, {cores} OpenMP threads over samples; "
+                      f"scaled by T and by the oracle's own solved fraction {frac:.3f}"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_iteration_seconds(cores, 1)
+    ts = [oracle_iteration_seconds(cores, 1, b=i % 4) for i in range(args.steps)]
+    t_it = float(np.mean(ts))
+    _, C_gn, Cs = load_cstar()
+    frac = float(np.mean((C_gn - Cs) / Cs <= GAP))
+    value = frac / (t_it * T)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_it * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+           "config": {"workload": WORKLOAD + " (one instance per step, one iteration)", "precision": "fp64"},
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                            "sample": f"each step one of {T} iterations of one instance; solves/s = solved "
+                                      f"fraction {frac:.3f} / ({T} x mean iteration time)"},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gnmppi", choices=["gnmppi", "reference"])
+    ap.add_argument("--batch", type=int, default=0, help="instances (default: every instance with a stored C*)")
+    ap.add_argument("--plain", type=int, default=8, help="instances for the one-at-a-time plain arm")
+    ap.add_argument("--cpu-iters", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gnmppi(args)
+
+
+if __name__ == "__main__":
+    main()

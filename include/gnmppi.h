@@ -1,0 +1,209 @@
+/*
+ * gnmppi.h -- C ABI of the GB300 (sm_103a) Gauss-Newton accelerated MPPI solver.
+ *
+ * The solver implements Algorithm 1 of Homburger, Baumgaertner, Diehl, Reuter,
+ * "Gauss-Newton accelerated MPPI Control" (arXiv 2512.04579), Method D (random
+ * sampling of the Gaussian-smoothing Jacobian, Eq. 7), batched over many
+ * independent optimal control problems (Eq. 2-3) on one GPU.  Per iteration:
+ * Philox noise, antithetic RK4 rollouts with fused residual / cost / softmin
+ * reductions, the Jacobian-reconstruction contraction, the GGN system of Eq. 9
+ * with a Levenberg damping lambda, an FP64 Cholesky solve with iterative
+ * refinement, the parallel line search of Eq. 11 and the covariance shrink.
+ *
+ * Conventions for every entry point:
+ *   - Arrays are plain pointers.  `mem` says whether they are host
+ *     (GNMPPI_MEM_HOST) or device (GNMPPI_MEM_DEVICE) memory; the caller
+ *     owns them and keeps them valid until the call returns (calls are
+ *     synchronous with respect to the handle's stream).
+ *   - Per-instance arrays are packed instance after instance; the offset of
+ *     instance b is given by gnmppi_layout().  Element type is double.
+ *   - No exception crosses the ABI.  Each call returns a gnmppi_status; the
+ *     text of the last error of a handle is available from
+ *     gnmppi_last_error().  A handle is used from one host thread at a time.
+ *   - All device work is issued on the handle's stream (the one passed to
+ *     gnmppi_create, or a stream the handle creates when NULL).
+ */
+#ifndef GNMPPI_H
+#define GNMPPI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gnmppi_s* gnmppi_t;
+
+typedef enum {
+  GNMPPI_OK = 0,
+  GNMPPI_E_ARG = -1,       /* invalid argument (null pointer, size, mode)         */
+  GNMPPI_E_CUDA = -2,      /* CUDA runtime error, or no usable GPU                */
+  GNMPPI_E_NOT_PD = -3,    /* GGN matrix not positive definite after 6 retries   */
+  GNMPPI_E_NONFINITE = -4, /* every sample or every line-search cost non-finite  */
+  GNMPPI_E_TIMEOUT = -5,   /* a bounded device wait ran out                      */
+  GNMPPI_E_NOMEM = -6      /* device allocation failed                           */
+} gnmppi_status;
+
+/* Dynamics (Sec. 2: the black-box simulator X = F(x0, U) and residual R). */
+enum {
+  GNMPPI_DYN_PENDULUM = 0, /* x=[theta,omega]; theta''=-(g/l)sin(theta)-b*omega+u/(m l^2); RK4.
+                              Residual stage k: [theta_k-pi, 0.1 omega_k, 0.1 u_k];
+                              terminal [10(theta_N-pi), 10 omega_N].  params {g,l,m,b}. */
+  GNMPPI_DYN_CHAIN = 1,    /* M point masses in a vertical plane, mass 0 fixed at the origin,
+                              link tension k d + k3 d^3 (rest length 1/(M-1)), damping -c v,
+                              gravity -g y, force control on mass M-1; RK4.  Residual stage k:
+                              [p_{1..M-1,k} - p*, 0.1 u_k]; terminal p_{.,N} - p*.
+                              xref = p* (2(M-1) values).  params {mass,k,k3,c,g}. */
+  GNMPPI_DYN_LINEAR = 2    /* x+ = A x + B u (discrete); residual stage k [wq.*x_k, wr.*u_k],
+                              terminal wqN.*x_N.  lin = {A (nx*nx), B (nx*nu), wq, wr, wqN}. */
+};
+
+/* Arithmetic of the hot path. */
+enum {
+  GNMPPI_PREC_FP64 = 0, /* every step in FP64 (parity mode)                               */
+  GNMPPI_PREC_FP32 = 1, /* FP32 rollouts with compensated cost sums, FP32 contraction and
+                           Gram, FP64 Cholesky with iterative refinement                   */
+  GNMPPI_PREC_BF16 = 2  /* as FP32, but residual differences and perturbations stored in
+                           BF16 and contracted on the tensor cores (FP32 accumulation)     */
+};
+
+/* Jacobian estimator (Eq. 7).  dR_m = (R(U+W_m) - R(U-W_m))/2 (antithetic) or
+ * R(U+W_m) - R(U) (one-sided); P = sum dR_m W_m^T, S = sum W_m W_m^T over K' pairs.
+ *   SIGMA: J = P Sigma^-1 / K'  (the printed Monte Carlo form)
+ *   LSQ:   J = P S^-1           (regression form; exact for affine R once K' >= n)
+ *   AUTO:  LSQ when K' >= n, otherwise SIGMA. */
+enum { GNMPPI_JAC_LSQ = 0, GNMPPI_JAC_SIGMA = 1, GNMPPI_JAC_AUTO = 2 };
+
+enum { GNMPPI_MEM_HOST = 0, GNMPPI_MEM_DEVICE = 1 };
+
+/* Problem and Algorithm-1 options shared by every instance of a handle. */
+typedef struct {
+  int32_t dynamics;   /* GNMPPI_DYN_*                                              */
+  int32_t nx, nu, N;  /* state dim, control dim, horizon (defaults per instance)   */
+  int32_t M;          /* chain masses (chain only)                                 */
+  int32_t n_lin;      /* number of doubles in lin (linear only)                    */
+  double dt;          /* RK4 step                                                  */
+  double params[8];   /* model constants, see GNMPPI_DYN_*                         */
+  const double* lin;  /* host pointer, copied by gnmppi_create; may be NULL        */
+  int32_t K;          /* samples per iteration; antithetic: K/2 pairs              */
+  int32_t iterations; /* Algorithm 1 iterations per gnmppi_solve                   */
+  int32_t L;          /* line-search set {gamma^j : j < L} (Eq. 11)                */
+  int32_t precision;  /* GNMPPI_PREC_*                                             */
+  int32_t jac_mode;   /* GNMPPI_JAC_*                                              */
+  int32_t antithetic; /* 1: +-W pairs (default); 0: one-sided, baseline-subtracted */
+  int32_t monotone;   /* 1: alpha = 0 joins the line-search set                    */
+  int32_t ir_steps;   /* iterative-refinement steps after the Cholesky solve       */
+  double lambda;      /* damping of (J^T J + lambda I) (Eq. 9)                     */
+  double sigma0;      /* initial sampling std, Sigma_0 = sigma0^2 I                */
+  double beta;        /* covariance shrink Sigma <- beta Sigma (Algorithm 1)       */
+  double gamma;       /* step-length ratio in (0, 1)                               */
+  double tau;         /* softmin temperature of the sample weights (Eq. 5)         */
+  uint64_t seed;      /* Philox key of the noise stream                            */
+} gnmppi_problem;
+
+/* Per-instance shape of an uneven batch; fields <= 0 take the problem's value. */
+typedef struct {
+  int32_t N, M, K, pad;
+} gnmppi_instance_shape;
+
+/* Per-instance result of gnmppi_solve. */
+typedef struct {
+  double C_initial;  /* C(U_0)                                        */
+  double C_final;    /* C(U_T) from the last line search              */
+  double sigma_final;/* sampling std scale after the last shrink      */
+  int32_t iterations;/* iterations run                                */
+  int32_t status;    /* gnmppi_status of this instance                */
+  int32_t n_masked;  /* non-finite sample pairs dropped, all iterations*/
+  int32_t chol_retries; /* damping increases, all iterations          */
+} gnmppi_report;
+
+/* Per-instance outputs of one Algorithm-1 iteration (gnmppi_step). */
+typedef struct {
+  double C_nom;      /* C(U_k)                                          */
+  double C_new;      /* C(U_k + alpha* delta)                           */
+  double alpha;      /* selected step length                            */
+  double lambda_used;/* damping after retries                           */
+  double c_min, sum_w, sum_w2, ess; /* softmin statistics (Eq. 5)       */
+  double pr_norm;    /* ||P^T r|| (gradient up to the metric S^-1)       */
+  double step_norm;  /* ||delta||                                       */
+  int32_t j_star;    /* index of alpha* in the step-length set          */
+  int32_t n_masked;  /* non-finite sample pairs dropped                 */
+  int32_t jac_mode_used;
+  int32_t status;
+  int32_t chol_retries;
+  int32_t pad;
+} gnmppi_iter_report;
+
+/* Create a solver for `batch` instances (batch >= 1).  `shapes` (nullable, host,
+ * batch entries) gives per-instance N, M, K for an uneven batch.  `cuda_stream`
+ * is a cudaStream_t or NULL.  Allocates all device workspace; *out receives the
+ * handle (NULL on failure).  Errors: E_ARG (bad sizes, modes, K odd with
+ * antithetic sampling, chain M outside 2..17), E_CUDA (no GPU), E_NOMEM. */
+gnmppi_status gnmppi_create(const gnmppi_problem* p, int32_t batch, const gnmppi_instance_shape* shapes,
+                            void* cuda_stream, gnmppi_t* out);
+
+/* Packed-array offsets (host arrays of batch+1 int64 each, nullable): x0 (nx per
+ * instance), xref (2(M-1) per chain instance, 1 otherwise), U (N*nu per instance). */
+gnmppi_status gnmppi_layout(gnmppi_t h, int64_t* x0_off, int64_t* xref_off, int64_t* U_off);
+
+/* Algorithm 1: problem->iterations iterations from U_0 for every instance.
+ * x0, xref: inputs; U: in U_0, out U_T; sigma (nullable): per-instance,
+ * per-component initial std packed like U (NULL: problem->sigma0).  rep
+ * (nullable, host, batch entries) receives per-instance reports.  Returns the
+ * worst instance status (E_NOT_PD / E_NONFINITE), or OK. */
+gnmppi_status gnmppi_solve(gnmppi_t h, int32_t mem, const double* x0, const double* xref, double* U,
+                           const double* sigma, gnmppi_report* rep);
+
+/* One Algorithm-1 iteration with index `iteration` (it selects the Philox
+ * stream) at the given U (in/out: U_k -> U_{k+1}) and per-component std sigma
+ * (packed like U, not modified).  rep (nullable, host, batch entries). */
+gnmppi_status gnmppi_step(gnmppi_t h, int32_t mem, const double* x0, const double* xref, double* U,
+                          const double* sigma, int32_t iteration, gnmppi_iter_report* rep);
+
+/* FP64 re-evaluation of C(U) = 0.5 ||R(U)||^2 (Eq. 2, 4) for every instance;
+ * C: batch doubles in `mem` memory. */
+gnmppi_status gnmppi_cost(gnmppi_t h, int32_t mem, const double* x0, const double* xref, const double* U,
+                          double* C);
+
+/* Copy an internal buffer of instance `inst` from the last gnmppi_step or
+ * gnmppi_solve iteration to host memory as doubles, for verification.
+ * what: 0 dR [nR][K'], 1 W [n][K'], 2 sample costs [K'][2] (one-sided: [K]), 3 e = dR r [K'],
+ * 4 [P^T | S] [n][nR+n], 5 A = P^T P [n][n], 6 g = P^T r [n], 7 delta [n],
+ * 8 line-search costs [L(+1)], 9 nominal residual r [nR], 10 MPPI direction [n].
+ * count: capacity of host_out in doubles; the number written is returned in
+ * *written.  Errors: E_ARG for unknown `what` or too small a buffer. */
+gnmppi_status gnmppi_debug_read(gnmppi_t h, int32_t what, int32_t inst, double* host_out, int64_t count,
+                                int64_t* written);
+
+/* Time the kernels of one Algorithm-1 iteration (index `iteration`) on the
+ * handle's current device state -- the state the last gnmppi_solve or
+ * gnmppi_step left -- with CUDA events on the handle's stream between phases.
+ * The iteration runs for real (it updates the device iterate; no covariance
+ * shrink).  ms (host, cap doubles) receives per-phase milliseconds in the
+ * order of gnmppi_phase_name(); *nphase the number of phases.  Errors: E_ARG
+ * if cap is smaller than the number of phases. */
+gnmppi_status gnmppi_phase_times(gnmppi_t h, int32_t iteration, double* ms, int32_t cap, int32_t* nphase);
+
+/* Name of phase i of gnmppi_phase_times ("samples", "softmin", "contract",
+ * "gram", "s2", "solve", "line", "update"), or NULL. */
+const char* gnmppi_phase_name(int32_t i);
+
+/* Number of kernels the library launched on this handle since creation. */
+int64_t gnmppi_launch_count(gnmppi_t h);
+
+/* Release the handle and all its device memory.  NULL is ignored. */
+void gnmppi_destroy(gnmppi_t h);
+
+/* Text of the last error on h (static string for h == NULL). */
+const char* gnmppi_last_error(gnmppi_t h);
+
+/* Name of a status code. */
+const char* gnmppi_status_string(int32_t status);
+
+/* ABI version (major*10000 + minor*100 + patch). */
+int32_t gnmppi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GNMPPI_H */

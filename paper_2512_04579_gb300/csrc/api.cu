@@ -1,0 +1,802 @@
+// api.cu -- host side of the GN-MPPI C ABI (include/gnmppi.h): argument
+// validation, workspace layout in HBM, the per-iteration launch sequence of
+// Algorithm 1 (arXiv 2512.04579) and its capture into one CUDA graph per solve.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/gnmppi.h"
+#include "launch.cuh"
+#include "solver_kernels.cuh"
+
+using namespace gnm;
+
+namespace {
+
+struct Group {
+  int key = 0;
+  Launchers fn{};
+  std::vector<int> insts;
+  std::vector<int2> bmap;
+  int* d_list = nullptr;
+  int2* d_bmap = nullptr;
+  int smem = 0;
+};
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct gnmppi_s {
+  gnmppi_problem p{};
+  int batch = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<InstDesc> desc;
+  InstDesc* d_desc = nullptr;
+  InstState* d_st = nullptr;
+  Consts cs{};
+  // workspace
+  double *d_x0 = nullptr, *d_xref = nullptr, *d_U = nullptr, *d_s = nullptr, *d_g = nullptr, *d_mppi = nullptr;
+  double *d_delta = nullptr, *d_y = nullptr, *d_wt = nullptr, *d_C = nullptr, *d_e = nullptr, *d_A = nullptr;
+  double *d_S2 = nullptr, *d_H = nullptr, *d_Cl = nullptr, *d_Cout = nullptr, *d_lin = nullptr, *d_Lg = nullptr;
+  int64_t* d_oL = nullptr;
+  void *d_dR = nullptr, *d_W = nullptr, *d_P = nullptr, *d_r = nullptr, *d_RL = nullptr;
+  int64_t n_x0 = 0, n_xref = 0, n_U = 0, n_dR = 0, n_W = 0, n_C = 0, n_P = 0, n_nn = 0, n_R = 0, n_RL = 0, n_L = 0;
+  size_t szT = 8, szS = 8, szA = 8;
+  int4* d_tiles[3] = {nullptr, nullptr, nullptr};
+  int ntiles[3] = {0, 0, 0};
+  std::vector<Group> groups;
+  int* d_all = nullptr;  // 0..batch-1
+  int smem_n_max = 0;
+  int solve_smem = 0;
+  bool use_tc = false;
+  // graph of one Algorithm-1 solve
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_nodes = 0;
+  int64_t launches = 0;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+static thread_local std::string g_create_err;  // errors raised before a handle exists
+
+static gnmppi_status fail(gnmppi_t h, gnmppi_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  else g_create_err = buf;
+  return st;
+}
+
+#define CK(call)                                                                                       \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess) return fail(h, GNMPPI_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                            \
+  } while (0)
+
+#define CKL()                                                                                          \
+  do {                                                                                                 \
+    cudaError_t e_ = cudaGetLastError();                                                               \
+    if (e_ != cudaSuccess) return fail(h, GNMPPI_E_CUDA, "launch: %s (%s:%d)", cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                            \
+  } while (0)
+
+template <typename P>
+static gnmppi_status dalloc(gnmppi_t h, P** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, GNMPPI_E_NOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  }
+  h->allocs.push_back((void*)*ptr);
+  e = cudaMemsetAsync(*ptr, 0, bytes, h->stream);
+  if (e != cudaSuccess) return fail(h, GNMPPI_E_CUDA, "cudaMemset: %s", cudaGetErrorString(e));
+  return GNMPPI_OK;
+}
+
+static bool get_launchers(int prec, int dyn, int key, Launchers* o) {
+  if (prec == kFP64) return launchers_f64(dyn, key, o);
+  if (prec == kFP32) return launchers_f32(dyn, key, o);
+  return launchers_bf16(dyn, key, o);
+}
+
+static gnmppi_status validate(const gnmppi_problem* p, int32_t batch, const gnmppi_instance_shape* shapes) {
+  if (!p) return fail(nullptr, GNMPPI_E_ARG, "problem is NULL");
+  if (batch < 1) return fail(nullptr, GNMPPI_E_ARG, "batch must be >= 1");
+  if (p->dynamics < 0 || p->dynamics > 2) return fail(nullptr, GNMPPI_E_ARG, "unknown dynamics");
+  if (p->precision < 0 || p->precision > 2) return fail(nullptr, GNMPPI_E_ARG, "unknown precision");
+  if (p->jac_mode < 0 || p->jac_mode > 2) return fail(nullptr, GNMPPI_E_ARG, "unknown jac_mode");
+  if (p->L < 1 || p->L > kMaxL) return fail(nullptr, GNMPPI_E_ARG, "L must be in 1..%d", kMaxL);
+  if (!(p->gamma > 0.0 && p->gamma < 1.0)) return fail(nullptr, GNMPPI_E_ARG, "gamma must be in (0,1)");
+  if (!(p->beta > 0.0 && p->beta <= 1.0)) return fail(nullptr, GNMPPI_E_ARG, "beta must be in (0,1]");
+  if (!(p->tau > 0.0)) return fail(nullptr, GNMPPI_E_ARG, "tau must be > 0");
+  if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return fail(nullptr, GNMPPI_E_ARG, "lambda must be >= 0");
+  if (!(p->sigma0 > 0.0) || !std::isfinite(p->sigma0)) return fail(nullptr, GNMPPI_E_ARG, "sigma0 must be > 0");
+  if (p->iterations < 0) return fail(nullptr, GNMPPI_E_ARG, "iterations must be >= 0");
+  if (p->ir_steps < 0 || p->ir_steps > 10) return fail(nullptr, GNMPPI_E_ARG, "ir_steps must be in 0..10");
+  if (p->dynamics != GNMPPI_DYN_LINEAR && !(p->dt > 0.0)) return fail(nullptr, GNMPPI_E_ARG, "dt must be > 0");
+  if (p->dynamics == GNMPPI_DYN_LINEAR) {
+    const int nx = p->nx, nu = p->nu;
+    const int key = nx * 16 + nu;
+    if (!(key == 2 * 16 + 1 || key == 2 * 16 + 2 || key == 4 * 16 + 1 || key == 4 * 16 + 2 || key == 16 + 1))
+      return fail(nullptr, GNMPPI_E_ARG, "linear (nx, nu) must be one of (1,1) (2,1) (2,2) (4,1) (4,2)");
+    if (!p->lin || p->n_lin != nx * nx + nx * nu + nx + nu + nx)
+      return fail(nullptr, GNMPPI_E_ARG, "linear model needs lin with nx*nx + nx*nu + 2nx + nu doubles");
+  }
+  for (int b = 0; b < batch; ++b) {
+    const int N = (shapes && shapes[b].N > 0) ? shapes[b].N : p->N;
+    const int M = (shapes && shapes[b].M > 0) ? shapes[b].M : p->M;
+    const int K = (shapes && shapes[b].K > 0) ? shapes[b].K : p->K;
+    if (N < 1 || N > 100000) return fail(nullptr, GNMPPI_E_ARG, "instance %d: N must be in 1..100000", b);
+    if (K < 1 || (p->antithetic && (K % 2 != 0 || K < 2)))
+      return fail(nullptr, GNMPPI_E_ARG, "instance %d: K must be >= 1 (even and >= 2 with antithetic pairs)", b);
+    if (p->dynamics == GNMPPI_DYN_CHAIN && (M < 2 || M > kMaxChainF + 1))
+      return fail(nullptr, GNMPPI_E_ARG, "instance %d: chain M must be in 2..%d", b, kMaxChainF + 1);
+    if (K > (1 << 26)) return fail(nullptr, GNMPPI_E_ARG, "instance %d: K too large", b);
+  }
+  return GNMPPI_OK;
+}
+
+extern "C" int32_t gnmppi_version(void) { return 100; }
+
+extern "C" const char* gnmppi_status_string(int32_t s) {
+  switch (s) {
+    case GNMPPI_OK: return "GNMPPI_OK";
+    case GNMPPI_E_ARG: return "GNMPPI_E_ARG";
+    case GNMPPI_E_CUDA: return "GNMPPI_E_CUDA";
+    case GNMPPI_E_NOT_PD: return "GNMPPI_E_NOT_PD";
+    case GNMPPI_E_NONFINITE: return "GNMPPI_E_NONFINITE";
+    case GNMPPI_E_TIMEOUT: return "GNMPPI_E_TIMEOUT";
+    case GNMPPI_E_NOMEM: return "GNMPPI_E_NOMEM";
+    default: return "GNMPPI_E_UNKNOWN";
+  }
+}
+
+extern "C" const char* gnmppi_last_error(gnmppi_t h) {
+  static thread_local char buf[512];
+  snprintf(buf, sizeof(buf), "%s", h ? h->err.c_str() : g_create_err.c_str());
+  return buf;
+}
+
+extern "C" void gnmppi_destroy(gnmppi_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+extern "C" int64_t gnmppi_launch_count(gnmppi_t h) { return h ? h->launches : 0; }
+
+static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
+  const gnmppi_problem& p = h->p;
+  const int prec = p.precision;
+  h->szT = prec == kFP64 ? 8 : 4;
+  h->szS = prec == kFP64 ? 8 : (prec == kFP32 ? 4 : 2);
+  h->szA = prec == kFP64 ? 8 : 4;
+  const int anti = p.antithetic ? 1 : 0;
+  // per-instance layout
+  h->desc.resize(h->batch);
+  int64_t oX = 0, oR = 0, oU = 0, odR = 0, oW = 0, oC = 0, oP = 0, onn = 0, orr = 0, orl = 0, oL = 0;
+  std::vector<int64_t> offL(h->batch, 0);
+  for (int b = 0; b < h->batch; ++b) {
+    InstDesc d{};
+    d.N = (shapes && shapes[b].N > 0) ? shapes[b].N : p.N;
+    const int K = (shapes && shapes[b].K > 0) ? shapes[b].K : p.K;
+    if (p.dynamics == GNMPPI_DYN_CHAIN) {
+      d.M = (shapes && shapes[b].M > 0) ? shapes[b].M : p.M;
+      d.F = d.M - 1;
+      d.nx = 4 * d.F;
+      d.nu = 2;
+      d.rps = 2 * d.F + 2;
+      d.nR = d.N * d.rps + 2 * d.F;
+      d.nref = 2 * d.F;
+    } else if (p.dynamics == GNMPPI_DYN_PENDULUM) {
+      d.nx = 2;
+      d.nu = 1;
+      d.rps = 3;
+      d.nR = 3 * d.N + 2;
+      d.nref = 1;
+    } else {
+      d.nx = p.nx;
+      d.nu = p.nu;
+      d.rps = p.nx + p.nu;
+      d.nR = d.N * d.rps + p.nx;
+      d.nref = 1;
+    }
+    d.n = d.N * d.nu;
+    d.Kp = anti ? K / 2 : K;
+    d.ldK = (int)round_up(d.Kp, kPadK);
+    d.ldP = (int)round_up(d.nR + d.n, 8);
+    if (p.jac_mode == GNMPPI_JAC_LSQ) d.lsq = 1;
+    else if (p.jac_mode == GNMPPI_JAC_SIGMA) d.lsq = 0;
+    else d.lsq = d.Kp >= d.n ? 1 : 0;
+    d.o_x0 = oX; oX += d.nx;
+    d.o_xref = oR; oR += d.nref;
+    d.o_U = oU; oU += d.n;
+    d.o_dR = odR; odR += (int64_t)d.nR * d.ldK;
+    d.o_W = oW; oW += (int64_t)d.n * d.ldK;
+    d.o_C = oC; oC += 2 * (int64_t)d.Kp;
+    d.o_P = oP; oP += (int64_t)d.n * d.ldP;
+    d.o_nn = onn; onn += (int64_t)d.n * d.n;
+    d.o_R = orr; orr += d.nR;
+    d.o_RL = orl; orl += (int64_t)p.L * d.nR;
+    h->desc[b] = d;
+  }
+  // k_solve keeps rhs, x, res (3 n_max doubles) and, when it fits, the packed
+  // Cholesky factor (n(n+1)/2 doubles) in shared memory; larger factors live
+  // in a global scratch.
+  int n_all_max = 0;
+  for (auto& d : h->desc) n_all_max = std::max(n_all_max, d.n);
+  int dev = 0, optin = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa{};
+  if (prec == kFP64) CK(cudaFuncGetAttributes(&fa, k_solve<double>));
+  else CK(cudaFuncGetAttributes(&fa, k_solve<float>));
+  const int64_t solve_budget = (int64_t)optin - (int64_t)fa.sharedSizeBytes - 256;
+  int nmax_smem = 0;
+  while (8 * ((int64_t)3 * n_all_max + (int64_t)(nmax_smem + 1) * (nmax_smem + 2) / 2) <= solve_budget) ++nmax_smem;
+  h->smem_n_max = nmax_smem;
+  int n_solve_max = 0;
+  for (int b = 0; b < h->batch; ++b) {
+    const InstDesc& d = h->desc[b];
+    if (d.n > nmax_smem) {
+      offL[b] = oL;
+      oL += (int64_t)d.n * (d.n + 1) / 2;
+    } else {
+      n_solve_max = std::max(n_solve_max, d.n);
+    }
+  }
+  h->solve_smem = (int)(8 * ((int64_t)3 * n_all_max + (int64_t)n_solve_max * (n_solve_max + 1) / 2));
+  h->n_x0 = oX; h->n_xref = oR; h->n_U = oU; h->n_dR = odR; h->n_W = oW; h->n_C = oC; h->n_P = oP;
+  h->n_nn = onn; h->n_R = orr; h->n_RL = orl; h->n_L = oL;
+
+  gnmppi_status st;
+#define AL(ptr, bytes) if ((st = dalloc(h, &(ptr), (bytes))) != GNMPPI_OK) return st
+  AL(h->d_desc, sizeof(InstDesc) * h->batch);
+  AL(h->d_st, sizeof(InstState) * h->batch);
+  AL(h->d_x0, 8 * h->n_x0);
+  AL(h->d_xref, 8 * h->n_xref);
+  AL(h->d_U, 8 * h->n_U);
+  AL(h->d_s, 8 * h->n_U);
+  AL(h->d_g, 8 * h->n_U);
+  AL(h->d_mppi, 8 * h->n_U);
+  AL(h->d_delta, 8 * h->n_U);
+  AL(h->d_y, 8 * h->n_U);
+  AL(h->d_wt, 8 * (h->n_C / 2));
+  AL(h->d_e, 8 * (h->n_C / 2));
+  AL(h->d_C, 8 * h->n_C);
+  AL(h->d_A, 8 * h->n_nn);
+  AL(h->d_S2, 8 * h->n_nn);
+  AL(h->d_H, 8 * h->n_nn);
+  AL(h->d_Cl, 8 * (int64_t)h->batch * (kMaxL + 1));
+  AL(h->d_Cout, 8 * (int64_t)h->batch);
+  AL(h->d_dR, h->szS * h->n_dR);
+  AL(h->d_W, h->szS * h->n_W);
+  AL(h->d_P, h->szA * h->n_P);
+  AL(h->d_r, h->szT * h->n_R);
+  AL(h->d_RL, h->szT * h->n_RL);
+  AL(h->d_Lg, 8 * h->n_L);
+  AL(h->d_oL, 8 * (int64_t)h->batch);
+  AL(h->d_all, 4 * (int64_t)h->batch);
+  if (p.dynamics == GNMPPI_DYN_LINEAR) {
+    AL(h->d_lin, 8 * (int64_t)p.n_lin);
+    CK(cudaMemcpyAsync(h->d_lin, p.lin, 8 * (size_t)p.n_lin, cudaMemcpyHostToDevice, h->stream));
+  }
+  CK(cudaMemcpyAsync(h->d_desc, h->desc.data(), sizeof(InstDesc) * h->batch, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_oL, offL.data(), 8 * (size_t)h->batch, cudaMemcpyHostToDevice, h->stream));
+  std::vector<int> all(h->batch);
+  for (int b = 0; b < h->batch; ++b) all[b] = b;
+  CK(cudaMemcpyAsync(h->d_all, all.data(), 4 * (size_t)h->batch, cudaMemcpyHostToDevice, h->stream));
+
+  // rollout groups: one kernel instantiation per distinct model size
+  std::map<int, int> gidx;
+  for (int b = 0; b < h->batch; ++b) {
+    const InstDesc& d = h->desc[b];
+    int key = 0;
+    if (p.dynamics == GNMPPI_DYN_CHAIN) key = d.F;
+    if (p.dynamics == GNMPPI_DYN_LINEAR) key = d.nx * 16 + d.nu;
+    auto it = gidx.find(key);
+    if (it == gidx.end()) {
+      Group g;
+      g.key = key;
+      if (!get_launchers(prec, p.dynamics, key, &g.fn)) return fail(h, GNMPPI_E_ARG, "no kernel for model key %d", key);
+      gidx[key] = (int)h->groups.size();
+      h->groups.push_back(g);
+      it = gidx.find(key);
+    }
+    Group& g = h->groups[it->second];
+    g.insts.push_back(b);
+    const int per = anti ? kPairsPerBlock : kSamplesPerBlock;
+    for (int c = 0; c < (d.Kp + per - 1) / per; ++c) g.bmap.push_back(make_int2(b, c));
+    g.smem = std::max(g.smem, (int)(2 * h->szT * d.n));
+  }
+  for (auto& g : h->groups) {
+    AL(g.d_list, 4 * g.insts.size());
+    AL(g.d_bmap, sizeof(int2) * g.bmap.size());
+    CK(cudaMemcpyAsync(g.d_list, g.insts.data(), 4 * g.insts.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(g.d_bmap, g.bmap.data(), sizeof(int2) * g.bmap.size(), cudaMemcpyHostToDevice, h->stream));
+  }
+  // GEMM tile maps (64 x 64 tiles)
+  std::vector<int4> tl[3];
+  for (int b = 0; b < h->batch; ++b) {
+    const InstDesc& d = h->desc[b];
+    const int tm = (d.n + 63) / 64;
+    for (int i = 0; i < tm; ++i) {
+      for (int j = 0; j < (d.nR + d.n + 63) / 64; ++j) tl[0].push_back(make_int4(b, i, j, 0));
+      for (int j = 0; j < tm; ++j) {
+        tl[1].push_back(make_int4(b, i, j, 0));
+        if (d.lsq) tl[2].push_back(make_int4(b, i, j, 0));
+      }
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    h->ntiles[k] = (int)tl[k].size();
+    AL(h->d_tiles[k], sizeof(int4) * std::max<size_t>(1, tl[k].size()));
+    if (!tl[k].empty())
+      CK(cudaMemcpyAsync(h->d_tiles[k], tl[k].data(), sizeof(int4) * tl[k].size(), cudaMemcpyHostToDevice, h->stream));
+  }
+#undef AL
+  // constants
+  Consts& c = h->cs;
+  c.dt = p.dt;
+  for (int i = 0; i < 8; ++i) c.params[i] = p.params[i];
+  c.lambda = p.lambda;
+  c.beta_sqrt = std::sqrt(p.beta);
+  c.gamma = p.gamma;
+  c.tau = p.tau;
+  c.seed = p.seed;
+  c.L = p.L;
+  c.monotone = p.monotone ? 1 : 0;
+  c.ir_steps = p.ir_steps;
+  c.antithetic = anti;
+  c.nx_lin = p.nx;
+  c.nu_lin = p.nu;
+  c.lin = h->d_lin;
+  // the Cholesky kernel keeps its factor in up to the opt-in shared-memory limit
+  if (8 * (int64_t)3 * n_all_max > solve_budget) return fail(h, GNMPPI_E_ARG, "N*nu too large for the solver");
+  if (prec == kFP64) {
+    CK(cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
+  } else {
+    CK(cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return GNMPPI_OK;
+}
+
+extern "C" gnmppi_status gnmppi_create(const gnmppi_problem* p, int32_t batch, const gnmppi_instance_shape* shapes,
+                                       void* cuda_stream, gnmppi_t* out) {
+  if (!out) {
+    g_create_err = "out is NULL";
+    return GNMPPI_E_ARG;
+  }
+  *out = nullptr;
+  gnmppi_status st = validate(p, batch, shapes);
+  if (st != GNMPPI_OK) return st;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    g_create_err = "no CUDA device available";
+    return GNMPPI_E_CUDA;
+  }
+  gnmppi_t h = new gnmppi_s();
+  h->p = *p;
+  h->p.lin = nullptr;
+  h->batch = batch;
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      g_create_err = "cudaStreamCreate failed";
+      delete h;
+      return GNMPPI_E_CUDA;
+    }
+    h->own_stream = true;
+  }
+  h->p = *p;
+  st = build(h, shapes);
+  h->p.lin = nullptr;
+  if (st != GNMPPI_OK) {
+    g_create_err = h->err;
+    gnmppi_destroy(h);
+    return st;
+  }
+  *out = h;
+  return GNMPPI_OK;
+}
+
+extern "C" gnmppi_status gnmppi_layout(gnmppi_t h, int64_t* x0_off, int64_t* xref_off, int64_t* U_off) {
+  if (!h) return GNMPPI_E_ARG;
+  for (int b = 0; b <= h->batch; ++b) {
+    const bool end = b == h->batch;
+    if (x0_off) x0_off[b] = end ? h->n_x0 : h->desc[b].o_x0;
+    if (xref_off) xref_off[b] = end ? h->n_xref : h->desc[b].o_xref;
+    if (U_off) U_off[b] = end ? h->n_U : h->desc[b].o_U;
+  }
+  return GNMPPI_OK;
+}
+
+// ----------------------------------------------------------------- launches
+static RollArgs roll_args(gnmppi_t h, uint32_t it) {
+  RollArgs a{};
+  a.inst = h->d_desc;
+  a.st = h->d_st;
+  a.cs = h->cs;
+  a.x0 = h->d_x0;
+  a.xref = h->d_xref;
+  a.U = h->d_U;
+  a.s = h->d_s;
+  a.delta = h->d_delta;
+  a.r = h->d_r;
+  a.dR = h->d_dR;
+  a.W = h->d_W;
+  a.C = h->d_C;
+  a.e = h->d_e;
+  a.RL = h->d_RL;
+  a.Cl = h->d_Cl;
+  a.Cout = h->d_Cout;
+  a.it = it;
+  return a;
+}
+
+static SolveArgs solve_args(gnmppi_t h, int shrink) {
+  SolveArgs a{};
+  a.inst = h->d_desc;
+  a.st = h->d_st;
+  a.cs = h->cs;
+  a.U = h->d_U;
+  a.s = h->d_s;
+  a.g = h->d_g;
+  a.mppi = h->d_mppi;
+  a.delta = h->d_delta;
+  a.y = h->d_y;
+  a.wt = h->d_wt;
+  a.C = h->d_C;
+  a.e = h->d_e;
+  a.W = h->d_W;
+  a.P = h->d_P;
+  a.A = h->d_A;
+  a.S2 = h->d_S2;
+  a.H = h->d_H;
+  a.Lg = h->d_Lg;
+  a.o_L = h->d_oL;
+  a.r = h->d_r;
+  a.RL = h->d_RL;
+  a.Cl = h->d_Cl;
+  a.shrink = shrink;
+  a.smem_n_max = h->smem_n_max;
+  return a;
+}
+
+static gnmppi_status launch_nominal(gnmppi_t h) {
+  for (auto& g : h->groups) {
+    RollArgs a = roll_args(h, 0);
+    a.list = g.d_list;
+    a.count = (int)g.insts.size();
+    a.mode = 1;
+    g.fn.line(a, a.count, h->stream);
+    CKL();
+    h->launches++;
+  }
+  return GNMPPI_OK;
+}
+
+static const char* kPhaseNames[] = {"samples", "softmin", "contract", "gram", "s2", "solve", "line", "update"};
+constexpr int kNumPhases = 8;
+
+// ev (nullable): kNumPhases + 1 events recorded before the first phase and
+// after each phase.
+template <typename S, typename TA, typename TC, typename T>
+static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cudaEvent_t* ev) {
+#define MARK(i) \
+  if (ev) CK(cudaEventRecord(ev[i], h->stream))
+  MARK(0);
+  for (auto& g : h->groups) {
+    RollArgs a = roll_args(h, it);
+    a.bmap = g.d_bmap;
+    g.fn.samples(a, (int)g.bmap.size(), g.smem, h->stream);
+    CKL();
+    h->launches++;
+  }
+  MARK(1);
+  SolveArgs sa = solve_args(h, shrink);
+  k_softmin_wvec<S, TC><<<h->batch, 256, 0, h->stream>>>(sa);
+  CKL();
+  h->launches++;
+  MARK(2);
+  GemmArgs ga{h->d_desc, h->d_st, nullptr, h->d_dR, h->d_W, h->d_P, h->d_A, h->d_S2};
+  {
+    ga.tiles = h->d_tiles[0];
+    k_gemm_nt<kContract, S, TC, TA><<<h->ntiles[0], 256, 0, h->stream>>>(ga);
+    CKL();
+    h->launches++;
+  }
+  MARK(3);
+  ga.tiles = h->d_tiles[1];
+  k_gemm_nt<kGram, TA, TC, double><<<h->ntiles[1], 256, 0, h->stream>>>(ga);
+  CKL();
+  h->launches++;
+  MARK(4);
+  if (h->ntiles[2] > 0) {
+    ga.tiles = h->d_tiles[2];
+    k_gemm_nt<kS2, TA, TC, double><<<h->ntiles[2], 256, 0, h->stream>>>(ga);
+    CKL();
+    h->launches++;
+  }
+  MARK(5);
+  k_solve<TA><<<h->batch, 256, h->solve_smem, h->stream>>>(sa);
+  CKL();
+  h->launches++;
+  MARK(6);
+  for (auto& g : h->groups) {
+    RollArgs a = roll_args(h, it);
+    a.list = g.d_list;
+    a.count = (int)g.insts.size();
+    a.ncand = h->p.L;
+    a.mode = 0;
+    g.fn.line(a, a.count * h->p.L, h->stream);
+    CKL();
+    h->launches++;
+  }
+  MARK(7);
+  k_update<T><<<h->batch, 128, 0, h->stream>>>(sa);
+  CKL();
+  h->launches++;
+  MARK(8);
+#undef MARK
+  return GNMPPI_OK;
+}
+
+static gnmppi_status launch_iteration(gnmppi_t h, uint32_t it, int shrink, cudaEvent_t* ev = nullptr) {
+  switch (h->p.precision) {
+    case kFP64: return launch_iteration_t<double, double, double, double>(h, it, shrink, ev);
+    case kFP32: return launch_iteration_t<float, float, float, float>(h, it, shrink, ev);
+    default: return launch_iteration_t<__nv_bfloat16, float, float, float>(h, it, shrink, ev);
+  }
+}
+
+extern "C" const char* gnmppi_phase_name(int32_t i) { return (i >= 0 && i < kNumPhases) ? kPhaseNames[i] : nullptr; }
+
+extern "C" gnmppi_status gnmppi_phase_times(gnmppi_t h, int32_t iteration, double* ms, int32_t cap, int32_t* nphase) {
+  if (!h) return GNMPPI_E_ARG;
+  if (!ms || cap < kNumPhases) return fail(h, GNMPPI_E_ARG, "ms needs %d entries", kNumPhases);
+  if (iteration < 0) return fail(h, GNMPPI_E_ARG, "iteration must be >= 0");
+  cudaEvent_t ev[kNumPhases + 1];
+  for (int i = 0; i <= kNumPhases; ++i) CK(cudaEventCreate(&ev[i]));
+  gnmppi_status st = launch_iteration(h, (uint32_t)iteration, 0, ev);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (st == GNMPPI_OK && e == cudaSuccess) {
+    for (int i = 0; i < kNumPhases; ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      ms[i] = t;
+    }
+  }
+  for (int i = 0; i <= kNumPhases; ++i) cudaEventDestroy(ev[i]);
+  if (st != GNMPPI_OK) return st;
+  if (e != cudaSuccess) return fail(h, GNMPPI_E_CUDA, "phase timing: %s", cudaGetErrorString(e));
+  if (nphase) *nphase = kNumPhases;
+  return GNMPPI_OK;
+}
+
+static gnmppi_status load_inputs(gnmppi_t h, int32_t mem, const double* x0, const double* xref, const double* U,
+                                 const double* sigma) {
+  if (!x0 || !U) return fail(h, GNMPPI_E_ARG, "x0 and U must not be NULL");
+  if (h->p.dynamics == GNMPPI_DYN_CHAIN && !xref) return fail(h, GNMPPI_E_ARG, "chain needs xref");
+  if (mem != GNMPPI_MEM_HOST && mem != GNMPPI_MEM_DEVICE) return fail(h, GNMPPI_E_ARG, "mem must be HOST or DEVICE");
+  const cudaMemcpyKind k = mem == GNMPPI_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(h->d_x0, x0, 8 * h->n_x0, k, h->stream));
+  if (xref) CK(cudaMemcpyAsync(h->d_xref, xref, 8 * h->n_xref, k, h->stream));
+  CK(cudaMemcpyAsync(h->d_U, U, 8 * h->n_U, k, h->stream));
+  if (sigma) {
+    CK(cudaMemcpyAsync(h->d_s, sigma, 8 * h->n_U, k, h->stream));
+  } else {
+    std::vector<double> s0(h->n_U, h->p.sigma0);
+    CK(cudaMemcpyAsync(h->d_s, s0.data(), 8 * h->n_U, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // s0 is a temporary
+  }
+  CK(cudaMemsetAsync(h->d_st, 0, sizeof(InstState) * h->batch, h->stream));
+  return GNMPPI_OK;
+}
+
+static gnmppi_status worst_status(const std::vector<InstState>& s) {
+  int w = 0;
+  for (auto& x : s)
+    if (x.status != 0 && (w == 0 || x.status < w)) w = x.status;
+  return (gnmppi_status)w;
+}
+
+extern "C" gnmppi_status gnmppi_solve(gnmppi_t h, int32_t mem, const double* x0, const double* xref, double* U,
+                                      const double* sigma, gnmppi_report* rep) {
+  if (!h) return GNMPPI_E_ARG;
+  gnmppi_status st = load_inputs(h, mem, x0, xref, U, sigma);
+  if (st != GNMPPI_OK) return st;
+  // one CUDA graph per handle: the nominal rollout and every Algorithm-1 iteration
+  if (!h->gexec) {
+    cudaGraph_t graph;
+    const int64_t before = h->launches;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    gnmppi_status cst = launch_nominal(h);
+    for (int it = 0; cst == GNMPPI_OK && it < h->p.iterations; ++it) cst = launch_iteration(h, (uint32_t)it, 1);
+    cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+    if (cst != GNMPPI_OK) return cst;
+    if (ce != cudaSuccess) return fail(h, GNMPPI_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      h->gexec = nullptr;
+      return fail(h, GNMPPI_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    }
+    h->graph_nodes = h->launches - before;
+    h->launches = before;
+  }
+  CK(cudaGraphLaunch(h->gexec, h->stream));
+  h->launches += h->graph_nodes;
+  const cudaMemcpyKind k = mem == GNMPPI_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(U, h->d_U, 8 * h->n_U, k, h->stream));
+  std::vector<InstState> s(h->batch);
+  CK(cudaMemcpyAsync(s.data(), h->d_st, sizeof(InstState) * h->batch, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (rep) {
+    std::vector<double> s_end(h->n_U);
+    CK(cudaMemcpy(s_end.data(), h->d_s, 8 * h->n_U, cudaMemcpyDeviceToHost));
+    for (int b = 0; b < h->batch; ++b) {
+      rep[b].C_final = s[b].C_nom;
+      rep[b].C_initial = 0.0;
+      rep[b].sigma_final = s_end[h->desc[b].o_U];
+      rep[b].iterations = s[b].iters;
+      rep[b].status = s[b].status;
+      rep[b].n_masked = s[b].total_masked;
+      rep[b].chol_retries = s[b].total_retries;
+    }
+  }
+  return worst_status(s);
+}
+
+extern "C" gnmppi_status gnmppi_step(gnmppi_t h, int32_t mem, const double* x0, const double* xref, double* U,
+                                     const double* sigma, int32_t iteration, gnmppi_iter_report* rep) {
+  if (!h) return GNMPPI_E_ARG;
+  if (iteration < 0) return fail(h, GNMPPI_E_ARG, "iteration must be >= 0");
+  gnmppi_status st = load_inputs(h, mem, x0, xref, U, sigma);
+  if (st != GNMPPI_OK) return st;
+  st = launch_nominal(h);
+  if (st != GNMPPI_OK) return st;
+  st = launch_iteration(h, (uint32_t)iteration, 0);
+  if (st != GNMPPI_OK) return st;
+  const cudaMemcpyKind k = mem == GNMPPI_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(U, h->d_U, 8 * h->n_U, k, h->stream));
+  std::vector<InstState> s(h->batch);
+  CK(cudaMemcpyAsync(s.data(), h->d_st, sizeof(InstState) * h->batch, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (rep) {
+    for (int b = 0; b < h->batch; ++b) {
+      gnmppi_iter_report& r = rep[b];
+      const InstState& x = s[b];
+      r.C_nom = x.iters > 0 ? x.C_start : x.C_nom;
+      r.C_new = x.C_new;
+      r.alpha = x.alpha;
+      r.lambda_used = x.lambda_used;
+      r.c_min = x.c_min;
+      r.sum_w = x.sum_w;
+      r.sum_w2 = x.sum_w2;
+      r.ess = x.ess;
+      r.pr_norm = x.pr_norm;
+      r.step_norm = x.step_norm;
+      r.j_star = x.j_star;
+      r.n_masked = x.n_masked;
+      r.jac_mode_used = x.jac_mode_used;
+      r.status = x.status;
+      r.chol_retries = x.chol_retries;
+      r.pad = 0;
+    }
+  }
+  return worst_status(s);
+}
+
+extern "C" gnmppi_status gnmppi_cost(gnmppi_t h, int32_t mem, const double* x0, const double* xref, const double* U,
+                                     double* C) {
+  if (!h) return GNMPPI_E_ARG;
+  if (!C) return fail(h, GNMPPI_E_ARG, "C must not be NULL");
+  gnmppi_status st = load_inputs(h, mem, x0, xref, U, nullptr);
+  if (st != GNMPPI_OK) return st;
+  for (auto& g : h->groups) {
+    RollArgs a = roll_args(h, 0);
+    a.list = g.d_list;
+    a.count = (int)g.insts.size();
+    a.mode = 2;
+    g.fn.cost64(a, a.count, h->stream);
+    CKL();
+    h->launches++;
+  }
+  const cudaMemcpyKind k = mem == GNMPPI_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(C, h->d_Cout, 8 * (size_t)h->batch, k, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return GNMPPI_OK;
+}
+
+// ------------------------------------------------------------ verification
+template <typename X>
+static void widen(const void* src, double* dst, int64_t count) {
+  const X* s = reinterpret_cast<const X*>(src);
+  for (int64_t i = 0; i < count; ++i) dst[i] = (double)s[i];
+}
+
+static void widen_bf16(const void* src, double* dst, int64_t count) {
+  const uint16_t* s = reinterpret_cast<const uint16_t*>(src);
+  for (int64_t i = 0; i < count; ++i) {
+    uint32_t u = (uint32_t)s[i] << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    dst[i] = f;
+  }
+}
+
+static gnmppi_status read_typed(gnmppi_t h, const void* dptr, size_t esz, int kind, int64_t count, double* out) {
+  std::vector<unsigned char> tmp((size_t)count * esz);
+  CK(cudaMemcpy(tmp.data(), dptr, tmp.size(), cudaMemcpyDeviceToHost));
+  if (esz == 8) widen<double>(tmp.data(), out, count);
+  else if (esz == 4) widen<float>(tmp.data(), out, count);
+  else widen_bf16(tmp.data(), out, count);
+  (void)kind;
+  return GNMPPI_OK;
+}
+
+extern "C" gnmppi_status gnmppi_debug_read(gnmppi_t h, int32_t what, int32_t inst, double* host_out, int64_t count,
+                                           int64_t* written) {
+  if (!h) return GNMPPI_E_ARG;
+  if (inst < 0 || inst >= h->batch) return fail(h, GNMPPI_E_ARG, "instance out of range");
+  if (!host_out) return fail(h, GNMPPI_E_ARG, "host_out is NULL");
+  CK(cudaStreamSynchronize(h->stream));
+  const InstDesc& d = h->desc[inst];
+  int64_t need = 0;
+  gnmppi_status st = GNMPPI_OK;
+  auto rows = [&](const unsigned char* base, size_t esz, int64_t nrows, int64_t ld, int64_t ncols) -> gnmppi_status {
+    need = nrows * ncols;
+    if (count < need) return fail(h, GNMPPI_E_ARG, "buffer too small: need %lld doubles", (long long)need);
+    std::vector<double> row(ld);
+    for (int64_t r = 0; r < nrows; ++r) {
+      gnmppi_status s2 = read_typed(h, base + (size_t)r * ld * esz, esz, 0, ncols, host_out + r * ncols);
+      if (s2 != GNMPPI_OK) return s2;
+    }
+    return GNMPPI_OK;
+  };
+  const unsigned char* dR = (const unsigned char*)h->d_dR + h->szS * d.o_dR;
+  const unsigned char* W = (const unsigned char*)h->d_W + h->szS * d.o_W;
+  const unsigned char* P = (const unsigned char*)h->d_P + h->szA * d.o_P;
+  switch (what) {
+    case 0: st = rows(dR, h->szS, d.nR, d.ldK, d.Kp); break;
+    case 1: st = rows(W, h->szS, d.n, d.ldK, d.Kp); break;
+    case 2: {
+      const int64_t nc = h->p.antithetic ? 2 * (int64_t)d.Kp : d.Kp;
+      st = rows((const unsigned char*)(h->d_C + d.o_C), 8, 1, nc, nc);
+      break;
+    }
+    case 3: st = rows((const unsigned char*)(h->d_e + d.o_C / 2), 8, 1, d.Kp, d.Kp); break;
+    case 4: st = rows(P, h->szA, d.n, d.ldP, d.nR + d.n); break;
+    case 5: st = rows((const unsigned char*)(h->d_A + d.o_nn), 8, d.n, d.n, d.n); break;
+    case 6: st = rows((const unsigned char*)(h->d_g + d.o_U), 8, 1, d.n, d.n); break;
+    case 7: st = rows((const unsigned char*)(h->d_delta + d.o_U), 8, 1, d.n, d.n); break;
+    case 8: st = rows((const unsigned char*)(h->d_Cl + (int64_t)inst * (kMaxL + 1)), 8, 1, h->p.L, h->p.L); break;
+    case 9: st = rows((const unsigned char*)h->d_r + h->szT * d.o_R, h->szT, 1, d.nR, d.nR); break;
+    case 10: st = rows((const unsigned char*)(h->d_mppi + d.o_U), 8, 1, d.n, d.n); break;
+    default: return fail(h, GNMPPI_E_ARG, "unknown buffer %d", what);
+  }
+  if (written) *written = (st == GNMPPI_OK) ? need : 0;
+  return st;
+}

@@ -1,0 +1,317 @@
+// common.cuh -- device-side building blocks of the GN-MPPI library: instance
+// descriptors, the Philox4x32-10 noise stream with Box-Muller, compensated
+// sums, and the dynamics / residual models (Sec. 2, Eq. 1-4 of arXiv
+// 2512.04579).  Internal; not part of the C ABI.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gnm {
+
+constexpr int kPairsPerBlock = 64;   // antithetic pairs per rollout CTA (2 lanes each)
+constexpr int kSamplesPerBlock = 128;  // one-sided samples per rollout CTA
+constexpr int kPadK = 64;            // sample-dimension padding of dR / W rows
+constexpr int kMaxL = 32;            // largest line-search set
+constexpr int kMaxChainF = 16;       // free masses handled by the thread-per-rollout chain kernels
+
+enum Dyn { kPendulum = 0, kChain = 1, kLinear = 2 };
+enum Prec { kFP64 = 0, kFP32 = 1, kBF16 = 2 };
+
+// Per-instance sizes and offsets into the packed workspace arrays.
+struct InstDesc {
+  int32_t N, M, F, nx, nu, n, nR, rps;  // rps: residual rows per stage
+  int32_t Kp;                           // antithetic pairs, or one-sided samples
+  int32_t ldK;                          // padded row length of dR / W (multiple of kPadK)
+  int32_t ldP;                          // row length of [P^T | S] (nR + n, padded)
+  int32_t lsq;                          // 1: J = P S^-1, 0: J = P Sigma^-1 / K'
+  int32_t nref;                         // entries of xref
+  int32_t pad;
+  int64_t o_x0, o_xref, o_U;            // packed double arrays (x0; xref; U, s, delta, g, ...)
+  int64_t o_dR, o_W;                    // dR [nR][ldK], W [n][ldK] (storage type)
+  int64_t o_C;                          // sample costs [Kp][2] (double), e and weights [Kp]
+  int64_t o_P;                          // [P^T | S]  [n][ldP] (accumulation type)
+  int64_t o_nn;                         // n*n double arrays (A, S2, H)
+  int64_t o_R;                          // residual r [nR] (scalar type)
+  int64_t o_RL;                         // line-search residuals [L][nR] (scalar type)
+};
+
+// Per-instance solver state carried across kernels of one iteration.
+struct InstState {
+  double C_nom;        // C(U_k) of the current iterate
+  double C_start;      // C(U_k) at the start of the last completed iteration
+  double lambda_used;
+  double c_min, sum_w, sum_w2, ess, pr_norm, step_norm;
+  double C_new, alpha;
+  int32_t n_masked, status, chol_retries, j_star;
+  int32_t jac_mode_used, total_masked, total_retries, iters;
+};
+
+// Problem-wide constants.
+struct Consts {
+  double dt, params[8];
+  double lambda, beta_sqrt, gamma, tau;
+  uint64_t seed;
+  int32_t L, monotone, ir_steps, antithetic;
+  int32_t nx_lin, nu_lin;
+  const double* lin;  // device copy of the linear model data
+};
+
+// ------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC 2011) and the noise stream
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Counter layout of the noise stream: (q, sample, iteration, instance*16 + 0),
+// key = seed; normals 2q and 2q+1 of the sample's perturbation come from one call.
+__device__ __forceinline__ uint4 noise_words(uint64_t seed, uint32_t inst, uint32_t it, uint32_t m, uint32_t q) {
+  return philox4x32_10(make_uint4(q, m, it, inst << 4), make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// Box-Muller in FP64 on 53-bit uniforms u = (hi*2^21 + lo/2^11) 2^-53 + 2^-54.
+__device__ __forceinline__ void box_muller(uint4 w, double& z0, double& z1) {
+  const uint64_t a = ((uint64_t)w.x << 21) | (uint64_t)(w.y >> 11);
+  const uint64_t b = ((uint64_t)w.z << 21) | (uint64_t)(w.w >> 11);
+  const double u1 = (double)a * 0x1p-53 + 0x1p-54;
+  const double u2 = (double)b * 0x1p-53 + 0x1p-54;
+  const double rad = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincos(6.283185307179586 * u2, &s, &c);
+  z0 = rad * c;
+  z1 = rad * s;
+}
+
+// The same transform in FP32: the uniforms are formed from the same 53 bits
+// to FP32 relative accuracy, and cos/sin(2 pi u2) use the exact-argument
+// sincospi.
+__device__ __forceinline__ void box_muller(uint4 w, float& z0, float& z1) {
+  const float u1 = fmaf((float)w.x, 0x1p-32f, fmaf((float)(w.y >> 11), 0x1p-53f, 0x1p-54f));
+  const float u2 = fmaf((float)w.z, 0x1p-32f, fmaf((float)(w.w >> 11), 0x1p-53f, 0x1p-54f));
+  const float rad = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  z0 = rad * c;
+  z1 = rad * s;
+}
+
+// ------------------------------------------------------------------------
+// Accumulators: plain in FP64; in FP32 a Neumaier-compensated sum, so that
+// costs and dot products over thousands of rows keep FP32-level relative error.
+// ------------------------------------------------------------------------
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <typename S>
+__device__ __forceinline__ S to_store(float x);
+template <>
+__device__ __forceinline__ float to_store<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ double to_store<double>(float x) { return (double)x; }
+template <typename S>
+__device__ __forceinline__ S to_store(double x) { return to_store<S>((float)x); }
+template <>
+__device__ __forceinline__ double to_store<double>(double x) { return x; }
+
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(double x) { return (float)x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// ------------------------------------------------------------------------
+// Models.  Each provides NX, NU, RPS (rows per stage), RT (terminal rows),
+// step(x, u) (one RK4 / discrete step in place), stage(x, u, emit) and
+// terminal(x, emit), where emit(row, value) receives residual rows in order.
+// ------------------------------------------------------------------------
+template <typename T>
+struct Pendulum {
+  static constexpr int NX = 2, NU = 1, RPS = 3, RT = 2;
+  T g_l, b, inv_ml2, h, h2, h6;
+  __device__ Pendulum(const Consts& c) {
+    g_l = (T)(c.params[0] / c.params[1]);
+    b = (T)c.params[3];
+    inv_ml2 = (T)(1.0 / (c.params[2] * c.params[1] * c.params[1]));
+    h = (T)c.dt;
+    h2 = (T)(0.5 * c.dt);
+    h6 = (T)(c.dt / 6.0);
+  }
+  __device__ __forceinline__ void f(const T* x, const T* u, T* d) const {
+    d[0] = x[1];
+    d[1] = -g_l * sin(x[0]) - b * x[1] + u[0] * inv_ml2;
+  }
+  __device__ __forceinline__ void step(T* x, const T* u) const {
+    T k[2], t[2], a[2];
+    f(x, u, k);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) { a[i] = k[i]; t[i] = x[i] + h2 * k[i]; }
+    f(t, u, k);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) { a[i] = a[i] + (T)2 * k[i]; t[i] = x[i] + h2 * k[i]; }
+    f(t, u, k);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) { a[i] = a[i] + (T)2 * k[i]; t[i] = x[i] + h * k[i]; }
+    f(t, u, k);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) x[i] = x[i] + h6 * (a[i] + k[i]);
+  }
+  template <class E>
+  __device__ __forceinline__ void stage(const T* x, const T* u, E& emit) const {
+    emit(0, x[0] - (T)3.141592653589793);
+    emit(1, (T)0.1 * x[1]);
+    emit(2, (T)0.1 * u[0]);
+  }
+  template <class E>
+  __device__ __forceinline__ void terminal(const T* x, E& emit) const {
+    emit(0, (T)10 * (x[0] - (T)3.141592653589793));
+    emit(1, (T)10 * x[1]);
+  }
+};
+
+// Chain of F = M-1 free point masses: state [p_1..p_F, v_1..v_F] (2-D each).
+template <typename T, int F>
+struct Chain {
+  static constexpr int NX = 4 * F, NU = 2, RPS = 2 * F + 2, RT = 2 * F;
+  T mass_inv, k, k3, c, g, l0, h, h2, h6;
+  const double* pref;  // target positions p* (2F)
+  __device__ Chain(const Consts& cs) {
+    mass_inv = (T)(1.0 / cs.params[0]);
+    k = (T)cs.params[1];
+    k3 = (T)cs.params[2];
+    c = (T)cs.params[3];
+    g = (T)cs.params[4];
+    l0 = (T)(1.0 / (double)F);
+    h = (T)cs.dt;
+    h2 = (T)(0.5 * cs.dt);
+    h6 = (T)(cs.dt / 6.0);
+    pref = nullptr;
+  }
+  // d = f(s, u): positions' rate is the velocity; link i (masses i-1, i) pulls
+  // with tension k d + k3 d^3 along its direction; damping -c v; force u on
+  // the last mass; gravity -g along y.
+  __device__ __forceinline__ void f(const T* s, const T* u, T* d) const {
+#pragma unroll
+    for (int i = 0; i < 2 * F; ++i) {
+      d[i] = s[2 * F + i];
+      d[2 * F + i] = -c * s[2 * F + i];
+    }
+#pragma unroll
+    for (int i = 1; i <= F; ++i) {
+      const T px0 = (i == 1) ? (T)0 : s[2 * (i - 2)];
+      const T py0 = (i == 1) ? (T)0 : s[2 * (i - 2) + 1];
+      const T dx = s[2 * (i - 1)] - px0;
+      const T dy = s[2 * (i - 1) + 1] - py0;
+      const T len = sqrt(dx * dx + dy * dy);
+      const T dd = len - l0;
+      const T fm = k * dd + k3 * dd * dd * dd;
+      const T fx = fm * dx / len, fy = fm * dy / len;
+      d[2 * F + 2 * (i - 1)] -= fx;
+      d[2 * F + 2 * (i - 1) + 1] -= fy;
+      if (i >= 2) {
+        d[2 * F + 2 * (i - 2)] += fx;
+        d[2 * F + 2 * (i - 2) + 1] += fy;
+      }
+    }
+    d[2 * F + 2 * (F - 1)] += u[0];
+    d[2 * F + 2 * (F - 1) + 1] += u[1];
+#pragma unroll
+    for (int i = 0; i < 2 * F; ++i) d[2 * F + i] = d[2 * F + i] * mass_inv;
+#pragma unroll
+    for (int i = 0; i < F; ++i) d[2 * F + 2 * i + 1] -= g;
+  }
+  __device__ __forceinline__ void step(T* x, const T* u) const {
+    T kk[NX], t[NX], a[NX];
+    f(x, u, kk);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { a[i] = kk[i]; t[i] = x[i] + h2 * kk[i]; }
+    f(t, u, kk);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { a[i] = a[i] + (T)2 * kk[i]; t[i] = x[i] + h2 * kk[i]; }
+    f(t, u, kk);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { a[i] = a[i] + (T)2 * kk[i]; t[i] = x[i] + h * kk[i]; }
+    f(t, u, kk);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) x[i] = x[i] + h6 * (a[i] + kk[i]);
+  }
+  template <class E>
+  __device__ __forceinline__ void stage(const T* x, const T* u, E& emit) const {
+#pragma unroll
+    for (int i = 0; i < 2 * F; ++i) emit(i, x[i] - (T)pref[i]);
+    emit(2 * F, (T)0.1 * u[0]);
+    emit(2 * F + 1, (T)0.1 * u[1]);
+  }
+  template <class E>
+  __device__ __forceinline__ void terminal(const T* x, E& emit) const {
+#pragma unroll
+    for (int i = 0; i < 2 * F; ++i) emit(i, x[i] - (T)pref[i]);
+  }
+};
+
+// Discrete linear model x+ = A x + B u with diagonal residual weights.
+template <typename T, int NXv, int NUv>
+struct Linear {
+  static constexpr int NX = NXv, NU = NUv, RPS = NXv + NUv, RT = NXv;
+  const double* lin;  // A (NX*NX), B (NX*NU), wq, wr, wqN
+  __device__ Linear(const Consts& cs) : lin(cs.lin) {}
+  __device__ __forceinline__ void step(T* x, const T* u) const {
+    T y[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      T s = (T)0;
+#pragma unroll
+      for (int j = 0; j < NX; ++j) s += (T)lin[i * NX + j] * x[j];
+#pragma unroll
+      for (int j = 0; j < NU; ++j) s += (T)lin[NX * NX + i * NU + j] * u[j];
+      y[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < NX; ++i) x[i] = y[i];
+  }
+  template <class E>
+  __device__ __forceinline__ void stage(const T* x, const T* u, E& emit) const {
+    const double* wq = lin + NX * NX + NX * NU;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) emit(i, (T)wq[i] * x[i]);
+#pragma unroll
+    for (int j = 0; j < NU; ++j) emit(NX + j, (T)wq[NX + j] * u[j]);
+  }
+  template <class E>
+  __device__ __forceinline__ void terminal(const T* x, E& emit) const {
+    const double* wqN = lin + NX * NX + NX * NU + NX + NU;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) emit(i, (T)wqN[i] * x[i]);
+  }
+};
+
+}  // namespace gnm

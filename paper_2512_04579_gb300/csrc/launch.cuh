@@ -1,0 +1,73 @@
+// launch.cuh -- host-side launch table of the model-templated rollout kernels.
+// Internal; one table per storage precision (rollout_{f64,f32,bf16}.cu).
+#pragma once
+#include "rollout.cuh"
+
+namespace gnm {
+
+struct Launchers {
+  void (*samples)(const RollArgs&, int nblocks, int smem, cudaStream_t);
+  void (*line)(const RollArgs&, int nthreads, cudaStream_t);
+  void (*cost64)(const RollArgs&, int nthreads, cudaStream_t);
+};
+
+// key: chain -> free masses F; linear -> nx * 16 + nu; pendulum -> 0.
+bool launchers_f64(int dyn, int key, Launchers* out);
+bool launchers_f32(int dyn, int key, Launchers* out);
+bool launchers_bf16(int dyn, int key, Launchers* out);
+
+template <class Model, typename T, typename S>
+void launch_samples(const RollArgs& a, int nb, int smem, cudaStream_t s) {
+  if (a.cs.antithetic)
+    k_samples<Model, T, S, true><<<nb, 128, smem, s>>>(a);
+  else
+    k_samples<Model, T, S, false><<<nb, 128, smem, s>>>(a);
+}
+template <class Model, typename T>
+void launch_line(const RollArgs& a, int nthreads, cudaStream_t s) {
+  if (nthreads > 0) k_line<Model, T><<<(nthreads + 127) / 128, 128, 0, s>>>(a);
+}
+
+template <class M32, class M64, typename T, typename S>
+void fill(Launchers* o) {
+  o->samples = &launch_samples<M32, T, S>;
+  o->line = &launch_line<M32, T>;
+  o->cost64 = &launch_line<M64, double>;
+}
+
+#define GNM_DEFINE_LAUNCHERS(NAME, T, S)                                              \
+  bool NAME(int dyn, int key, Launchers* o) {                                         \
+    switch (dyn) {                                                                    \
+      case kPendulum:                                                                 \
+        fill<Pendulum<T>, Pendulum<double>, T, S>(o);                                 \
+        return true;                                                                  \
+      case kChain:                                                                    \
+        switch (key) {                                                                \
+          GNM_CHAIN_CASE(T, S, 1) GNM_CHAIN_CASE(T, S, 2) GNM_CHAIN_CASE(T, S, 3)     \
+          GNM_CHAIN_CASE(T, S, 4) GNM_CHAIN_CASE(T, S, 5) GNM_CHAIN_CASE(T, S, 6)     \
+          GNM_CHAIN_CASE(T, S, 7) GNM_CHAIN_CASE(T, S, 8) GNM_CHAIN_CASE(T, S, 9)     \
+          GNM_CHAIN_CASE(T, S, 10) GNM_CHAIN_CASE(T, S, 11) GNM_CHAIN_CASE(T, S, 12)  \
+          GNM_CHAIN_CASE(T, S, 13) GNM_CHAIN_CASE(T, S, 14) GNM_CHAIN_CASE(T, S, 15)  \
+          GNM_CHAIN_CASE(T, S, 16)                                                    \
+          default: return false;                                                      \
+        }                                                                             \
+      case kLinear:                                                                   \
+        switch (key) {                                                                \
+          GNM_LIN_CASE(T, S, 2, 1) GNM_LIN_CASE(T, S, 2, 2) GNM_LIN_CASE(T, S, 4, 1)  \
+          GNM_LIN_CASE(T, S, 4, 2) GNM_LIN_CASE(T, S, 1, 1)                           \
+          default: return false;                                                      \
+        }                                                                             \
+      default:                                                                        \
+        return false;                                                                 \
+    }                                                                                 \
+  }
+#define GNM_CHAIN_CASE(T, S, F) \
+  case F:                       \
+    fill<Chain<T, F>, Chain<double, F>, T, S>(o); \
+    return true;
+#define GNM_LIN_CASE(T, S, X, U) \
+  case X * 16 + U:               \
+    fill<Linear<T, X, U>, Linear<double, X, U>, T, S>(o); \
+    return true;
+
+}  // namespace gnm

@@ -1,0 +1,229 @@
+// rollout.cuh -- batched RK4 rollouts of the GN-MPPI hot path (arXiv 2512.04579):
+//   * k_samples: the K perturbed rollouts of one Algorithm-1 iteration (Sec. 4.1,
+//     Eq. 7 sampled as in Method D, antithetic pairs as in Sec. 5), with the
+//     residual, cost and Jacobian-reconstruction operands fused into the rollout:
+//     each pair writes dR_m = (R(U+W_m) - R(U-W_m))/2 and W_m column-wise into
+//     sample-contiguous rows, its two costs C = 0.5||R||^2 (Eq. 2, 4) and
+//     e_m = dR_m . r (so that P^T r = W^T e needs no second pass over dR);
+//   * k_line: the L step-length candidates of the line search (Eq. 11), the
+//     nominal rollout R(U_k), and FP64 cost re-evaluation.
+// One thread per rollout; the two rollouts of an antithetic pair sit in
+// adjacent lanes and exchange residual rows with one shuffle.  States stay in
+// registers (the models are compile-time sized), controls and sampling scales
+// are staged through shared memory.  Internal; instantiated per precision.
+#pragma once
+#include "common.cuh"
+
+namespace gnm {
+
+struct RollArgs {
+  const InstDesc* inst;
+  InstState* st;
+  Consts cs;
+  const double* x0;
+  const double* xref;
+  const double* U;
+  const double* s;
+  const double* delta;
+  const void* r;      // nominal residual [nR] per instance (scalar type)
+  void* dR;           // [nR][ldK] storage type
+  void* W;            // [n][ldK]  storage type
+  double* C;          // [Kp][2]
+  double* e;          // [Kp]
+  void* RL;           // [L][nR] scalar type
+  double* Cl;         // [kMaxL + 1] per instance
+  double* Cout;       // cost output (mode 2)
+  const int2* bmap;   // sample blocks: (instance, chunk)
+  const int* list;    // instances of this launch (line / nominal / cost)
+  int count;          // entries of list
+  int ncand;          // candidates per instance (line search)
+  uint32_t it;        // iteration index of the noise stream
+  int mode;           // k_line: 0 line search, 1 nominal, 2 FP64 cost only
+};
+
+template <class Model>
+__device__ __forceinline__ void bind_model(Model&, const RollArgs&, const InstDesc&) {}
+template <typename T, int F>
+__device__ __forceinline__ void bind_model(Chain<T, F>& m, const RollArgs& a, const InstDesc& I) {
+  m.pref = a.xref + I.o_xref;
+}
+
+template <typename T>
+struct StageSum {
+  T s = (T)0;
+};
+
+// Emitter for the sample kernel: antithetic difference across the pair lanes,
+// dR / e written by the lane whose parity matches the row.
+template <typename T, typename S, bool ANTI>
+struct SampleEmit {
+  S* dR;
+  const T* r;
+  int ldK, m, base, par;
+  bool active;
+  T sign;
+  T csum;
+  Acc<T>* eacc;
+  __device__ __forceinline__ void operator()(int i, T v) {
+    csum += v * v;
+    const int row = base + i;
+    if (ANTI) {
+      const T vo = __shfl_xor_sync(0xffffffffu, v, 1);
+      if (par == (row & 1)) {
+        const T d = sign * (v - vo) * (T)0.5;
+        if (active) dR[(int64_t)row * ldK + m] = to_store<S>(d);
+        eacc->add(d * r[row]);
+      }
+    } else {
+      const T d = v - r[row];
+      if (active) dR[(int64_t)row * ldK + m] = to_store<S>(d);
+      eacc->add(d * r[row]);
+    }
+  }
+};
+
+template <class Model, typename T, typename S, bool ANTI>
+__global__ void __launch_bounds__(128) k_samples(RollArgs a) {
+  constexpr int NX = Model::NX, NU = Model::NU;
+  const int2 bm = a.bmap[blockIdx.x];
+  const InstDesc I = a.inst[bm.x];
+  if (a.st[bm.x].status != 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sU = reinterpret_cast<T*>(smem_raw);
+  T* sS = sU + I.n;
+  for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+    sU[j] = (T)a.U[I.o_U + j];
+    sS[j] = (T)a.s[I.o_U + j];
+  }
+  __syncthreads();
+
+  const int per_block = ANTI ? kPairsPerBlock : kSamplesPerBlock;
+  const int local = ANTI ? (threadIdx.x >> 1) : threadIdx.x;
+  const int m = bm.y * per_block + local;
+  const bool active = m < I.Kp;
+  const int par = ANTI ? (threadIdx.x & 1) : 0;
+  const T sign = par ? (T)-1 : (T)1;
+
+  Model md(a.cs);
+  bind_model(md, a, I);
+  T x[NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) x[i] = (T)a.x0[I.o_x0 + i];
+
+  S* dR = reinterpret_cast<S*>(a.dR) + I.o_dR;
+  S* Wm = reinterpret_cast<S*>(a.W) + I.o_W;
+  const T* r = reinterpret_cast<const T*>(a.r) + I.o_R;
+  Acc<T> cost, eacc;
+  SampleEmit<T, S, ANTI> em{dR, r, I.ldK, m, 0, par, active, sign, (T)0, &eacc};
+  const uint32_t mm = active ? (uint32_t)m : 0u;
+  int qc = -1;
+  T z0 = (T)0, z1 = (T)0;
+  for (int k = 0; k < I.N; ++k) {
+    T u[NU];
+#pragma unroll
+    for (int c = 0; c < NU; ++c) {
+      const int j = k * NU + c;
+      const int q = j >> 1;
+      if (q != qc) {
+        box_muller(noise_words(a.cs.seed, (uint32_t)bm.x, a.it, mm, (uint32_t)q), z0, z1);
+        qc = q;
+      }
+      const T w = sS[j] * ((j & 1) ? z1 : z0);
+      u[c] = sU[j] + sign * w;
+      if (active && par == (ANTI ? (j & 1) : 0)) Wm[(int64_t)j * I.ldK + m] = to_store<S>(w);
+    }
+    em.base = k * Model::RPS;
+    em.csum = (T)0;
+    md.stage(x, u, em);
+    cost.add(em.csum);
+    md.step(x, u);
+  }
+  em.base = I.N * Model::RPS;
+  em.csum = (T)0;
+  md.terminal(x, em);
+  cost.add(em.csum);
+
+  const double Cself = 0.5 * cost.value();
+  double ev = eacc.value();
+  double Cother = Cself;
+  if (ANTI) {
+    Cother = __shfl_xor_sync(0xffffffffu, Cself, 1);
+    ev += __shfl_xor_sync(0xffffffffu, ev, 1);
+  }
+  const bool ok = isfinite(Cself) && isfinite(Cother) && isfinite(ev);
+  if (active) {
+    a.C[I.o_C + (ANTI ? 2 * m + par : m)] = Cself;
+    if (par == 0) a.e[I.o_C / 2 + m] = ok ? ev : 0.0;
+    if (!ok) {  // dropped pair: its columns leave P and S
+      const int rows = I.N * Model::RPS + Model::RT;
+      for (int row = par; row < rows; row += (ANTI ? 2 : 1)) dR[(int64_t)row * I.ldK + m] = to_store<S>(0.0f);
+      for (int j = par; j < I.n; j += (ANTI ? 2 : 1)) Wm[(int64_t)j * I.ldK + m] = to_store<S>(0.0f);
+    }
+  }
+}
+
+template <typename T>
+struct LineEmit {
+  T* out;  // nullptr: cost only
+  int base;
+  T csum;
+  __device__ __forceinline__ void operator()(int i, T v) {
+    csum += v * v;
+    if (out) out[base + i] = v;
+  }
+};
+
+// One thread per (instance, candidate).  mode 0: candidate j rolls out
+// U + gamma^j delta; mode 1: the nominal U; mode 2: the nominal U in FP64 into
+// Cout.  Instances whose status is not OK are skipped.
+template <class Model, typename T>
+__global__ void __launch_bounds__(128) k_line(RollArgs a) {
+  constexpr int NX = Model::NX, NU = Model::NU;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ncand = a.mode == 0 ? a.ncand : 1;
+  if (t >= a.count * ncand) return;
+  const int b = a.list[t / ncand];
+  const int j = t % ncand;
+  const InstDesc I = a.inst[b];
+  if (a.mode != 2 && a.st[b].status != 0) return;
+  double alpha = 0.0;
+  if (a.mode == 0) {
+    alpha = 1.0;
+    for (int q = 0; q < j; ++q) alpha *= a.cs.gamma;
+  }
+  Model md(a.cs);
+  bind_model(md, a, I);
+  T x[NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) x[i] = (T)a.x0[I.o_x0 + i];
+  T* out = nullptr;
+  if (a.mode == 0) out = reinterpret_cast<T*>(a.RL) + I.o_RL + (int64_t)j * I.nR;
+  if (a.mode == 1) out = const_cast<T*>(reinterpret_cast<const T*>(a.r)) + I.o_R;
+  LineEmit<T> em{out, 0, (T)0};
+  Acc<T> cost;
+  const double* U = a.U + I.o_U;
+  const double* D = a.delta + I.o_U;
+  for (int k = 0; k < I.N; ++k) {
+    T u[NU];
+#pragma unroll
+    for (int c = 0; c < NU; ++c) {
+      const int q = k * NU + c;
+      u[c] = (a.mode == 0) ? (T)(U[q] + alpha * D[q]) : (T)U[q];
+    }
+    em.base = k * Model::RPS;
+    em.csum = (T)0;
+    md.stage(x, u, em);
+    cost.add(em.csum);
+    md.step(x, u);
+  }
+  em.base = I.N * Model::RPS;
+  em.csum = (T)0;
+  md.terminal(x, em);
+  cost.add(em.csum);
+  const double C = 0.5 * cost.value();
+  if (a.mode == 0) a.Cl[(int64_t)b * (kMaxL + 1) + j] = C;
+  if (a.mode == 1) a.st[b].C_nom = C;
+  if (a.mode == 2) a.Cout[b] = C;
+}
+
+}  // namespace gnm

@@ -1,0 +1,5 @@
+// FP64 instantiation of the rollout kernels (parity mode).
+#include "launch.cuh"
+namespace gnm {
+GNM_DEFINE_LAUNCHERS(launchers_f64, double, double)
+}

@@ -1,0 +1,55 @@
+"""Write the reference optima C* of the chain benchmark instances.
+
+Calls only the FP64 CPU oracle.  For each instance b of the seeded workload
+(chain M=10, N=100, K=2048, 30 iterations, sigma0 0.2, lambda 1e-3,
+seed 2512045790 + 1):
+  C_gn  = cost after the oracle's 30-iteration GN-MPPI solve (Algorithm 1),
+  C*    = cost after polishing that solution with Method A (central-FD GGN,
+          Sec. 5) until the FD gradient falls below 1e-10 or no step helps.
+Output: chain_m10_cstar.txt (one line per instance: b C_gn C*).
+
+Usage: python tests/golden/make_cstar.py [batch] [processes]
+"""
+import multiprocessing as mp
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+M, N, K, T, SIGMA0, LAM = 10, 100, 2048, 30, 0.2, 1e-3
+
+
+def one(b):
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2512_04579_gb300 import inputs as I
+
+    seed = I.BASE_SEED + 1
+    x0, tgt = I.chain_instances(seed, BATCH, M)
+    m = O.chain(M=M, N=N)
+    opt = O.Options(K=K, iterations=T, lam=LAM, seed=seed, threads=1)
+    st, U, Uh, Ch, its = O.solve(m, opt, x0[b], tgt[b], np.zeros(m.n), SIGMA0, inst=b)
+    stA, UA, CA, itA = O.method_a(m, x0[b], tgt[b], U.copy(), max_iter=300, lam=LAM)
+    return b, Ch[-1], min(CA, Ch[-1])
+
+
+BATCH = int(sys.argv[1]) if len(sys.argv) > 1 else 256
+
+if __name__ == "__main__":
+    procs = int(sys.argv[2]) if len(sys.argv) > 2 else os.cpu_count()
+    from oracle import oracle as O
+
+    O.build()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        rows = sorted(pool.map(one, range(BATCH), chunksize=1))
+    out = os.path.join(HERE, "chain_m10_cstar.txt")
+    with open(out, "w") as f:
+        f.write(f"# chain M={M} N={N} K={K} T={T} sigma0={SIGMA0} lambda={LAM} seed=2512045790+1 batch={BATCH}\n")
+        f.write("# written by tests/golden/make_cstar.py from the FP64 oracle: b C_gn C_star\n")
+        for b, cg, cs in rows:
+            f.write(f"{b} {cg:.17g} {cs:.17g}\n")
+    print("wrote", out)

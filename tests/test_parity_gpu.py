@@ -1,0 +1,281 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+FP64 mode: relative 1e-10 (normwise for vectors) per Algorithm-1 iteration,
+with the oracle's iterate U_k fed to both sides so that the comparison never
+drifts.  Reduced-precision modes: 1e-4 relative on costs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2512_04579_gb300 import gnmppi as G
+from paper_2512_04579_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOLRED = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2512_04579_gb300 import build as B
+
+    B.build()
+    return G.load()
+
+
+def rel(a, b):
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def sigmas(s0, beta, T, n):
+    s = np.full(n, float(s0))
+    out = []
+    sb = math.sqrt(beta)
+    for _ in range(T):
+        out.append(s.copy())
+        s = s * sb
+    return out
+
+
+def check_iteration(rep, Ug, it, C_ref, tol, tie=1e-12):
+    """Compare one GPU iteration report with an oracle record."""
+    assert rep.status == it.status == 0
+    assert rep.C_nom == pytest.approx(it.C_nom, rel=tol)
+    if rep.j_star != it.j_star:
+        # a tie between two step lengths: both must give the same cost
+        assert abs(it.C_line[rep.j_star] - it.C_line[it.j_star]) <= tie * abs(C_ref)
+    else:
+        assert rel(Ug, it.U_next) < tol
+    assert rep.C_new == pytest.approx(it.C_new, rel=tol)
+
+
+def per_iteration_parity(model, gprob, opt, x0, xref, U0, s0, T, tol=TOL64, sample_check=True):
+    st, Uend, Uh, Ch, its = O.solve(model, opt, x0, xref, U0, s0)
+    assert st == 0
+    ss = sigmas(s0, opt.beta, T, model.n)
+    solver = G.Solver(gprob, 1)
+    try:
+        for k in range(T):
+            stg, Ug, rep = solver.step(x0, xref, Uh[k], ss[k], k)
+            r = rep[0]
+            it = its[k]
+            check_iteration(r, Ug, it, Ch[k], tol)
+            d = solver.debug("delta")
+            assert rel(d, it.delta) < tol, f"iteration {k}: delta"
+            np.testing.assert_allclose(solver.debug("Cline"), it.C_line[: opt.L], rtol=tol)
+            assert r.c_min == pytest.approx(it.c_min, rel=tol)
+            assert r.ess == pytest.approx(it.ess, rel=1e-8)
+            assert r.n_masked == it.n_masked
+            assert rel(solver.debug("mppi"), it.mppi_dir) < 1e-8
+            if sample_check and k in (0, T - 1):
+                big = O.iteration(model, opt, x0, xref, Uh[k], ss[k], it=k, want_big=True)
+                Kp = big.W.shape[0]
+                dR = solver.debug("dR").reshape(model.nR, Kp)
+                W = solver.debug("W").reshape(model.n, Kp)
+                assert rel(dR, big.dR.T) < tol
+                assert rel(W, big.W.T) < 1e-13
+                np.testing.assert_allclose(solver.debug("C"), big.C_samp, rtol=1e-12)
+                assert rel(solver.debug("e"), big.dR @ big.r) < tol
+    finally:
+        solver.close()
+    return its
+
+
+# ----------------------------------------------------------------- FP64 mode
+def test_fp64_pendulum_swingup_per_iteration():
+    """Pendulum swing-up, N=50, K=256, sigma 0.5, lambda 1e-3, 20 iterations."""
+    seed = I.BASE_SEED
+    x0 = I.pendulum_x0(seed, 1)[0]
+    m = O.pendulum()
+    opt = O.Options(K=256, iterations=20, lam=1e-3, seed=seed)
+    gp = G.pendulum_problem(N=50, K=256, iterations=20, lam=1e-3, sigma0=0.5, seed=seed)
+    per_iteration_parity(m, gp, opt, x0, None, np.zeros(m.n), 0.5, 20)
+
+
+def test_fp64_chain_ragged_sizes_per_iteration():
+    """Chain M=5, N=30 (n=60, nR=308), K=300 (150 pairs: 64+64+22), 6 iterations."""
+    seed = I.BASE_SEED + 11
+    M, N, K = 5, 30, 300
+    x0, tgt = I.chain_instances(seed, 1, M)
+    m = O.chain(M=M, N=N)
+    opt = O.Options(K=K, iterations=6, lam=1e-3, seed=seed)
+    gp = G.chain_problem(M=M, N=N, K=K, iterations=6, lam=1e-3, sigma0=0.2, seed=seed)
+    per_iteration_parity(m, gp, opt, x0[0], tgt[0], np.zeros(m.n), 0.2, 6)
+
+
+def test_fp64_sigma_mode_when_samples_are_fewer_than_unknowns():
+    """K' = 20 pairs < n = 60: AUTO picks the printed Monte Carlo form (SIGMA)."""
+    seed = 5
+    M, N, K = 4, 30, 40
+    x0, tgt = I.chain_instances(seed, 1, M)
+    m = O.chain(M=M, N=N)
+    opt = O.Options(K=K, iterations=3, lam=1e-2, seed=seed)
+    gp = G.chain_problem(M=M, N=N, K=K, iterations=3, lam=1e-2, sigma0=0.2, seed=seed)
+    its = per_iteration_parity(m, gp, opt, x0[0], tgt[0], np.zeros(m.n), 0.2, 3)
+    assert all(it.jac_mode_used == 1 for it in its)
+
+
+def test_fp64_one_sided_and_monotone_options():
+    seed = 9
+    x0 = I.pendulum_x0(seed, 1)[0]
+    m = O.pendulum(N=25)
+    opt = O.Options(K=80, iterations=3, lam=1e-3, antithetic=False, monotone=True, seed=seed)
+    gp = G.pendulum_problem(N=25, K=80, iterations=3, lam=1e-3, sigma0=0.4, antithetic=False, monotone=True,
+                            seed=seed)
+    per_iteration_parity(m, gp, opt, x0, None, np.zeros(m.n), 0.4, 3)
+
+
+def _lq(N):
+    h = 0.1
+    A = np.array([[1.0, h], [0.0, 1.0]])
+    B = np.array([[h * h / 2], [h]])
+    wq = np.sqrt(2.0) * np.ones(2)
+    wr = np.sqrt(0.02) * np.ones(1)
+    wqN = np.sqrt(20.0) * np.ones(2)
+    return A, B, wq, wr, wqN
+
+
+def test_fp64_lq_single_newton_step_reaches_closed_form():
+    """Problem IV: one GGN step with lambda = 0 reaches the batch least-squares solution."""
+    N = 50
+    A, B, wq, wr, wqN = _lq(N)
+    x0 = np.array([1.0, 0.0])
+    m = O.linear(A, B, wq, wr, wqN, N)
+    # closed form from the oracle-independent affine map R(U) = G U + h
+    Gm = np.zeros((m.nR, N))
+    h0 = O.residual(m, x0, None, np.zeros(N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        Gm[:, j] = O.residual(m, x0, None, e) - h0
+    Ustar = np.linalg.lstsq(Gm, -h0, rcond=None)[0]
+    gp = G.linear_problem(A, B, wq, wr, wqN, N=N, K=128, iterations=1, lam=0.0, sigma0=0.5, seed=3)
+    s = G.Solver(gp, 1)
+    st, U, rep = s.step(x0, None, np.zeros(N), np.full(N, 0.5), 0)
+    s.close()
+    assert st == 0 and rep[0].j_star == 0
+    assert rel(U, Ustar) < 1e-8
+
+
+def test_fp64_uneven_batch_matches_per_instance_oracle():
+    """Three chain instances of different M, N, K in one handle."""
+    seed = 21
+    shapes = [(20, 4, 64), (33, 6, 130), (12, 3, 200)]
+    x0s, tgts, U0s = [], [], []
+    for i, (N, M, K) in enumerate(shapes):
+        x0, tg = I.chain_instances(seed + i, 1, M)
+        x0s.append(x0[0])
+        tgts.append(tg[0])
+        U0s.append(np.zeros(N * 2))
+    gp = G.chain_problem(M=4, N=20, K=64, iterations=2, lam=1e-3, sigma0=0.2, seed=seed)
+    s = G.Solver(gp, 3, shapes=shapes)
+    sig = [np.full(N * 2, 0.2) for (N, M, K) in shapes]
+    st, U, rep = s.step(np.concatenate(x0s), np.concatenate(tgts), np.concatenate(U0s), np.concatenate(sig), 0)
+    assert st == 0
+    for i, (N, M, K) in enumerate(shapes):
+        m = O.chain(M=M, N=N)
+        it = O.iteration(m, O.Options(K=K, lam=1e-3, seed=seed), x0s[i], tgts[i], U0s[i], 0.2, inst=i, it=0)
+        Ui = U[s.off_U[i]: s.off_U[i + 1]]
+        check_iteration(rep[i], Ui, it, it.C_nom, TOL64)
+        assert rel(s.debug("delta", i), it.delta) < TOL64
+    s.close()
+
+
+def test_fp64_whole_solve_graph_matches_oracle():
+    """gnmppi_solve (one CUDA graph) over 8 iterations vs the oracle's solve."""
+    seed = 33
+    M, N, K = 4, 20, 128
+    x0, tgt = I.chain_instances(seed, 1, M)
+    m = O.chain(M=M, N=N)
+    opt = O.Options(K=K, iterations=8, lam=1e-3, seed=seed)
+    st, Uo, Uh, Ch, its = O.solve(m, opt, x0[0], tgt[0], np.zeros(m.n), 0.2)
+    gp = G.chain_problem(M=M, N=N, K=K, iterations=8, lam=1e-3, sigma0=0.2, seed=seed)
+    s = G.Solver(gp, 1)
+    stg, U, rep = s.solve(x0[0], tgt[0], np.zeros(m.n))
+    assert stg == 0 and rep[0].iterations == 8
+    assert rep[0].C_final == pytest.approx(Ch[-1], rel=TOL64)
+    assert rel(U, Uo) < 1e-9
+    assert rep[0].sigma_final == pytest.approx(0.2 * math.sqrt(0.7) ** 8, rel=1e-14)
+    # a second solve on the same handle replays the graph and gives the same answer
+    stg2, U2, rep2 = s.solve(x0[0], tgt[0], np.zeros(m.n))
+    assert np.array_equal(U, U2)
+    s.close()
+
+
+def test_fp64_cost_reevaluation():
+    seed = 4
+    M, N = 10, 100
+    x0, tgt = I.chain_instances(seed, 3, M)
+    rng = np.random.default_rng(1)
+    U = rng.normal(0, 0.3, size=(3, N * 2))
+    gp = G.chain_problem(M=M, N=N, K=64, iterations=1, precision=G.PREC_FP32, seed=seed)
+    s = G.Solver(gp, 3)
+    C = s.cost(x0, tgt, U)
+    s.close()
+    m = O.chain(M=M, N=N)
+    for b in range(3):
+        assert C[b] == pytest.approx(O.cost(m, x0[b], tgt[b], U[b]), rel=1e-12)
+
+
+def test_nonfinite_samples_are_dropped_like_the_oracle():
+    seed = 0
+    m = O.pendulum(N=5)
+    x0 = np.array([0.1, 0.0])
+    it = O.iteration(m, O.Options(K=16, seed=seed), x0, None, np.zeros(5), 1e200)
+    gp = G.pendulum_problem(N=5, K=16, iterations=1, sigma0=1.0, seed=seed)
+    s = G.Solver(gp, 1)
+    st, U, rep = s.step(x0, None, np.zeros(5), np.full(5, 1e200), 0)
+    s.close()
+    assert rep[0].n_masked == it.n_masked
+    assert rep[0].status == it.status
+
+
+# -------------------------------------------------------- reduced precision
+@pytest.mark.parametrize("prec", [G.PREC_FP32, G.PREC_BF16])
+def test_reduced_precision_chain_full_size_iteration(prec):
+    """Chain M=10, N=100 (n=200, nR=2018), K=2048, sigma 0.2: one iteration at
+    full size against the FP64 oracle, costs within 1e-4."""
+    seed = I.BASE_SEED + 1
+    M, N, K = 10, 100, 2048
+    x0, tgt = I.chain_instances(seed, 1, M)
+    m = O.chain(M=M, N=N)
+    opt = O.Options(K=K, iterations=1, lam=1e-3, seed=seed, threads=8)
+    it = O.iteration(m, opt, x0[0], tgt[0], np.zeros(m.n), 0.2)
+    gp = G.chain_problem(M=M, N=N, K=K, iterations=1, lam=1e-3, sigma0=0.2, seed=seed, precision=prec)
+    s = G.Solver(gp, 1)
+    st, U, rep = s.step(x0[0], tgt[0], np.zeros(m.n), np.full(m.n, 0.2), 0)
+    Cs = s.debug("C")
+    s.close()
+    assert st == 0
+    assert rep[0].C_nom == pytest.approx(it.C_nom, rel=TOLRED)
+    np.testing.assert_allclose(Cs, it.C_samp, rtol=TOLRED)
+    assert rep[0].C_new == pytest.approx(it.C_new, rel=TOLRED)
+    # U_0 = 0, so U_1 = alpha* delta on both sides: the step directions agree
+    cosang = float(np.dot(U, it.U_next) / (np.linalg.norm(U) * np.linalg.norm(it.U_next)))
+    assert cosang > 0.999
+
+
+@pytest.mark.parametrize("prec", [G.PREC_FP32, G.PREC_BF16])
+def test_reduced_precision_chain_solve_cost(prec):
+    """Chain M=6, N=40, K=512, 10 iterations: final cost within 1e-4 of the oracle's."""
+    seed = 77
+    M, N, K, T = 6, 40, 512, 10
+    x0, tgt = I.chain_instances(seed, 1, M)
+    m = O.chain(M=M, N=N)
+    st, Uo, Uh, Ch, its = O.solve(m, O.Options(K=K, iterations=T, lam=1e-3, seed=seed, threads=8), x0[0], tgt[0],
+                                  np.zeros(m.n), 0.2)
+    gp = G.chain_problem(M=M, N=N, K=K, iterations=T, lam=1e-3, sigma0=0.2, seed=seed, precision=prec)
+    s = G.Solver(gp, 1)
+    stg, U, rep = s.solve(x0[0], tgt[0], np.zeros(m.n))
+    C = s.cost(x0[0], tgt[0], U)[0]
+    s.close()
+    assert stg == 0
+    assert C == pytest.approx(Ch[-1], rel=TOLRED)
+    assert O.cost(m, x0[0], tgt[0], U) == pytest.approx(C, rel=1e-12)
