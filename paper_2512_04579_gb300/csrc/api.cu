@@ -15,6 +15,7 @@
 #include "../../include/gnmppi.h"
 #include "launch.cuh"
 #include "solver_kernels.cuh"
+#include "tc_contract.cuh"
 
 using namespace gnm;
 
@@ -58,6 +59,7 @@ struct gnmppi_s {
   int smem_n_max = 0;
   int solve_smem = 0;
   bool use_tc = false;
+  TcPlan tc{};
   // graph of one Algorithm-1 solve
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_nodes = 0;
@@ -229,8 +231,11 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     d.o_x0 = oX; oX += d.nx;
     d.o_xref = oR; oR += d.nref;
     d.o_U = oU; oU += d.n;
-    d.o_dR = odR; odR += (int64_t)d.nR * d.ldK;
-    d.o_W = oW; oW += (int64_t)d.n * d.ldK;
+    // dR and W of an instance form one [nR + n][ldK] block (W rows last), so a
+    // single TMA tensor map covers both contraction operands
+    d.o_dR = odR;
+    d.o_W = odR + (int64_t)d.nR * d.ldK;
+    odR += (int64_t)(d.nR + d.n) * d.ldK;
     d.o_C = oC; oC += 2 * (int64_t)d.Kp;
     d.o_P = oP; oP += (int64_t)d.n * d.ldP;
     d.o_nn = onn; onn += (int64_t)d.n * d.n;
@@ -288,7 +293,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   AL(h->d_Cl, 8 * (int64_t)h->batch * (kMaxL + 1));
   AL(h->d_Cout, 8 * (int64_t)h->batch);
   AL(h->d_dR, h->szS * h->n_dR);
-  AL(h->d_W, h->szS * h->n_W);
+  h->d_W = h->d_dR;
   AL(h->d_P, h->szA * h->n_P);
   AL(h->d_r, h->szT * h->n_R);
   AL(h->d_RL, h->szT * h->n_RL);
@@ -369,6 +374,13 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   c.nx_lin = p.nx;
   c.nu_lin = p.nu;
   c.lin = h->d_lin;
+  // tensor-core contraction (TF32 on FP32 operands, or BF16)
+  h->use_tc = prec != kFP64;
+  if (h->use_tc) {
+    st = tc_plan_create(h->desc, h->d_dR, prec == kBF16 ? 1 : 0, h->stream, &h->tc, h->err);
+    for (void* q : h->tc.allocs) h->allocs.push_back(q);
+    if (st != GNMPPI_OK) return st;
+  }
   // the Cholesky kernel keeps its factor in up to the opt-in shared-memory limit
   if (8 * (int64_t)3 * n_all_max > solve_budget) return fail(h, GNMPPI_E_ARG, "N*nu too large for the solver");
   if (prec == kFP64) {
@@ -521,7 +533,10 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
   h->launches++;
   MARK(2);
   GemmArgs ga{h->d_desc, h->d_st, nullptr, h->d_dR, h->d_W, h->d_P, h->d_A, h->d_S2};
-  {
+  if (h->use_tc) {
+    CK(tc_contract_launch(h->tc, h->d_desc, h->d_st, reinterpret_cast<float*>(h->d_P), h->stream));
+    h->launches++;
+  } else {
     ga.tiles = h->d_tiles[0];
     k_gemm_nt<kContract, S, TC, TA><<<h->ntiles[0], 256, 0, h->stream>>>(ga);
     CKL();
@@ -615,6 +630,18 @@ static gnmppi_status load_inputs(gnmppi_t h, int32_t mem, const double* x0, cons
   return GNMPPI_OK;
 }
 
+// A bounded device wait that ran out leaves a flag; report it once and clear it.
+static gnmppi_status check_timeout(gnmppi_t h) {
+  if (!h->use_tc) return GNMPPI_OK;
+  int flag = 0;
+  CK(cudaMemcpy(&flag, h->tc.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    CK(cudaMemset(h->tc.d_err, 0, sizeof(int)));
+    return fail(h, GNMPPI_E_TIMEOUT, "a bounded wait in the tensor-core contraction ran out");
+  }
+  return GNMPPI_OK;
+}
+
 static gnmppi_status worst_status(const std::vector<InstState>& s) {
   int w = 0;
   for (auto& x : s)
@@ -653,6 +680,7 @@ extern "C" gnmppi_status gnmppi_solve(gnmppi_t h, int32_t mem, const double* x0,
   std::vector<InstState> s(h->batch);
   CK(cudaMemcpyAsync(s.data(), h->d_st, sizeof(InstState) * h->batch, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if ((st = check_timeout(h)) != GNMPPI_OK) return st;
   if (rep) {
     std::vector<double> s_end(h->n_U);
     CK(cudaMemcpy(s_end.data(), h->d_s, 8 * h->n_U, cudaMemcpyDeviceToHost));
@@ -684,6 +712,7 @@ extern "C" gnmppi_status gnmppi_step(gnmppi_t h, int32_t mem, const double* x0, 
   std::vector<InstState> s(h->batch);
   CK(cudaMemcpyAsync(s.data(), h->d_st, sizeof(InstState) * h->batch, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if ((st = check_timeout(h)) != GNMPPI_OK) return st;
   if (rep) {
     for (int b = 0; b < h->batch; ++b) {
       gnmppi_iter_report& r = rep[b];
