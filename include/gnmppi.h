@@ -188,6 +188,35 @@ gnmppi_status gnmppi_phase_times(gnmppi_t h, int32_t iteration, double* ms, int3
  * "gram", "s2", "solve", "line", "update"), or NULL. */
 const char* gnmppi_phase_name(int32_t i);
 
+/* Softmin weights exp(-(C - min C)/tau) and the weighted mean perturbation
+ * sum w_i W_i / sum w_i of one sample set, computed without any device
+ * allocation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory when they call in -- a real-time
+ * controller whose per-cycle latency budget has no room for cudaMalloc /
+ * cudaFree (unbounded latency; cudaFree synchronises the device), or a host
+ * that grants the library a fixed memory budget up front and forbids later
+ * allocation.
+ *   C      device, count doubles (one-sided) or 2*count doubles (antithetic:
+ *          C[2m] = C(U + W_m), C[2m+1] = C(U - W_m)); non-finite pairs get
+ *          weight 0.
+ *   W      device, [n][count] doubles, sample-contiguous rows (the layout of
+ *          gnmppi_debug_read buffer 1).
+ *   mppi   device, n doubles out; stats device, 4 doubles out:
+ *          {min C, sum w, sum w^2, effective sample size}.
+ *   cuda_stream  cudaStream_t or NULL; the call is asynchronous on it.
+ *   err    optional host buffer of err_len bytes for the error text.
+ * Scratch: one double per sample pair in a fixed device array of 65536
+ * entries (512 KB) that every GPU loading the library holds until exit; count
+ * above 65536 is rejected with E_ARG.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture.  Every call on a device
+ * shares the array, so calls that overlap on the GPU race: serialise them
+ * (one stream, or synchronise between calls).  No cudaMalloc, cudaFree or
+ * other allocating routine is called. */
+gnmppi_status gnmppi_softmin_noalloc(const double* C, const double* W, int32_t count, int32_t n,
+                                     int32_t antithetic, double tau, double* mppi, double* stats,
+                                     void* cuda_stream, char* err, int32_t err_len);
+
 /* Number of kernels the library launched on this handle since creation. */
 int64_t gnmppi_launch_count(gnmppi_t h);
 

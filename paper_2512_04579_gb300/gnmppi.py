@@ -23,8 +23,8 @@ JAC_LSQ, JAC_SIGMA, JAC_AUTO = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 
 EXPORTS = ["gnmppi_create", "gnmppi_layout", "gnmppi_solve", "gnmppi_step", "gnmppi_cost", "gnmppi_debug_read",
-           "gnmppi_phase_times", "gnmppi_phase_name", "gnmppi_launch_count", "gnmppi_destroy", "gnmppi_last_error",
-           "gnmppi_status_string", "gnmppi_version"]
+           "gnmppi_phase_times", "gnmppi_phase_name", "gnmppi_softmin_noalloc", "gnmppi_launch_count",
+           "gnmppi_destroy", "gnmppi_last_error", "gnmppi_status_string", "gnmppi_version"]
 
 
 class Problem(C.Structure):
@@ -77,6 +77,9 @@ def load(path: str | None = None):
     L.gnmppi_phase_times.restype = C.c_int32
     L.gnmppi_phase_name.argtypes = [C.c_int32]
     L.gnmppi_phase_name.restype = C.c_char_p
+    L.gnmppi_softmin_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, vp, vp, vp, C.c_char_p,
+                                         C.c_int32]
+    L.gnmppi_softmin_noalloc.restype = C.c_int32
     L.gnmppi_launch_count.argtypes = [vp]
     L.gnmppi_launch_count.restype = C.c_int64
     L.gnmppi_destroy.argtypes = [vp]
@@ -248,6 +251,16 @@ def gnmppi_phase_times(h, iteration: int = 0) -> dict:
 def gnmppi_phase_name(i: int):
     v = load().gnmppi_phase_name(i)
     return v.decode() if v else None
+
+
+def gnmppi_softmin_noalloc(C_dev, W_dev, count: int, n: int, antithetic: bool, tau: float, mppi_dev, stats_dev,
+                           stream=None):
+    """Softmin weights and MPPI mean perturbation of one sample set; device
+    pointers in and out, no device allocation.  Returns (status, error text)."""
+    buf = C.create_string_buffer(256)
+    st = load().gnmppi_softmin_noalloc(_ptr(C_dev), _ptr(W_dev), count, n, int(antithetic), tau, _ptr(mppi_dev),
+                                       _ptr(stats_dev), stream, buf, 256)
+    return int(st), buf.value.decode()
 
 
 def gnmppi_launch_count(h) -> int:
