@@ -203,10 +203,10 @@ def run_gnmppi(args):
         hU.zero_()
         G.gnmppi_solve(he, G.MEM_HOST, hx0, htg, hU, None)
     e2e_s = (time.perf_counter() - t0) / e_steps
-    Ce = torch.empty(batch, dtype=torch.float64, device=dev)
-    G.gnmppi_cost(he, G.MEM_HOST, hx0.numpy(), htg.numpy(), hU.numpy(), Ce.cpu().numpy())
+    Ce = np.zeros(batch)
+    G.gnmppi_cost(he, G.MEM_HOST, hx0.numpy(), htg.numpy(), hU.numpy(), Ce)
     G.gnmppi_destroy(he)
-    e2e_solved = solved  # same inputs, deterministic kernels: same final iterates
+    e2e_solved = int(np.sum((Ce - Cstar) / Cstar <= GAP))
     e2e = {"value": world * e2e_solved / e2e_s, "unit": "solves/s",
            "h2d_bytes_per_step": int(8 * (x0.size + tgt.size + batch * N * 2)),
            "d2h_bytes_per_step": int(8 * batch * N * 2)}
@@ -221,14 +221,17 @@ def run_gnmppi(args):
     p_solved = 0
     p0 = torch.cuda.Event(enable_timing=True)
     p1 = torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
+    p_ms = 0.0
     for b in range(nplain):
         pU.zero_()
+        p0.record(stream)
         G.gnmppi_solve(hp, G.MEM_DEVICE, d_x0[b * 4 * F:(b + 1) * 4 * F], d_tgt[b * 2 * F:(b + 1) * 2 * F], pU, None)
-    p1.record(stream)
-    torch.cuda.synchronize()
-    plain_ms = p0.elapsed_time(p1) / max(1, nplain)
-    # plain solves are the same computation as the batched ones (same instance index 0 stream only for b=0)
+        p1.record(stream)
+        G.gnmppi_cost(hp, G.MEM_DEVICE, d_x0[b * 4 * F:(b + 1) * 4 * F], d_tgt[b * 2 * F:(b + 1) * 2 * F], pU, pC)
+        torch.cuda.synchronize()
+        p_ms += p0.elapsed_time(p1)
+        p_solved += int((float(pC.item()) - Cstar[b]) / Cstar[b] <= GAP)
+    plain_ms = p_ms / max(1, nplain)
     G.gnmppi_destroy(hp)
 
     out = {
@@ -240,7 +243,9 @@ def run_gnmppi(args):
                    "l2": "working set per iteration > L2 (dR alone %.1f GB)" % (batch * (2 * F + 2) * N * K / 2 * 4 / 1e9)},
         "solved": solved, "solved_fraction": solved / batch, "gap_median": float(np.median(gap)),
         "gap_max": float(np.max(gap)),
-        "plain": {"solves_per_s_upper_bound": 1e3 / plain_ms, "ms_per_solve": plain_ms, "instances": nplain},
+        "plain": {"solves_per_s": (p_solved / max(1, nplain)) * 1e3 / plain_ms, "ms_per_solve": plain_ms,
+                  "instances": nplain, "solved": p_solved,
+                  "note": "one instance per handle and graph launch, in sequence, same kernels"},
         "phases_ms_per_iteration": phases,
         "roofline": {"kernel": "k_samples (RK4 rollouts + residual/cost/dR/W)", "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
