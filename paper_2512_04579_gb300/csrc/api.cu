@@ -330,9 +330,10 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     g.insts.push_back(b);
     const int per = anti ? kPairsPerBlock : kSamplesPerBlock;
     for (int c = 0; c < (d.Kp + per - 1) / per; ++c) g.bmap.push_back(make_int2(b, c));
-    g.smem = std::max(g.smem, (int)(2 * h->szT * d.n));
+    g.smem = std::max(g.smem, (int)(h->szT * (2 * d.n + d.nR + d.nref)));
   }
   for (auto& g : h->groups) {
+    CK(g.fn.prepare(g.smem));
     AL(g.d_list, 4 * g.insts.size());
     AL(g.d_bmap, sizeof(int2) * g.bmap.size());
     CK(cudaMemcpyAsync(g.d_list, g.insts.data(), 4 * g.insts.size(), cudaMemcpyHostToDevice, h->stream));

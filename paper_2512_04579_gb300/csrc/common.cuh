@@ -203,7 +203,7 @@ template <typename T, int F>
 struct Chain {
   static constexpr int NX = 4 * F, NU = 2, RPS = 2 * F + 2, RT = 2 * F;
   T mass_inv, k, k3, c, g, l0, h, h2, h6;
-  const double* pref;  // target positions p* (2F)
+  const T* pref;  // target positions p* (2F), staged by the kernel
   __device__ Chain(const Consts& cs) {
     mass_inv = (T)(1.0 / cs.params[0]);
     k = (T)cs.params[1];
@@ -216,65 +216,96 @@ struct Chain {
     h6 = (T)(cs.dt / 6.0);
     pref = nullptr;
   }
-  // d = f(s, u): positions' rate is the velocity; link i (masses i-1, i) pulls
-  // with tension k d + k3 d^3 along its direction; damping -c v; force u on
-  // the last mass; gravity -g along y.
-  __device__ __forceinline__ void f(const T* s, const T* u, T* d) const {
+  // Accelerations at state s: link i (masses i-1, i) pulls with tension
+  // k d + k3 d^3 along its direction; damping -c v; force u on the last mass;
+  // gravity -g along y.  FP32 uses one rsqrt per link; FP64 keeps sqrt and a
+  // division.
+  __device__ __forceinline__ void accel(const T* s, const T* u, T* acc) const {
+    const T* v = s + 2 * F;
 #pragma unroll
-    for (int i = 0; i < 2 * F; ++i) {
-      d[i] = s[2 * F + i];
-      d[2 * F + i] = -c * s[2 * F + i];
-    }
+    for (int i = 0; i < 2 * F; ++i) acc[i] = -c * v[i];
 #pragma unroll
     for (int i = 1; i <= F; ++i) {
       const T px0 = (i == 1) ? (T)0 : s[2 * (i - 2)];
       const T py0 = (i == 1) ? (T)0 : s[2 * (i - 2) + 1];
       const T dx = s[2 * (i - 1)] - px0;
       const T dy = s[2 * (i - 1) + 1] - py0;
-      const T len = sqrt(dx * dx + dy * dy);
-      const T dd = len - l0;
-      const T fm = k * dd + k3 * dd * dd * dd;
-      const T fx = fm * dx / len, fy = fm * dy / len;
-      d[2 * F + 2 * (i - 1)] -= fx;
-      d[2 * F + 2 * (i - 1) + 1] -= fy;
+      const T q = dx * dx + dy * dy;
+      T fx, fy;
+      if constexpr (sizeof(T) == 4) {
+        const T rinv = rsqrtf(q);
+        const T dd = q * rinv - l0;
+        const T fr = (k * dd + k3 * dd * dd * dd) * rinv;
+        fx = fr * dx;
+        fy = fr * dy;
+      } else {
+        const T len = sqrt(q);
+        const T dd = len - l0;
+        const T fm = k * dd + k3 * dd * dd * dd;
+        fx = fm * dx / len;
+        fy = fm * dy / len;
+      }
+      acc[2 * (i - 1)] -= fx;
+      acc[2 * (i - 1) + 1] -= fy;
       if (i >= 2) {
-        d[2 * F + 2 * (i - 2)] += fx;
-        d[2 * F + 2 * (i - 2) + 1] += fy;
+        acc[2 * (i - 2)] += fx;
+        acc[2 * (i - 2) + 1] += fy;
       }
     }
-    d[2 * F + 2 * (F - 1)] += u[0];
-    d[2 * F + 2 * (F - 1) + 1] += u[1];
+    acc[2 * (F - 1)] += u[0];
+    acc[2 * (F - 1) + 1] += u[1];
 #pragma unroll
-    for (int i = 0; i < 2 * F; ++i) d[2 * F + i] = d[2 * F + i] * mass_inv;
+    for (int i = 0; i < 2 * F; ++i) acc[i] = acc[i] * mass_inv;
 #pragma unroll
-    for (int i = 0; i < F; ++i) d[2 * F + 2 * i + 1] -= g;
+    for (int i = 0; i < F; ++i) acc[2 * i + 1] -= g;
   }
+  // Classical RK4; the position rates are the stage velocities, so only the
+  // 2F accelerations are materialised per stage.
   __device__ __forceinline__ void step(T* x, const T* u) const {
-    T kk[NX], t[NX], a[NX];
-    f(x, u, kk);
+    constexpr int H = 2 * F;
+    T a[NX], t[NX], acc[H];
+    accel(x, u, acc);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { a[i] = kk[i]; t[i] = x[i] + h2 * kk[i]; }
-    f(t, u, kk);
+    for (int i = 0; i < H; ++i) {
+      a[i] = x[H + i];
+      a[H + i] = acc[i];
+      t[i] = x[i] + h2 * x[H + i];
+      t[H + i] = x[H + i] + h2 * acc[i];
+    }
+    accel(t, u, acc);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { a[i] = a[i] + (T)2 * kk[i]; t[i] = x[i] + h2 * kk[i]; }
-    f(t, u, kk);
+    for (int i = 0; i < H; ++i) {
+      a[i] = a[i] + (T)2 * t[H + i];
+      a[H + i] = a[H + i] + (T)2 * acc[i];
+      t[i] = x[i] + h2 * t[H + i];
+      t[H + i] = x[H + i] + h2 * acc[i];
+    }
+    accel(t, u, acc);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { a[i] = a[i] + (T)2 * kk[i]; t[i] = x[i] + h * kk[i]; }
-    f(t, u, kk);
+    for (int i = 0; i < H; ++i) {
+      a[i] = a[i] + (T)2 * t[H + i];
+      a[H + i] = a[H + i] + (T)2 * acc[i];
+      t[i] = x[i] + h * t[H + i];
+      t[H + i] = x[H + i] + h * acc[i];
+    }
+    accel(t, u, acc);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) x[i] = x[i] + h6 * (a[i] + kk[i]);
+    for (int i = 0; i < H; ++i) {
+      x[i] = x[i] + h6 * (a[i] + t[H + i]);
+      x[H + i] = x[H + i] + h6 * (a[H + i] + acc[i]);
+    }
   }
   template <class E>
   __device__ __forceinline__ void stage(const T* x, const T* u, E& emit) const {
 #pragma unroll
-    for (int i = 0; i < 2 * F; ++i) emit(i, x[i] - (T)pref[i]);
+    for (int i = 0; i < 2 * F; ++i) emit(i, x[i] - pref[i]);
     emit(2 * F, (T)0.1 * u[0]);
     emit(2 * F + 1, (T)0.1 * u[1]);
   }
   template <class E>
   __device__ __forceinline__ void terminal(const T* x, E& emit) const {
 #pragma unroll
-    for (int i = 0; i < 2 * F; ++i) emit(i, x[i] - (T)pref[i]);
+    for (int i = 0; i < 2 * F; ++i) emit(i, x[i] - pref[i]);
   }
 };
 

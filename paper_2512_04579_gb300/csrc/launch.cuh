@@ -6,6 +6,7 @@
 namespace gnm {
 
 struct Launchers {
+  cudaError_t (*prepare)(int smem);  // opt the sample kernel into `smem` bytes of shared memory
   void (*samples)(const RollArgs&, int nblocks, int smem, cudaStream_t);
   void (*line)(const RollArgs&, int nthreads, cudaStream_t);
   void (*cost64)(const RollArgs&, int nthreads, cudaStream_t);
@@ -23,6 +24,12 @@ void launch_samples(const RollArgs& a, int nb, int smem, cudaStream_t s) {
   else
     k_samples<Model, T, S, false><<<nb, 128, smem, s>>>(a);
 }
+template <class Model, typename T, typename S>
+cudaError_t prepare_samples(int smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_samples<Model, T, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_samples<Model, T, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
 template <class Model, typename T>
 void launch_line(const RollArgs& a, int nthreads, cudaStream_t s) {
   if (nthreads > 0) k_line<Model, T><<<(nthreads + 127) / 128, 128, 0, s>>>(a);
@@ -30,6 +37,7 @@ void launch_line(const RollArgs& a, int nthreads, cudaStream_t s) {
 
 template <class M32, class M64, typename T, typename S>
 void fill(Launchers* o) {
+  o->prepare = &prepare_samples<M32, T, S>;
   o->samples = &launch_samples<M32, T, S>;
   o->line = &launch_line<M32, T>;
   o->cost64 = &launch_line<M64, double>;

@@ -41,11 +41,21 @@ struct RollArgs {
   int mode;           // k_line: 0 line search, 1 nominal, 2 FP64 cost only
 };
 
+// Models that read a per-instance reference (the chain's target positions)
+// get it from a caller-staged copy in the scalar type.
 template <class Model>
-__device__ __forceinline__ void bind_model(Model&, const RollArgs&, const InstDesc&) {}
+struct RefSize {
+  static constexpr int value = 0;
+};
 template <typename T, int F>
-__device__ __forceinline__ void bind_model(Chain<T, F>& m, const RollArgs& a, const InstDesc& I) {
-  m.pref = a.xref + I.o_xref;
+struct RefSize<Chain<T, F>> {
+  static constexpr int value = 2 * F;
+};
+template <class Model, typename T>
+__device__ __forceinline__ void bind_model(Model&, const T*) {}
+template <typename T, int F>
+__device__ __forceinline__ void bind_model(Chain<T, F>& m, const T* ref) {
+  m.pref = ref;
 }
 
 template <typename T>
@@ -88,13 +98,19 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
   const int2 bm = a.bmap[blockIdx.x];
   const InstDesc I = a.inst[bm.x];
   if (a.st[bm.x].status != 0) return;
+  // shared: U, s (n each), the nominal residual r (nR) and the reference, in T
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sU = reinterpret_cast<T*>(smem_raw);
   T* sS = sU + I.n;
+  T* sR = sS + I.n;
+  T* sRef = sR + I.nR;
+  const T* rg = reinterpret_cast<const T*>(a.r) + I.o_R;
   for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
     sU[j] = (T)a.U[I.o_U + j];
     sS[j] = (T)a.s[I.o_U + j];
   }
+  for (int j = threadIdx.x; j < I.nR; j += blockDim.x) sR[j] = rg[j];
+  for (int j = threadIdx.x; j < RefSize<Model>::value; j += blockDim.x) sRef[j] = (T)a.xref[I.o_xref + j];
   __syncthreads();
 
   const int per_block = ANTI ? kPairsPerBlock : kSamplesPerBlock;
@@ -105,14 +121,14 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
   const T sign = par ? (T)-1 : (T)1;
 
   Model md(a.cs);
-  bind_model(md, a, I);
+  bind_model(md, (const T*)sRef);
   T x[NX];
 #pragma unroll
   for (int i = 0; i < NX; ++i) x[i] = (T)a.x0[I.o_x0 + i];
 
   S* dR = reinterpret_cast<S*>(a.dR) + I.o_dR;
   S* Wm = reinterpret_cast<S*>(a.W) + I.o_W;
-  const T* r = reinterpret_cast<const T*>(a.r) + I.o_R;
+  const T* r = sR;
   Acc<T> cost, eacc;
   SampleEmit<T, S, ANTI> em{dR, r, I.ldK, m, 0, par, active, sign, (T)0, &eacc};
   const uint32_t mm = active ? (uint32_t)m : 0u;
@@ -192,7 +208,10 @@ __global__ void __launch_bounds__(128) k_line(RollArgs a) {
     for (int q = 0; q < j; ++q) alpha *= a.cs.gamma;
   }
   Model md(a.cs);
-  bind_model(md, a, I);
+  T ref[RefSize<Model>::value > 0 ? RefSize<Model>::value : 1];
+#pragma unroll
+  for (int i = 0; i < RefSize<Model>::value; ++i) ref[i] = (T)a.xref[I.o_xref + i];
+  bind_model(md, (const T*)ref);
   T x[NX];
 #pragma unroll
   for (int i = 0; i < NX; ++i) x[i] = (T)a.x0[I.o_x0 + i];
