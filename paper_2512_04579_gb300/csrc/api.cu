@@ -378,7 +378,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   // tensor-core contraction (TF32 on FP32 operands, or BF16)
   h->use_tc = prec != kFP64;
   if (h->use_tc) {
-    st = tc_plan_create(h->desc, h->d_dR, prec == kBF16 ? 1 : 0, h->stream, &h->tc, h->err);
+    st = tc_plan_create(h->desc, h->d_dR, h->d_P, prec == kBF16 ? 1 : 0, h->stream, &h->tc, h->err);
     for (void* q : h->tc.allocs) h->allocs.push_back(q);
     if (st != GNMPPI_OK) return st;
   }
@@ -535,7 +535,7 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
   MARK(2);
   GemmArgs ga{h->d_desc, h->d_st, nullptr, h->d_dR, h->d_W, h->d_P, h->d_A, h->d_S2};
   if (h->use_tc) {
-    CK(tc_contract_launch(h->tc, h->d_desc, h->d_st, reinterpret_cast<float*>(h->d_P), h->stream));
+    CK(tc_contract_launch(h->tc, h->d_st, reinterpret_cast<float*>(h->d_P), h->stream));
     h->launches++;
   } else {
     ga.tiles = h->d_tiles[0];
@@ -544,10 +544,15 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
     h->launches++;
   }
   MARK(3);
-  ga.tiles = h->d_tiles[1];
-  k_gemm_nt<kGram, TA, TC, double><<<h->ntiles[1], 256, 0, h->stream>>>(ga);
-  CKL();
-  h->launches++;
+  if (h->use_tc) {
+    CK(tc_gram_launch(h->tc, h->d_desc, h->d_st, reinterpret_cast<const float*>(h->d_P), h->d_A, h->stream));
+    h->launches += 2;
+  } else {
+    ga.tiles = h->d_tiles[1];
+    k_gemm_nt<kGram, TA, TC, double><<<h->ntiles[1], 256, 0, h->stream>>>(ga);
+    CKL();
+    h->launches++;
+  }
   MARK(4);
   if (h->ntiles[2] > 0) {
     ga.tiles = h->d_tiles[2];

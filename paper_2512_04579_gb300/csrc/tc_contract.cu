@@ -1,5 +1,6 @@
-// tc_contract.cu -- Jacobian-reconstruction contraction on the sm_103a tensor
-// cores.  For every instance: D = W^T [dR | W]^T-rows, i.e.
+// tc_contract.cu -- batched NT GEMMs on the sm_103a tensor cores:
+//  (1) the Jacobian-reconstruction contraction; for every instance
+//      D = W^T [dR | W]^T-rows, i.e.
 //   P^T[i][j] = sum_m W_m[i] dR_m[j]   (P = sum_m dR_m W_m^T, Eq. 7 of arXiv 2512.04579)
 //   S[i][k]   = sum_m W_m[i] W_m[k]
 // with the sample index m as the reduction dimension.  dR and W of an instance
@@ -10,6 +11,10 @@
 //   warp 1 lane 0  issues tcgen05.mma (M=128, N=256, K=16 BF16 / K=8 TF32)
 //                  into a 256-column TMEM accumulator,
 //   warps 0-3      read TMEM back (tcgen05.ld 32x32b) and store FP32 rows.
+//  (2) the Gram product A = P^T P of Eq. 9 in FP32-level accuracy from three
+//      TF32 passes, A ~ Ph Ph^T + Ph Pl^T + Pl Ph^T with P^T = Ph + Pl split into
+//      a TF32 head and its FP32 remainder (k_split_tf32 writes [Ph; Pl] rows).
+// Both use the same kernel, driven by per-instance job descriptors.
 // Every mbarrier wait is bounded by the global timer; a wait that runs out
 // sets the plan's error word and the CTA winds down without a trap.
 #include <cudaTypedefs.h>
@@ -22,11 +27,11 @@ namespace gnm {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, STAGES = 4;
+constexpr int BM = 128, BN = 256;
 constexpr int ROW_BYTES = 128;  // one k-block of a row: 64 BF16 or 32 FP32 values
 constexpr int A_BYTES = BM * ROW_BYTES;
 constexpr int B_BYTES = BN * ROW_BYTES;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int RING_BYTES = 4 * (A_BYTES + B_BYTES);  // 192 KB of operand ring
 constexpr int TMEM_COLS = 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
 
@@ -135,21 +140,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <bool BF16>
-__global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __restrict__ maps,
-                                                        const InstDesc* __restrict__ inst,
-                                                        const InstState* __restrict__ st,
-                                                        const int4* __restrict__ tiles, float* __restrict__ P,
-                                                        int* __restrict__ err) {
+// D[i][j] = sum_k A[i][k] B[j][k] for one 128 x 256 tile of one job.  SPLIT3:
+// A and B each have a head block and a remainder block lo_off rows below, and
+// the tile accumulates head*head + head*rem + rem*head.
+template <bool BF16, bool SPLIT3, typename TOut>
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
+                                                    const InstState* __restrict__ st, const int4* __restrict__ tiles,
+                                                    TOut* __restrict__ D, int* __restrict__ err) {
   constexpr int KBLK = BF16 ? 64 : 32;   // elements per k-block
   constexpr int KSTEP = BF16 ? 16 : 8;   // elements per MMA
-  constexpr int NSUB = KBLK / KSTEP;     // MMAs per k-block (4)
+  constexpr int NSUB = KBLK / KSTEP;     // MMAs per k-block and operand pair (4)
+  constexpr int PARTS = SPLIT3 ? 2 : 1;  // head (+ remainder) blocks per operand
+  constexpr int STAGE_BYTES = PARTS * (A_BYTES + B_BYTES);
+  constexpr int STAGES = RING_BYTES / STAGE_BYTES;
   const int4 tl = tiles[blockIdx.x];
-  const int b = tl.x;
-  if (st[b].status != 0) return;  // uniform over the CTA, before any allocation
-  const InstDesc I = inst[b];
-  const int nkb = I.ldK / KBLK;
-  const CUtensorMap* map = maps + b;
+  const TcJob J = jobs[tl.x];
+  if (st[J.inst].status != 0) return;  // uniform over the CTA, before any allocation
+  const int nkb = J.nkb;
+  const CUtensorMap* map = maps + J.map;
 
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
@@ -190,11 +198,15 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
       const uint32_t full = su32(bars + s);
       mbar_expect_tx(full, STAGE_BYTES);
       const uint32_t a_dst = su32(base + s * STAGE_BYTES);
-      const uint32_t b_dst = a_dst + A_BYTES;
+      const uint32_t b_dst = a_dst + PARTS * A_BYTES;
       const int x = kb * KBLK;
-      tma_load(a_dst, map, full, x, I.nR + tl.y * BM);
-      tma_load(b_dst, map, full, x, tl.z * BN);
-      tma_load(b_dst + BM * ROW_BYTES, map, full, x, tl.z * BN + BM);
+#pragma unroll
+      for (int p = 0; p < PARTS; ++p) {
+        const int off = p * J.lo_off;
+        tma_load(a_dst + p * A_BYTES, map, full, x, J.a_row0 + off + tl.y * BM);
+        tma_load(b_dst + p * B_BYTES, map, full, x, J.b_row0 + off + tl.z * BN);
+        tma_load(b_dst + p * B_BYTES + BM * ROW_BYTES, map, full, x, J.b_row0 + off + tl.z * BN + BM);
+      }
       ++issued;
     }
     // every copy this thread issued has landed before the CTA may exit
@@ -212,33 +224,37 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
       }
       tc_fence_after();
       const uint32_t a0 = su32(base + s * STAGE_BYTES);
-      const uint32_t b0 = a0 + A_BYTES;
+      const uint32_t b0 = a0 + PARTS * A_BYTES;
 #pragma unroll
-      for (int k = 0; k < NSUB; ++k)
+      for (int k = 0; k < NSUB; ++k) {
         mma<BF16>(tmem, sdesc(a0 + k * 32), sdesc(b0 + k * 32), id, (kb > 0 || k > 0) ? 1u : 0u);
+        if (SPLIT3) {
+          mma<BF16>(tmem, sdesc(a0 + k * 32), sdesc(b0 + B_BYTES + k * 32), id, 1u);
+          mma<BF16>(tmem, sdesc(a0 + A_BYTES + k * 32), sdesc(b0 + k * 32), id, 1u);
+        }
+      }
       mma_commit(su32(bars + STAGES + s));  // frees the stage once these MMAs have read it
     }
     mma_commit(done);  // accumulator complete (or every issued MMA retired, on abort)
   }
   __syncwarp();
 
-  // ---------------- epilogue: TMEM -> registers -> global (rows of P^T | S)
+  // ---------------- epilogue: TMEM -> registers -> global rows of D
   const bool ok = mbar_wait(done, 0, abort, false);
   tc_fence_after();
   // tcgen05.ld is warp-collective: the whole warp takes the same branch
   if (__all_sync(0xffffffffu, ok && !*abort)) {
     const int row = tl.y * BM + warp * 32 + lane;
-    const int ncols = I.nR + I.n;
-    float* out = P + I.o_P + (int64_t)row * I.ldP;
+    TOut* out = D + J.out_off + (int64_t)row * J.ldc;
 #pragma unroll 1
     for (int c = 0; c < BN / 32; ++c) {
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
       const int col0 = tl.z * BN + c * 32;
-      if (row < I.n) {
+      if (row < J.M) {
 #pragma unroll
         for (int q = 0; q < 32; ++q)
-          if (col0 + q < ncols) out[col0 + q] = __uint_as_float(v[q]);
+          if (col0 + q < J.Nc) out[col0 + q] = (TOut)__uint_as_float(v[q]);
       }
     }
   } else if (threadIdx.x == 0) {
@@ -252,84 +268,198 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
   }
 }
 
+// [Ph; Pl] rows of the Gram operand: Ph = P^T rounded to TF32 (cvt.rna),
+// Pl = P^T - Ph (exact in FP32).  One CTA row-block per instance row.
+__global__ void __launch_bounds__(256) k_split_tf32(const InstDesc* __restrict__ inst, const InstState* __restrict__ st,
+                                                    const int2* __restrict__ rows, const float* __restrict__ P,
+                                                    float* __restrict__ G, const int64_t* __restrict__ g_off,
+                                                    const int* __restrict__ g_ld) {
+  const int2 rb = rows[blockIdx.x];  // (instance, row)
+  if (st[rb.x].status != 0) return;
+  const InstDesc I = inst[rb.x];
+  const float* src = P + I.o_P + (int64_t)rb.y * I.ldP;
+  float* hi = G + g_off[rb.x] + (int64_t)rb.y * g_ld[rb.x];
+  float* lo = hi + (int64_t)I.n * g_ld[rb.x];
+  for (int k = threadIdx.x; k < I.nR; k += blockDim.x) {
+    const float x = src[k];
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const float hf = __uint_as_float(h);
+    hi[k] = hf;
+    lo[k] = x - hf;
+  }
+}
+
 }  // namespace
 
-gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, int bf16, cudaStream_t stream,
-                             TcPlan* plan, std::string& err) {
-  plan->bf16 = bf16;
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode(std::string& err) {
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q{};
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
       q != cudaDriverEntryPointSuccess || !fn) {
     err = "cuTensorMapEncodeTiled is not available";
-    return GNMPPI_E_CUDA;
+    return nullptr;
   }
-  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+}
+
+// Rank-2 tensor map over rows of `cols` elements (row stride ld elements),
+// box = one 128-byte k-block x 128 rows, 128-byte swizzle, zero fill outside.
+static bool encode_rows(PFN_cuTensorMapEncodeTiled_v12000 encode, CUtensorMap* m, void* gaddr, bool bf16, int64_t cols,
+                        int64_t ld, int64_t rows) {
+  const size_t esz = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / esz), (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  return encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, gaddr, dims, strides,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename P>
+static bool plan_alloc(TcPlan* plan, P** p, size_t bytes) {
+  if (cudaMalloc((void**)p, bytes) != cudaSuccess) return false;
+  plan->allocs.push_back((void*)*p);
+  return true;
+}
+
+gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void* P, int bf16, cudaStream_t stream,
+                             TcPlan* plan, std::string& err) {
+  plan->bf16 = bf16;
+  auto encode = get_encode(err);
+  if (!encode) return GNMPPI_E_CUDA;
   const size_t esz = bf16 ? 2 : 4;
   const int kblk = bf16 ? 64 : 32;
-  std::vector<CUtensorMap> maps(desc.size());
-  std::vector<int4> tiles;
-  for (size_t b = 0; b < desc.size(); ++b) {
+  const int nb = (int)desc.size();
+  // Gram operand blocks [Ph; Pl], rows of ldG = nR rounded to 32 floats
+  std::vector<int64_t> g_off(nb);
+  std::vector<int> g_ld(nb);
+  int64_t g_total = 0;
+  for (int b = 0; b < nb; ++b) {
+    g_ld[b] = (int)((desc[b].nR + 31) / 32 * 32);
+    g_off[b] = g_total;
+    g_total += 2 * (int64_t)desc[b].n * g_ld[b];
+  }
+  if (!plan_alloc(plan, &plan->d_G, 4 * (size_t)std::max<int64_t>(g_total, 4))) {
+    err = "cudaMalloc failed for the Gram operands";
+    return GNMPPI_E_NOMEM;
+  }
+  std::vector<CUtensorMap> maps(2 * (size_t)nb);
+  std::vector<TcJob> jobs(2 * (size_t)nb);
+  std::vector<int4> tc, tg;
+  std::vector<int2> rows;
+  for (int b = 0; b < nb; ++b) {
     const InstDesc& d = desc[b];
     if (d.ldK % kblk != 0) {
       err = "sample padding is not a multiple of the k-block";
       return GNMPPI_E_ARG;
     }
-    char* gaddr = reinterpret_cast<char*>(dRW) + esz * (size_t)d.o_dR;
-    cuuint64_t dims[2] = {(cuuint64_t)d.ldK, (cuuint64_t)(d.nR + d.n)};
-    cuuint64_t strides[1] = {(cuuint64_t)d.ldK * esz};
-    cuuint32_t box[2] = {(cuuint32_t)kblk, (cuuint32_t)BM};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(&maps[b], bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, gaddr,
-                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-      err = "cuTensorMapEncodeTiled failed for instance " + std::to_string(b) + " (code " + std::to_string((int)r) + ")";
+    // contraction: one map over the instance's [dR; W] block
+    if (!encode_rows(encode, &maps[b], reinterpret_cast<char*>(dRW) + esz * (size_t)d.o_dR, bf16, d.ldK, d.ldK,
+                     d.nR + d.n)) {
+      err = "cuTensorMapEncodeTiled failed (contraction, instance " + std::to_string(b) + ")";
       return GNMPPI_E_CUDA;
     }
+    TcJob& jc = jobs[b];
+    jc.inst = b;
+    jc.map = b;
+    jc.a_row0 = d.nR;
+    jc.b_row0 = 0;
+    jc.lo_off = 0;
+    jc.M = d.n;
+    jc.Nc = d.nR + d.n;
+    jc.nkb = d.ldK / kblk;
+    jc.out_off = d.o_P;
+    jc.ldc = d.ldP;
     for (int i = 0; i < (d.n + BM - 1) / BM; ++i)
-      for (int j = 0; j < (d.nR + d.n + BN - 1) / BN; ++j) tiles.push_back(make_int4((int)b, i, j, 0));
+      for (int j = 0; j < (d.nR + d.n + BN - 1) / BN; ++j) tc.push_back(make_int4(b, i, j, 0));
+    // Gram: one FP32 map over [Ph; Pl] (2n rows, nR columns)
+    if (!encode_rows(encode, &maps[nb + b], plan->d_G + g_off[b], false, d.nR, g_ld[b], 2 * (int64_t)d.n)) {
+      err = "cuTensorMapEncodeTiled failed (Gram, instance " + std::to_string(b) + ")";
+      return GNMPPI_E_CUDA;
+    }
+    TcJob& jg = jobs[nb + b];
+    jg.inst = b;
+    jg.map = nb + b;
+    jg.a_row0 = 0;
+    jg.b_row0 = 0;
+    jg.lo_off = d.n;
+    jg.M = d.n;
+    jg.Nc = d.n;
+    jg.nkb = (d.nR + 31) / 32;
+    jg.out_off = d.o_nn;
+    jg.ldc = d.n;
+    for (int i = 0; i < (d.n + BM - 1) / BM; ++i)
+      for (int j = 0; j < (d.n + BN - 1) / BN; ++j) tg.push_back(make_int4(nb + b, i, j, 0));
+    for (int r = 0; r < d.n; ++r) rows.push_back(make_int2(b, r));
   }
-  auto alloc = [&](void** p, size_t bytes) -> bool {
-    if (cudaMalloc(p, bytes) != cudaSuccess) return false;
-    plan->allocs.push_back(*p);
-    return true;
-  };
-  if (!alloc((void**)&plan->d_maps, sizeof(CUtensorMap) * maps.size()) ||
-      !alloc((void**)&plan->d_tiles, sizeof(int4) * std::max<size_t>(1, tiles.size())) ||
-      !alloc((void**)&plan->d_err, sizeof(int))) {
+  if (!plan_alloc(plan, &plan->d_maps, sizeof(CUtensorMap) * maps.size()) ||
+      !plan_alloc(plan, &plan->d_jobs, sizeof(TcJob) * jobs.size()) ||
+      !plan_alloc(plan, &plan->d_tiles_c, sizeof(int4) * std::max<size_t>(1, tc.size())) ||
+      !plan_alloc(plan, &plan->d_tiles_g, sizeof(int4) * std::max<size_t>(1, tg.size())) ||
+      !plan_alloc(plan, &plan->d_rows, sizeof(int2) * std::max<size_t>(1, rows.size())) ||
+      !plan_alloc(plan, &plan->d_goff, sizeof(int64_t) * (size_t)nb) ||
+      !plan_alloc(plan, &plan->d_gld, sizeof(int) * (size_t)nb) || !plan_alloc(plan, &plan->d_err, sizeof(int))) {
     err = "cudaMalloc failed for the tensor-core plan";
     return GNMPPI_E_NOMEM;
   }
-  plan->ntiles = (int)tiles.size();
-  if (cudaMemcpyAsync(plan->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, stream) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(plan->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, stream) !=
-          cudaSuccess ||
-      cudaMemsetAsync(plan->d_err, 0, sizeof(int), stream) != cudaSuccess) {
+  plan->ntiles_c = (int)tc.size();
+  plan->ntiles_g = (int)tg.size();
+  plan->nrows = (int)rows.size();
+  bool ok = cudaMemcpyAsync(plan->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                            stream) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(plan->d_jobs, jobs.data(), sizeof(TcJob) * jobs.size(), cudaMemcpyHostToDevice, stream) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpyAsync(plan->d_tiles_c, tc.data(), sizeof(int4) * tc.size(), cudaMemcpyHostToDevice, stream) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpyAsync(plan->d_tiles_g, tg.data(), sizeof(int4) * tg.size(), cudaMemcpyHostToDevice, stream) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpyAsync(plan->d_rows, rows.data(), sizeof(int2) * rows.size(), cudaMemcpyHostToDevice, stream) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpyAsync(plan->d_goff, g_off.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, stream) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpyAsync(plan->d_gld, g_ld.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, stream) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(plan->d_G, 0, 4 * (size_t)std::max<int64_t>(g_total, 4), stream) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(plan->d_err, 0, sizeof(int), stream) == cudaSuccess;
+  if (!ok) {
     err = "copying the tensor-core plan failed";
     return GNMPPI_E_CUDA;
   }
-  plan->smem = STAGES * STAGE_BYTES + 1024 + 256;
-  cudaError_t e = bf16 ? cudaFuncSetAttribute(k_contract_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              plan->smem)
-                       : cudaFuncSetAttribute(k_contract_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              plan->smem);
+  plan->smem = RING_BYTES + 1024 + 256;
+  cudaError_t e = bf16 ? cudaFuncSetAttribute(k_gemm_tc<true, false, float>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem)
+                       : cudaFuncSetAttribute(k_gemm_tc<false, false, float>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gemm_tc<false, true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
   if (e != cudaSuccess) {
     err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
     return GNMPPI_E_CUDA;
   }
+  (void)P;
   return GNMPPI_OK;
 }
 
-cudaError_t tc_contract_launch(const TcPlan& plan, const InstDesc* d_desc, const InstState* d_st, float* P,
-                               cudaStream_t stream) {
-  if (plan.ntiles == 0) return cudaSuccess;
+cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float* P, cudaStream_t stream) {
+  if (plan.ntiles_c == 0) return cudaSuccess;
   if (plan.bf16)
-    k_contract_tc<true><<<plan.ntiles, 128, plan.smem, stream>>>(plan.d_maps, d_desc, d_st, plan.d_tiles, P, plan.d_err);
+    k_gemm_tc<true, false, float><<<plan.ntiles_c, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
+                                                                             plan.d_tiles_c, P, plan.d_err);
   else
-    k_contract_tc<false><<<plan.ntiles, 128, plan.smem, stream>>>(plan.d_maps, d_desc, d_st, plan.d_tiles, P,
-                                                                 plan.d_err);
+    k_gemm_tc<false, false, float><<<plan.ntiles_c, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
+                                                                              plan.d_tiles_c, P, plan.d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gram_launch(const TcPlan& plan, const InstDesc* d_desc, const InstState* d_st, const float* P, double* A,
+                           cudaStream_t stream) {
+  if (plan.ntiles_g == 0) return cudaSuccess;
+  k_split_tf32<<<plan.nrows, 256, 0, stream>>>(d_desc, d_st, plan.d_rows, P, plan.d_G, plan.d_goff, plan.d_gld);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_gemm_tc<false, true, double><<<plan.ntiles_g, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
+                                                                            plan.d_tiles_g, A, plan.d_err);
   return cudaGetLastError();
 }
 

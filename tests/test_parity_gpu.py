@@ -302,6 +302,10 @@ def test_tensor_core_contraction_matches_oracle(prec, tol):
     s = G.Solver(gp, 1)
     s.step(x0[0], tgt[0], np.zeros(m.n), np.full(m.n, 0.2), 0)
     PS = s.debug("PS").reshape(m.n, m.nR + m.n)
+    A = s.debug("A").reshape(m.n, m.n)
     s.close()
     assert rel(PS[:, : m.nR], P.T) < tol
     assert rel(PS[:, m.nR:], S) < tol
+    # Gram A = P^T P on the tensor cores (three TF32 passes): its error is that of P
+    assert rel(A, P.T @ P) < 2 * tol
+    assert np.allclose(A, A.T, rtol=1e-5, atol=1e-5 * np.abs(A).max())
