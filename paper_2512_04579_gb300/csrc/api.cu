@@ -243,7 +243,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     d.o_RL = orl; orl += (int64_t)p.L * d.nR;
     h->desc[b] = d;
   }
-  // k_solve keeps rhs, x, res (3 n_max doubles) and, when it fits, the packed
+  // k_solve keeps rhs, x, res, 1/diag (4 n_max doubles) and, when it fits, the packed
   // Cholesky factor (n(n+1)/2 doubles) in shared memory; larger factors live
   // in a global scratch.
   int n_all_max = 0;
@@ -256,7 +256,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   else CK(cudaFuncGetAttributes(&fa, k_solve<float>));
   const int64_t solve_budget = (int64_t)optin - (int64_t)fa.sharedSizeBytes - 256;
   int nmax_smem = 0;
-  while (8 * ((int64_t)3 * n_all_max + (int64_t)(nmax_smem + 1) * (nmax_smem + 2) / 2) <= solve_budget) ++nmax_smem;
+  while (8 * ((int64_t)4 * n_all_max + (int64_t)(nmax_smem + 1) * (nmax_smem + 2) / 2) <= solve_budget) ++nmax_smem;
   h->smem_n_max = nmax_smem;
   int n_solve_max = 0;
   for (int b = 0; b < h->batch; ++b) {
@@ -268,7 +268,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
       n_solve_max = std::max(n_solve_max, d.n);
     }
   }
-  h->solve_smem = (int)(8 * ((int64_t)3 * n_all_max + (int64_t)n_solve_max * (n_solve_max + 1) / 2));
+  h->solve_smem = (int)(8 * ((int64_t)4 * n_all_max + (int64_t)n_solve_max * (n_solve_max + 1) / 2));
   h->n_x0 = oX; h->n_xref = oR; h->n_U = oU; h->n_dR = odR; h->n_W = oW; h->n_C = oC; h->n_P = oP;
   h->n_nn = onn; h->n_R = orr; h->n_RL = orl; h->n_L = oL;
 
@@ -383,7 +383,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     if (st != GNMPPI_OK) return st;
   }
   // the Cholesky kernel keeps its factor in up to the opt-in shared-memory limit
-  if (8 * (int64_t)3 * n_all_max > solve_budget) return fail(h, GNMPPI_E_ARG, "N*nu too large for the solver");
+  if (8 * (int64_t)4 * n_all_max > solve_budget) return fail(h, GNMPPI_E_ARG, "N*nu too large for the solver");
   if (prec == kFP64) {
     CK(cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
   } else {

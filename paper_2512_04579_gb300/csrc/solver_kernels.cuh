@@ -258,23 +258,163 @@ __global__ void __launch_bounds__(256) k_gemm_nt(GemmArgs g) {
 // ----------------------------------------------------------- Cholesky solve
 __device__ __forceinline__ int64_t pk(int i, int j) { return (int64_t)i * (i + 1) / 2 + j; }  // j <= i
 
-// Solve (packed lower L) L L^T x = x in place; 256 threads; columns in order.
-__device__ void chol_subst(const double* L, double* x, int n) {
-  for (int j = 0; j < n; ++j) {
-    __syncthreads();
-    const double xj = x[j] / L[pk(j, j)];
-    __syncthreads();
-    if (threadIdx.x == 0) x[j] = xj;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) x[i] -= L[pk(i, j)] * xj;
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    __syncthreads();
-    const double xj = x[j] / L[pk(j, j)];
-    __syncthreads();
-    if (threadIdx.x == 0) x[j] = xj;
-    for (int i = threadIdx.x; i < j; i += blockDim.x) x[i] -= L[pk(j, i)] * xj;
-  }
+constexpr int CNB = 16;  // Cholesky panel width
+
+// Blocked right-looking Cholesky of a packed lower matrix, in place (256
+// threads): per panel of CNB columns, warp 0 factors the diagonal block,
+// every thread solves one panel row against it, and the trailing lower
+// triangle is updated in 4 x 4 register tiles (two DFMAs per shared-memory
+// load).  Returns false, uniformly across the CTA, on a non-positive pivot.
+__device__ bool chol_blocked(double* L, double* invd, int n, int* fail) {
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const double* inv = nullptr;  // reciprocals of the current panel's diagonal
+  if (tid == 0) *fail = 0;
   __syncthreads();
+  for (int p0 = 0; p0 < n; p0 += CNB) {
+    const int nb = min(CNB, n - p0);
+    inv = invd + p0;
+    if (warp == 0) {
+      for (int c = 0; c < nb; ++c) {
+        const int pc = p0 + c;
+        const double d = L[pk(pc, pc)];
+        const double rj = rsqrt(d);
+        const double ljj = d * rj;
+        __syncwarp();
+        if (lane == 0) {
+          L[pk(pc, pc)] = ljj;
+          invd[pc] = rj;
+          if (!(d > 0.0) || !isfinite(d)) *fail = 1;
+        }
+        if (lane > c && lane < nb) L[pk(p0 + lane, pc)] *= rj;
+        __syncwarp();
+        if (lane > c && lane < nb) {
+          const double lrc = L[pk(p0 + lane, pc)];
+          for (int k = c + 1; k <= lane; ++k) L[pk(p0 + lane, p0 + k)] -= lrc * L[pk(p0 + k, pc)];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (*fail) return false;
+    // panel rows: L21 = A21 L11^-T, one row per thread
+    for (int i = p0 + nb + tid; i < n; i += nt) {
+      double* Li = L + pk(i, p0);
+      double v[CNB];
+#pragma unroll
+      for (int c = 0; c < CNB; ++c) v[c] = (c < nb) ? Li[c] : 0.0;
+#pragma unroll
+      for (int c = 0; c < CNB; ++c) {
+        if (c < nb) {
+          double sacc = v[c];
+          const double* Lc = L + pk(p0 + c, p0);
+#pragma unroll
+          for (int q = 0; q < CNB; ++q)
+            if (q < c) sacc -= v[q] * Lc[q];
+          v[c] = sacc * inv[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CNB; ++c)
+        if (c < nb) Li[c] = v[c];
+    }
+    __syncthreads();
+    // trailing update A22 -= L21 L21^T on the lower triangle, 4 x 4 tiles
+    const int r0 = p0 + nb, m = n - r0;
+    if (m > 0) {
+      const int Tt = (m + 3) / 4, ntile = Tt * (Tt + 1) / 2;
+      for (int t = tid; t < ntile; t += nt) {
+        int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while ((I + 1) * (I + 2) / 2 <= t) ++I;
+        while (I * (I + 1) / 2 > t) --I;
+        const int Kt = t - I * (I + 1) / 2;
+        const int i0 = r0 + 4 * I, k0 = r0 + 4 * Kt;
+        double acc[4][4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] = 0.0;
+        const double* ra[4];
+        const double* rb[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          ra[p] = L + pk(min(i0 + p, n - 1), p0);
+          rb[p] = L + pk(min(k0 + p, n - 1), p0);
+        }
+        for (int c = 0; c < nb; ++c) {
+          double a[4], b[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            a[p] = ra[p][c];
+            b[p] = rb[p][c];
+          }
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = i0 + p, k = k0 + q;
+            if (i < n && k <= i) L[pk(i, k)] -= acc[p][q];
+          }
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Solve L L^T x = x in place (packed lower L, invd = 1 / diag(L)), blocked
+// like the factorisation.
+__device__ void chol_subst(const double* L, const double* invd, double* x, int n) {
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  __syncthreads();
+  // forward: L z = x
+  for (int p0 = 0; p0 < n; p0 += CNB) {
+    const int nb = min(CNB, n - p0);
+    if (warp == 0) {
+      for (int c = 0; c < nb; ++c) {
+        double zc = x[p0 + c];
+        __syncwarp();
+        zc *= invd[p0 + c];
+        if (lane == 0) x[p0 + c] = zc;
+        if (lane > c && lane < nb) x[p0 + lane] -= L[pk(p0 + lane, p0 + c)] * zc;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int i = p0 + nb + tid; i < n; i += nt) {
+      const double* Li = L + pk(i, p0);
+      double sacc = 0.0;
+      for (int c = 0; c < nb; ++c) sacc += Li[c] * x[p0 + c];
+      x[i] -= sacc;
+    }
+    __syncthreads();
+  }
+  // backward: L^T x = z
+  const int last = ((n - 1) / CNB) * CNB;
+  for (int p0 = last; p0 >= 0; p0 -= CNB) {
+    const int nb = min(CNB, n - p0);
+    if (warp == 0) {
+      for (int c = nb - 1; c >= 0; --c) {
+        double xc = x[p0 + c];
+        __syncwarp();
+        xc *= invd[p0 + c];
+        if (lane == 0) x[p0 + c] = xc;
+        if (lane < c) x[p0 + lane] -= L[pk(p0 + c, p0 + lane)] * xc;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < p0; i += nt) {
+      double sacc = 0.0;
+      for (int c = 0; c < nb; ++c) sacc += L[pk(p0 + c, i)] * x[p0 + c];
+      x[i] -= sacc;
+    }
+    __syncthreads();
+  }
 }
 
 // One CTA (256 threads) per instance.  Packed lower factor in shared memory
@@ -287,13 +427,13 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
   const InstDesc I = a.inst[b];
   const int n = I.n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* vec = reinterpret_cast<double*>(smem_raw);  // rhs, x, res
+  double* vec = reinterpret_cast<double*>(smem_raw);  // rhs, x, res, 1/diag(L)
   double* rhs = vec;
   double* x = vec + n;
   double* res = vec + 2 * n;
-  double* L = (n <= a.smem_n_max) ? vec + 3 * n : a.Lg + a.o_L[b];
+  double* invd = vec + 3 * n;
+  double* L = (n <= a.smem_n_max) ? vec + 4 * n : a.Lg + a.o_L[b];
   __shared__ int fail;
-  __shared__ double sdiag[1];
   const double* A = a.A + I.o_nn;
   const double* S2 = a.S2 + I.o_nn;
   double* H = a.H + I.o_nn;
@@ -320,30 +460,8 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
     __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x)
       for (int c = 0; c <= r; ++c) L[pk(r, c)] = H[(int64_t)r * n + c];
-    if (threadIdx.x == 0) fail = 0;
     __syncthreads();
-    // right-looking Cholesky, one column at a time
-    for (int j = 0; j < n; ++j) {
-      if (threadIdx.x == 0) {
-        const double d = L[pk(j, j)];
-        if (!(d > 0.0) || !isfinite(d)) fail = 1;
-        sdiag[0] = sqrt(d);
-        L[pk(j, j)] = sdiag[0];
-      }
-      __syncthreads();
-      if (fail) break;
-      const double ljj = sdiag[0];
-      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) L[pk(i, j)] /= ljj;
-      __syncthreads();
-      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      for (int i = j + 1 + warp; i < n; i += 8) {
-        const double lij = L[pk(i, j)];
-        for (int k = j + 1 + lane; k <= i; k += 32) L[pk(i, k)] -= lij * L[pk(k, j)];
-      }
-      __syncthreads();
-    }
-    __syncthreads();
-    if (!fail) {
+    if (chol_blocked(L, invd, n, &fail)) {
       ok = true;
       break;
     }
@@ -361,7 +479,7 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
   // y = H^-1 rhs with iterative refinement (residual in FP64 against H)
   for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = rhs[j];
   __syncthreads();
-  chol_subst(L, x, n);
+  chol_subst(L, invd, x, n);
   for (int t = 0; t < a.cs.ir_steps; ++t) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = warp; i < n; i += 8) {
@@ -371,7 +489,7 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
       if (lane == 0) res[i] = rhs[i] - acc;
     }
     __syncthreads();
-    chol_subst(L, res, n);
+    chol_subst(L, invd, res, n);
     for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] += res[j];
     __syncthreads();
   }
