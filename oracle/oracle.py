@@ -21,6 +21,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "gnmppi_oracle.c")
+MLP_SRC = os.path.join(HERE, "mlp_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
 DYN = {"pendulum": 0, "chain": 1, "linear": 2, "rosenbrock": 3, "rastrigin": 4, "heaviside": 5, "lincont": 6}
@@ -30,12 +31,12 @@ JAC = {"lsq": 0, "sigma": 1, "auto": 2}
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (FP contraction off so x86 and Arm agree)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "gnmppi_oracle.h"))
+        os.path.getmtime(SRC), os.path.getmtime(MLP_SRC), os.path.getmtime(os.path.join(HERE, "gnmppi_oracle.h"))
     ):
         tmp = LIB + f".tmp{os.getpid()}"
         subprocess.check_call(
             ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
-             "-o", tmp, SRC, "-lm"]
+             "-o", tmp, SRC, MLP_SRC, "-lm"]
         )
         os.replace(tmp, LIB)
     return LIB
@@ -89,6 +90,14 @@ def lib():
         L.orc_softmin.argtypes = [C.c_int32, _DP, C.c_void_p, C.c_double, _DP, _DP]
         L.orc_cholesky.argtypes = [C.c_int32, _DP]
         L.orc_chol_solve.argtypes = [C.c_int32, _DP, _DP]
+        IP = C.POINTER(C.c_int32)
+        L.mlo_num_params.restype = C.c_int64
+        L.mlo_num_params.argtypes = [C.c_int32, IP]
+        L.mlo_forward.argtypes = [C.c_int32, IP, _DP, _DP, _DP, C.c_int32, _DP, _DP]
+        L.mlo_loss_grad.restype = C.c_double
+        L.mlo_loss_grad.argtypes = [C.c_int32, IP, _DP, _DP, _DP, C.c_int32, _DP, _DP, C.c_int32, _DP]
+        L.mlo_adam.argtypes = [C.c_int64, _DP, _DP, _DP, _DP, C.c_int32, C.c_double, C.c_double, C.c_double,
+                               C.c_double]
     return _lib
 
 
@@ -376,3 +385,40 @@ def method_a(model: Model, x0, xref, U0, max_iter=200, eps=6e-6, lam=1e-10, gtol
     st = lib().orc_method_a(C.byref(model.c()), _p(x0), _p(_xref(model, xref)), _p(U), max_iter, eps, lam, gtol,
                             C.byref(c), C.byref(it))
     return int(st), U, float(c.value), int(it.value)
+
+
+# ---------------------------------------------------------------------------
+# learned warm start: FP64 MLP (mlp_oracle.c)
+
+
+def _dims(dims):
+    return (C.c_int32 * len(dims))(*dims)
+
+
+def mlp_num_params(dims) -> int:
+    return int(lib().mlo_num_params(len(dims) - 1, _dims(dims)))
+
+
+def mlp_forward(dims, params, x_mean, x_std, X) -> np.ndarray:
+    X = np.ascontiguousarray(X, float)
+    B = X.shape[0]
+    out = np.zeros((B, dims[-1]))
+    lib().mlo_forward(len(dims) - 1, _dims(dims), _p(np.ascontiguousarray(params, float)),
+                      _p(np.ascontiguousarray(x_mean, float)), _p(np.ascontiguousarray(x_std, float)), B, _p(X),
+                      _p(out))
+    return out
+
+
+def mlp_loss_grad(dims, params, x_mean, x_std, X, T, nu):
+    X = np.ascontiguousarray(X, float)
+    T = np.ascontiguousarray(T, float)
+    g = np.zeros(mlp_num_params(dims))
+    loss = lib().mlo_loss_grad(len(dims) - 1, _dims(dims), _p(np.ascontiguousarray(params, float)),
+                               _p(np.ascontiguousarray(x_mean, float)), _p(np.ascontiguousarray(x_std, float)),
+                               X.shape[0], _p(X), _p(T), nu, _p(g))
+    return float(loss), g
+
+
+def mlp_adam(params, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step in place on float64 arrays."""
+    lib().mlo_adam(params.size, _p(params), _p(np.ascontiguousarray(grad, float)), _p(m), _p(v), t, lr, b1, b2, eps)
