@@ -20,6 +20,8 @@ import numpy as np
 BASE_SEED = 2512045790
 CHAIN_DEFAULTS = dict(mass=0.1, k=10.0, k3=1.0, damping=0.05, gravity=9.81)
 PHI_RANGE = (np.pi / 16, np.pi / 8)
+WARM_PHI = 3 * np.pi / 32  # the one target of the warm-start workload
+TRAIN_STREAM, EVAL_STREAM = 0, 1  # initial-state streams of its training and evaluation sets
 
 
 def rng(seed: int, stream: int = 0) -> np.random.Generator:
@@ -78,10 +80,18 @@ def chain_instances(seed: int, batch: int, M: int, stream: int = 0, x0_std: floa
     return x0, tgt
 
 
+def stream_rng(seed: int, stream: int) -> np.random.Generator:
+    """Philox stream whose counter starts with the stream id in its third word,
+    so streams of one key never overlap."""
+    return np.random.Generator(np.random.Philox(key=int(seed) & ((1 << 64) - 1),
+                                                counter=np.array([0, 0, int(stream) + 1, 0], dtype=np.uint64)))
+
+
 def chain_fixed_target_states(seed: int, batch: int, M: int, phi: float, stream: int = 0, x0_std: float = 0.05,
                               **params):
-    """Initial states around the rest state for one fixed target (warm-start workload)."""
-    g = rng(seed, 3 + 16 * stream)
+    """Initial states around the rest state for one fixed target (warm-start
+    workload); training and evaluation sets come from disjoint streams."""
+    g = stream_rng(seed, stream)
     rest = chain_rest_state(M, **params)
     return rest[None, :] + g.normal(0.0, x0_std, size=(batch, rest.size)), chain_target(M, phi, **params)
 

@@ -1,14 +1,17 @@
 """Write the reference optima C* of the chain benchmark instances.
 
-Calls only the FP64 CPU oracle.  For each instance b of the seeded workload
-(chain M=10, N=100, K=2048, 30 iterations, sigma0 0.2, lambda 1e-3,
-seed 2512045790 + 1):
+Calls only the FP64 CPU oracle.  Two seeded workloads (chain M=10, N=100,
+K=2048, 30 iterations, sigma0 0.2, lambda 1e-3):
+  chain_m10        targets rotated by phi ~ U(pi/16, pi/8), seed 2512045790 + 1
+  chain_m10_fixed  one target (phi = 3 pi / 32), held-out initial states of the
+                   warm-start evaluation stream, seed 2512045790 + 3
+For each instance b:
   C_gn  = cost after the oracle's 30-iteration GN-MPPI solve (Algorithm 1),
   C*    = cost after polishing that solution with Method A (central-FD GGN,
           Sec. 5) until the FD gradient falls below 1e-10 or no step helps.
-Output: chain_m10_cstar.txt (one line per instance: b C_gn C*).
+Output: <workload>_cstar.txt (one line per instance: b C_gn C*).
 
-Usage: python tests/golden/make_cstar.py [batch] [processes]
+Usage: python tests/golden/make_cstar.py [batch] [processes] [workload]
 """
 import multiprocessing as mp
 import os
@@ -21,14 +24,28 @@ sys.path.insert(0, ROOT)
 M, N, K, T, SIGMA0, LAM = 10, 100, 2048, 30, 0.2, 1e-3
 
 
-def one(b):
+def instances(workload, batch):
+    """(seed, x0 [batch][nx], targets [batch][2(M-1)]) of a workload."""
+    import numpy as np
+
+    from paper_2512_04579_gb300 import inputs as I
+
+    if workload == "chain_m10":
+        seed = I.BASE_SEED + 1
+        x0, tgt = I.chain_instances(seed, batch, M)
+        return seed, x0, tgt
+    seed = I.BASE_SEED + 3
+    x0, t = I.chain_fixed_target_states(seed, batch, M, I.WARM_PHI, stream=I.EVAL_STREAM)
+    return seed, x0, np.tile(t, (batch, 1))
+
+
+def one(args):
     import numpy as np
 
     from oracle import oracle as O
-    from paper_2512_04579_gb300 import inputs as I
 
-    seed = I.BASE_SEED + 1
-    x0, tgt = I.chain_instances(seed, BATCH, M)
+    b, workload = args
+    seed, x0, tgt = instances(workload, BATCH)
     m = O.chain(M=M, N=N)
     opt = O.Options(K=K, iterations=T, lam=LAM, seed=seed, threads=1)
     st, U, Uh, Ch, its = O.solve(m, opt, x0[b], tgt[b], np.zeros(m.n), SIGMA0, inst=b)
@@ -40,15 +57,18 @@ BATCH = int(sys.argv[1]) if len(sys.argv) > 1 else 256
 
 if __name__ == "__main__":
     procs = int(sys.argv[2]) if len(sys.argv) > 2 else os.cpu_count()
+    workload = sys.argv[3] if len(sys.argv) > 3 else "chain_m10"
     from oracle import oracle as O
 
     O.build()
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
-        rows = sorted(pool.map(one, range(BATCH), chunksize=1))
-    out = os.path.join(HERE, "chain_m10_cstar.txt")
+        rows = sorted(pool.map(one, [(b, workload) for b in range(BATCH)], chunksize=1))
+    out = os.path.join(HERE, f"{workload}_cstar.txt")
+    seed_note = "2512045790+1" if workload == "chain_m10" else "2512045790+3 (fixed target, eval stream)"
     with open(out, "w") as f:
-        f.write(f"# chain M={M} N={N} K={K} T={T} sigma0={SIGMA0} lambda={LAM} seed=2512045790+1 batch={BATCH}\n")
+        f.write(f"# {workload}: chain M={M} N={N} K={K} T={T} sigma0={SIGMA0} lambda={LAM} seed={seed_note} "
+                f"batch={BATCH}\n")
         f.write("# written by tests/golden/make_cstar.py from the FP64 oracle: b C_gn C_star\n")
         for b, cg, cs in rows:
             f.write(f"{b} {cg:.17g} {cs:.17g}\n")
