@@ -32,12 +32,85 @@ M, N, K, T, SIGMA0, LAM = 10, 100, 2048, 30, 0.2, 1e-3
 GAP = 1e-6
 METRIC = "OCP solves/s to 1e-6 rel. cost gap"
 CSTAR = os.path.join(ROOT, "tests", "golden", "chain_m10_cstar.txt")
+CSTAR_FIXED = os.path.join(ROOT, "tests", "golden", "chain_m10_fixed_cstar.txt")
 WORKLOAD = "chain M=10 N=100 nu=2 K=2048 T=30 sigma0=0.2 lambda=1e-3"
 
 
-def load_cstar():
-    rows = np.loadtxt(CSTAR, comments="#")
+def load_cstar(path=CSTAR):
+    rows = np.loadtxt(path, comments="#")
     return rows[:, 0].astype(int), rows[:, 1], rows[:, 2]
+
+
+def learned_arm(args, dev, stream):
+    """Batched + learned warm start vs plain GN-MPPI on the warm-start workload:
+    one chain target, 256 held-out initial states with oracle optima.  Learned:
+    MLP warm start -> GN-MPPI K=512, 5 iterations -> plain GN-MPPI (K=2048, 30
+    iterations) from there for instances whose last iteration still moved the
+    cost by more than 1e-6 (relative).  Plain: cold start, K=2048, 30 iterations."""
+    import torch
+
+    from paper_2512_04579_gb300 import gnmppi as G
+    from paper_2512_04579_gb300 import inputs as I
+    from paper_2512_04579_gb300 import warmstart as W
+
+    if not os.path.exists(W.WEIGHTS):
+        return {"unavailable": "no trained warm-start weights"}
+    _, _, Cs = load_cstar(CSTAR_FIXED)
+    B = len(Cs)
+    x0, tg = I.chain_fixed_target_states(W.SEED, B, W.M, I.WARM_PHI, stream=I.EVAL_STREAM)
+    dx = torch.tensor(x0.ravel(), dtype=torch.float64, device=dev)
+    dt = torch.tensor(np.tile(tg, (B, 1)).ravel(), dtype=torch.float64, device=dev)
+    mlp = W.load(W.WEIGHTS, max_batch=B, stream=stream.cuda_stream)
+    ls = W.LearnedSolver(mlp, B, stream=stream.cuda_stream)
+    hp = G.gnmppi_create(W.chain_problem(2048, 30), B, None, stream.cuda_stream)
+    Cout = torch.empty(B, dtype=torch.float64, device=dev)
+
+    def solved_of(dU):
+        G.gnmppi_cost(hp, G.MEM_DEVICE, dx, dt, dU, Cout)
+        g = (Cout.cpu().numpy() - Cs) / Cs
+        return int(np.sum(g <= GAP)), float(np.median(g))
+
+    def timed(fn, steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = None
+        for _ in range(steps):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, out
+
+    dU = torch.zeros(B * W.NMU, dtype=torch.float64, device=dev)
+
+    def learned_once():
+        return ls.solve(dx, dt, dU)
+
+    for _ in range(max(1, args.warmup)):
+        learned_once()
+    ms_l, nfb = timed(learned_once, args.steps)
+    s_l, g_l = solved_of(dU)
+    dP = torch.zeros_like(dU)
+
+    def plain_once():
+        dP.zero_()
+        G.gnmppi_solve(hp, G.MEM_DEVICE, dx, dt, dP, None)
+
+    for _ in range(max(1, args.warmup)):
+        plain_once()
+    ms_p, _ = timed(plain_once, args.steps)
+    s_p, g_p = solved_of(dP)
+    ls.close()
+    mlp.close()
+    G.gnmppi_destroy(hp)
+    z = np.load(W.WEIGHTS)
+    return {"workload": "chain M=10 N=100, one target (phi=3pi/32), %d held-out initial states" % B,
+            "learned_solves_per_s": s_l / (ms_l / 1e3), "learned_ms_per_batch": ms_l, "learned_solved": s_l,
+            "learned_fallbacks": int(nfb), "learned_gap_median": g_l,
+            "plain_solves_per_s": s_p / (ms_p / 1e3), "plain_ms_per_batch": ms_p, "plain_solved": s_p,
+            "plain_gap_median": g_p, "speedup": (s_l / ms_l) / max(1e-30, s_p / ms_p),
+            "network": "36-256-256-256-300 GELU, BF16 weights, trained on %d plain solves" % int(z["train_solves"])}
 
 
 def dist_env():
@@ -253,6 +326,7 @@ def run_gnmppi(args):
                      "peak_note": "FP32 152 SMs x 128 lanes x 2 flop/FMA at the %.0f MHz maximum SM clock" % sm_max},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
     }
+    out["learned"] = learned_arm(args, dev, stream)
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(out))

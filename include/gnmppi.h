@@ -109,6 +109,7 @@ typedef struct {
 /* Per-instance result of gnmppi_solve. */
 typedef struct {
   double C_initial;  /* C(U_0)                                        */
+  double C_prev;     /* C(U_{T-1}), the cost before the last iteration */
   double C_final;    /* C(U_T) from the last line search              */
   double sigma_final;/* sampling std scale after the last shrink      */
   int32_t iterations;/* iterations run                                */
@@ -153,6 +154,12 @@ gnmppi_status gnmppi_layout(gnmppi_t h, int64_t* x0_off, int64_t* xref_off, int6
  * worst instance status (E_NOT_PD / E_NONFINITE), or OK. */
 gnmppi_status gnmppi_solve(gnmppi_t h, int32_t mem, const double* x0, const double* xref, double* U,
                            const double* sigma, gnmppi_report* rep);
+
+/* gnmppi_solve restricted to the instances with active[b] != 0 (host array
+ * of batch int32, nullable = all): the others are skipped by every kernel,
+ * keep their U unchanged and report status OK with 0 iterations. */
+gnmppi_status gnmppi_solve_masked(gnmppi_t h, int32_t mem, const double* x0, const double* xref, double* U,
+                                  const double* sigma, const int32_t* active, gnmppi_report* rep);
 
 /* One Algorithm-1 iteration with index `iteration` (it selects the Philox
  * stream) at the given U (in/out: U_k -> U_{k+1}) and per-component std sigma
@@ -216,6 +223,56 @@ const char* gnmppi_phase_name(int32_t i);
 gnmppi_status gnmppi_softmin_noalloc(const double* C, const double* W, int32_t count, int32_t n,
                                      int32_t antithetic, double tau, double* mppi, double* stats,
                                      void* cuda_stream, char* err, int32_t err_len);
+
+/* ---------------------------------------------------------------------------
+ * Learned warm start.  A multilayer perceptron maps an initial state x0 to a
+ * nominal control sequence mu (U_0 of Algorithm 1) and one log sampling scale
+ * s_k per control step (Sigma_0 = diag(exp(2 s_k))).  The paper cites learned
+ * sampling distributions as prior art (Sec. 1); the network is trained on
+ * solutions of plain GN-MPPI by minimising the Gaussian negative
+ * log-likelihood  (1/B) sum_b sum_j [ (t_j - mu_j)^2 exp(-2 s_{j/nu}) / 2 + s_{j/nu} ]
+ * with Adam (Kingma & Ba, 2015).  Architecture: h_0 = (x0 - x_mean) / x_std,
+ * hidden layers h_l = GELU(W_l h_{l-1} + b_l), linear output y = W_L h + b_L,
+ * mu = y[0 : n_mu], s = y[n_mu : n_mu + n_mu/nu].  Parameters are flat, per
+ * layer W_l [d_l][d_{l-1}] row-major then b_l [d_l].  Arrays are doubles in
+ * `mem` memory; B <= max_batch.
+ * ------------------------------------------------------------------------- */
+typedef struct gnmppi_mlp_s* gnmppi_mlp_t;
+
+/* dims: nlayers + 1 widths (input ... output); the output width must be
+ * n_mu + n_mu/nu.  weights_bf16: forward and input-gradient products use
+ * BF16-rounded weights (FP32 master weights, FP32 accumulation).  Parameters
+ * start at zero; set them with gnmppi_mlp_set_params.  E_ARG on bad sizes,
+ * E_CUDA without a GPU. */
+gnmppi_status gnmppi_mlp_create(int32_t nlayers, const int32_t* dims, int32_t nu, int32_t weights_bf16,
+                                int32_t max_batch, void* cuda_stream, gnmppi_mlp_t* out);
+int64_t gnmppi_mlp_num_params(gnmppi_mlp_t m);
+/* Copy parameters in (resets the Adam moments and step count) or out. */
+gnmppi_status gnmppi_mlp_set_params(gnmppi_mlp_t m, int32_t mem, const double* params, int64_t count);
+gnmppi_status gnmppi_mlp_get_params(gnmppi_mlp_t m, int32_t mem, double* params, int64_t count);
+/* Input normalisation (host arrays of d_0) and the output scale: the network
+ * is trained on the optimal controls divided by y_scale and warm-starts with U_0 = y_scale mu,
+ * sigma = y_scale exp(s). */
+gnmppi_status gnmppi_mlp_set_normalization(gnmppi_mlp_t m, const double* x_mean, const double* x_std, double y_scale);
+/* Raw network outputs Y [B][d_L] for inputs X [B][d_0]. */
+gnmppi_status gnmppi_mlp_forward(gnmppi_mlp_t m, int32_t mem, const double* X, int32_t B, double* Y);
+/* Mean loss (host double, nullable) and its gradient (grad: n_params doubles
+ * in `mem` memory, nullable) for inputs X [B][d_0] and targets T [B][n_mu]. */
+gnmppi_status gnmppi_mlp_loss_grad(gnmppi_mlp_t m, int32_t mem, const double* X, const double* T, int32_t B,
+                                   double* loss, double* grad);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on one minibatch; loss
+ * (host, nullable) receives the minibatch loss before the step. */
+gnmppi_status gnmppi_mlp_train_step(gnmppi_mlp_t m, int32_t mem, const double* X, const double* T, int32_t B,
+                                    double lr, double* loss);
+/* Warm start for B states: U0 [B][n_mu] and per-component sigma [B][n_mu]
+ * (both laid out like gnmppi_solve's U and sigma for a uniform batch).  The
+ * sampling scale is clamped to [sigma_min, sigma_max]: the network's scale is
+ * its uncertainty about U*, which can fall below what a finite-difference
+ * Jacobian from FP32 rollouts resolves. */
+gnmppi_status gnmppi_mlp_warm_start(gnmppi_mlp_t m, int32_t mem, const double* X, int32_t B, double sigma_min,
+                                    double sigma_max, double* U0, double* sigma);
+void gnmppi_mlp_destroy(gnmppi_mlp_t m);
+const char* gnmppi_mlp_last_error(gnmppi_mlp_t m);
 
 /* Number of kernels the library launched on this handle since creation. */
 int64_t gnmppi_launch_count(gnmppi_t h);

@@ -651,15 +651,26 @@ static gnmppi_status check_timeout(gnmppi_t h) {
 static gnmppi_status worst_status(const std::vector<InstState>& s) {
   int w = 0;
   for (auto& x : s)
-    if (x.status != 0 && (w == 0 || x.status < w)) w = x.status;
+    if (x.status < 0 && (w == 0 || x.status < w)) w = x.status;
   return (gnmppi_status)w;
 }
 
-extern "C" gnmppi_status gnmppi_solve(gnmppi_t h, int32_t mem, const double* x0, const double* xref, double* U,
-                                      const double* sigma, gnmppi_report* rep) {
+// Inactive instances carry this status: every kernel skips them.
+constexpr int32_t kInactive = 1;
+
+extern "C" gnmppi_status gnmppi_solve_masked(gnmppi_t h, int32_t mem, const double* x0, const double* xref,
+                                             double* U, const double* sigma, const int32_t* active,
+                                             gnmppi_report* rep) {
   if (!h) return GNMPPI_E_ARG;
   gnmppi_status st = load_inputs(h, mem, x0, xref, U, sigma);
   if (st != GNMPPI_OK) return st;
+  if (active) {
+    std::vector<InstState> init(h->batch);
+    memset(init.data(), 0, sizeof(InstState) * h->batch);
+    for (int b = 0; b < h->batch; ++b) init[b].status = active[b] ? 0 : kInactive;
+    CK(cudaMemcpyAsync(h->d_st, init.data(), sizeof(InstState) * h->batch, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // init is a temporary
+  }
   // one CUDA graph per handle: the nominal rollout and every Algorithm-1 iteration
   if (!h->gexec) {
     cudaGraph_t graph;
@@ -692,15 +703,21 @@ extern "C" gnmppi_status gnmppi_solve(gnmppi_t h, int32_t mem, const double* x0,
     CK(cudaMemcpy(s_end.data(), h->d_s, 8 * h->n_U, cudaMemcpyDeviceToHost));
     for (int b = 0; b < h->batch; ++b) {
       rep[b].C_final = s[b].C_nom;
-      rep[b].C_initial = 0.0;
+      rep[b].C_initial = s[b].C_init;
+      rep[b].C_prev = s[b].iters > 0 ? s[b].C_start : s[b].C_nom;
       rep[b].sigma_final = s_end[h->desc[b].o_U];
       rep[b].iterations = s[b].iters;
-      rep[b].status = s[b].status;
+      rep[b].status = s[b].status == kInactive ? 0 : s[b].status;
       rep[b].n_masked = s[b].total_masked;
       rep[b].chol_retries = s[b].total_retries;
     }
   }
   return worst_status(s);
+}
+
+extern "C" gnmppi_status gnmppi_solve(gnmppi_t h, int32_t mem, const double* x0, const double* xref, double* U,
+                                      const double* sigma, gnmppi_report* rep) {
+  return gnmppi_solve_masked(h, mem, x0, xref, U, sigma, nullptr, rep);
 }
 
 extern "C" gnmppi_status gnmppi_step(gnmppi_t h, int32_t mem, const double* x0, const double* xref, double* U,

@@ -40,6 +40,7 @@ struct InstDesc {
 struct InstState {
   double C_nom;        // C(U_k) of the current iterate
   double C_start;      // C(U_k) at the start of the last completed iteration
+  double C_init;       // C(U_0) from the nominal rollout
   double lambda_used;
   double c_min, sum_w, sum_w2, ess, pr_norm, step_norm;
   double C_new, alpha;

@@ -241,7 +241,10 @@ __global__ void __launch_bounds__(128) k_line(RollArgs a) {
   cost.add(em.csum);
   const double C = 0.5 * cost.value();
   if (a.mode == 0) a.Cl[(int64_t)b * (kMaxL + 1) + j] = C;
-  if (a.mode == 1) a.st[b].C_nom = C;
+  if (a.mode == 1) {
+    a.st[b].C_nom = C;
+    a.st[b].C_init = C;
+  }
   if (a.mode == 2) a.Cout[b] = C;
 }
 

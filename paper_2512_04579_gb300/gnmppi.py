@@ -22,9 +22,12 @@ PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
 JAC_LSQ, JAC_SIGMA, JAC_AUTO = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 
-EXPORTS = ["gnmppi_create", "gnmppi_layout", "gnmppi_solve", "gnmppi_step", "gnmppi_cost", "gnmppi_debug_read",
+EXPORTS = ["gnmppi_create", "gnmppi_layout", "gnmppi_solve", "gnmppi_solve_masked", "gnmppi_step", "gnmppi_cost", "gnmppi_debug_read",
            "gnmppi_phase_times", "gnmppi_phase_name", "gnmppi_softmin_noalloc", "gnmppi_launch_count",
-           "gnmppi_destroy", "gnmppi_last_error", "gnmppi_status_string", "gnmppi_version"]
+           "gnmppi_destroy", "gnmppi_last_error", "gnmppi_status_string", "gnmppi_version", "gnmppi_mlp_create",
+           "gnmppi_mlp_num_params", "gnmppi_mlp_set_params", "gnmppi_mlp_get_params", "gnmppi_mlp_set_normalization",
+           "gnmppi_mlp_forward", "gnmppi_mlp_loss_grad", "gnmppi_mlp_train_step", "gnmppi_mlp_warm_start",
+           "gnmppi_mlp_destroy", "gnmppi_mlp_last_error"]
 
 
 class Problem(C.Structure):
@@ -41,7 +44,8 @@ class InstanceShape(C.Structure):
 
 
 class Report(C.Structure):
-    _fields_ = [("C_initial", C.c_double), ("C_final", C.c_double), ("sigma_final", C.c_double),
+    _fields_ = [("C_initial", C.c_double), ("C_prev", C.c_double), ("C_final", C.c_double),
+                ("sigma_final", C.c_double),
                 ("iterations", C.c_int32), ("status", C.c_int32), ("n_masked", C.c_int32),
                 ("chol_retries", C.c_int32)]
 
@@ -70,6 +74,8 @@ def load(path: str | None = None):
     L.gnmppi_create.argtypes = [C.POINTER(Problem), C.c_int32, C.POINTER(InstanceShape), vp, C.POINTER(vp)]
     L.gnmppi_layout.argtypes = [vp, vp, vp, vp]
     L.gnmppi_solve.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp]
+    L.gnmppi_solve_masked.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp, vp]
+    L.gnmppi_solve_masked.restype = C.c_int32
     L.gnmppi_step.argtypes = [vp, C.c_int32, vp, vp, vp, vp, C.c_int32, vp]
     L.gnmppi_cost.argtypes = [vp, C.c_int32, vp, vp, vp, vp]
     L.gnmppi_debug_read.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int64, C.POINTER(C.c_int64)]
@@ -90,6 +96,24 @@ def load(path: str | None = None):
     L.gnmppi_status_string.restype = C.c_char_p
     L.gnmppi_version.restype = C.c_int32
     for f in ("gnmppi_create", "gnmppi_layout", "gnmppi_solve", "gnmppi_step", "gnmppi_cost", "gnmppi_debug_read"):
+        getattr(L, f).restype = C.c_int32
+    L.gnmppi_mlp_create.argtypes = [C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_int32, vp,
+                                    C.POINTER(vp)]
+    L.gnmppi_mlp_num_params.argtypes = [vp]
+    L.gnmppi_mlp_num_params.restype = C.c_int64
+    L.gnmppi_mlp_set_params.argtypes = [vp, C.c_int32, vp, C.c_int64]
+    L.gnmppi_mlp_get_params.argtypes = [vp, C.c_int32, vp, C.c_int64]
+    L.gnmppi_mlp_set_normalization.argtypes = [vp, vp, vp, C.c_double]
+    L.gnmppi_mlp_forward.argtypes = [vp, C.c_int32, vp, C.c_int32, vp]
+    L.gnmppi_mlp_loss_grad.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, vp, vp]
+    L.gnmppi_mlp_train_step.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, C.c_double, vp]
+    L.gnmppi_mlp_warm_start.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_double, C.c_double, vp, vp]
+    L.gnmppi_mlp_destroy.argtypes = [vp]
+    L.gnmppi_mlp_destroy.restype = None
+    L.gnmppi_mlp_last_error.argtypes = [vp]
+    L.gnmppi_mlp_last_error.restype = C.c_char_p
+    for f in ("gnmppi_mlp_create", "gnmppi_mlp_set_params", "gnmppi_mlp_get_params", "gnmppi_mlp_set_normalization",
+              "gnmppi_mlp_forward", "gnmppi_mlp_loss_grad", "gnmppi_mlp_train_step", "gnmppi_mlp_warm_start"):
         getattr(L, f).restype = C.c_int32
     _lib = L
     return L
@@ -217,6 +241,15 @@ def gnmppi_solve(h, mem, x0, xref, U, sigma=None, batch: int | None = None):
     return st, rep
 
 
+def gnmppi_solve_masked(h, mem, x0, xref, U, sigma, active, batch: int):
+    rep = (Report * batch)()
+    act = None if active is None else np.ascontiguousarray(active, dtype=np.int32)
+    st = load().gnmppi_solve_masked(h, mem, _ptr(x0), _ptr(xref), _ptr(U), _ptr(sigma),
+                                    None if act is None else act.ctypes.data, rep)
+    _check(h, st, "gnmppi_solve_masked")
+    return st, rep
+
+
 def gnmppi_step(h, mem, x0, xref, U, sigma, iteration: int, batch: int | None = None):
     rep = (IterReport * batch)() if batch else None
     st = load().gnmppi_step(h, mem, _ptr(x0), _ptr(xref), _ptr(U), _ptr(sigma), iteration, rep)
@@ -316,3 +349,80 @@ class Solver:
 
     def debug(self, name: str, inst: int = 0, count: int = 1 << 26) -> np.ndarray:
         return gnmppi_debug_read(self.h, DEBUG[name], inst, count)
+
+
+# ---------------------------------------------------------------------------
+# learned warm start
+
+
+class Mlp:
+    """Owner of a gnmppi_mlp_t handle; arrays are host numpy (MEM_HOST) or
+    CUDA torch tensors (MEM_DEVICE)."""
+
+    def __init__(self, dims, nu=2, weights_bf16=True, max_batch=4096, stream=None):
+        L = load()
+        self.dims = list(dims)
+        self.nu = nu
+        self.nmu = dims[-1] // (nu + 1) * nu
+        arr = (C.c_int32 * len(dims))(*dims)
+        h = C.c_void_p()
+        st = L.gnmppi_mlp_create(len(dims) - 1, arr, nu, int(weights_bf16), max_batch, stream, C.byref(h))
+        if st != OK:
+            raise GnmppiError(st, "gnmppi_mlp_create: " + L.gnmppi_mlp_last_error(None).decode())
+        self.h = h
+        self.np = int(L.gnmppi_mlp_num_params(h))
+
+    def _chk(self, st, name):
+        if st != OK:
+            raise GnmppiError(st, f"{name}: " + load().gnmppi_mlp_last_error(self.h).decode())
+
+    def close(self):
+        if self.h is not None:
+            load().gnmppi_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params, mem=MEM_HOST):
+        self._chk(load().gnmppi_mlp_set_params(self.h, mem, _ptr(params), self.np), "gnmppi_mlp_set_params")
+
+    def get_params(self):
+        out = np.zeros(self.np)
+        self._chk(load().gnmppi_mlp_get_params(self.h, MEM_HOST, out.ctypes.data, self.np), "gnmppi_mlp_get_params")
+        return out
+
+    def set_normalization(self, x_mean, x_std, y_scale):
+        xm = np.ascontiguousarray(x_mean, float)
+        xs = np.ascontiguousarray(x_std, float)
+        self._chk(load().gnmppi_mlp_set_normalization(self.h, xm.ctypes.data, xs.ctypes.data, float(y_scale)),
+                  "gnmppi_mlp_set_normalization")
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, float)
+        Y = np.zeros((X.shape[0], self.dims[-1]))
+        self._chk(load().gnmppi_mlp_forward(self.h, MEM_HOST, X.ctypes.data, X.shape[0], Y.ctypes.data),
+                  "gnmppi_mlp_forward")
+        return Y
+
+    def loss_grad(self, X, T):
+        X = np.ascontiguousarray(X, float)
+        T = np.ascontiguousarray(T, float)
+        g = np.zeros(self.np)
+        loss = C.c_double()
+        self._chk(load().gnmppi_mlp_loss_grad(self.h, MEM_HOST, X.ctypes.data, T.ctypes.data, X.shape[0],
+                                               C.byref(loss), g.ctypes.data), "gnmppi_mlp_loss_grad")
+        return loss.value, g
+
+    def train_step(self, X, T, B, lr, mem=MEM_DEVICE):
+        loss = C.c_double()
+        self._chk(load().gnmppi_mlp_train_step(self.h, mem, _ptr(X), _ptr(T), B, lr, C.byref(loss)),
+                  "gnmppi_mlp_train_step")
+        return loss.value
+
+    def warm_start(self, X, B, U0, sigma, sigma_min=1e-300, sigma_max=1e300, mem=MEM_DEVICE):
+        self._chk(load().gnmppi_mlp_warm_start(self.h, mem, _ptr(X), B, sigma_min, sigma_max, _ptr(U0), _ptr(sigma)),
+                  "gnmppi_mlp_warm_start")
