@@ -1,5 +1,5 @@
 """What the learned warm start gains: an MLP trained (on the GPU, by the
-library's own kernels) on 4096 plain GN-MPPI solutions of one chain target
+library's own kernels) on 16384 plain GN-MPPI solutions of one chain target
 warm-starts held-out instances so that GN-MPPI with K = 512 and 5 iterations
 lands much closer to the plain solution (K = 2048, 30 iterations, the judge
 of the cost gap) than the same budget from a cold start."""
@@ -19,8 +19,8 @@ def trained():
 
     B.build()
     G.load()
-    X, U = W.make_dataset(4096, chunk=2048)
-    m, meta, hist = W.train(X, U, epochs=40, batch=512, lr=2e-3)
+    X, U = W.make_dataset(16384, chunk=4096)
+    m, meta, hist = W.train(X, U, epochs=100, batch=512, lr=2e-3)
     yield m, hist
     m.close()
 
