@@ -139,7 +139,9 @@ typedef struct {
  * batch entries) gives per-instance N, M, K for an uneven batch.  `cuda_stream`
  * is a cudaStream_t or NULL.  Allocates all device workspace; *out receives the
  * handle (NULL on failure).  Errors: E_ARG (bad sizes, modes, K odd with
- * antithetic sampling, chain M outside 2..17), E_CUDA (no GPU), E_NOMEM. */
+ * antithetic sampling, chain M outside 2..65, one-sided sampling with M > 17), E_CUDA (no
+ * GPU), E_NOMEM.  Chains of up to 17 masses roll out one thread per sample; longer
+ * chains (up to 65 masses) use a group of 4 or 8 lanes per sample. */
 gnmppi_status gnmppi_create(const gnmppi_problem* p, int32_t batch, const gnmppi_instance_shape* shapes,
                             void* cuda_stream, gnmppi_t* out);
 

@@ -111,6 +111,11 @@ static gnmppi_status dalloc(gnmppi_t h, P** ptr, size_t bytes) {
 }
 
 static bool get_launchers(int prec, int dyn, int key, Launchers* o) {
+  if (dyn == kChain && key > kMaxChainF) {
+    if (prec == kFP64) return group_launchers_f64(key, o);
+    if (prec == kFP32) return group_launchers_f32(key, o);
+    return group_launchers_bf16(key, o);
+  }
   if (prec == kFP64) return launchers_f64(dyn, key, o);
   if (prec == kFP32) return launchers_f32(dyn, key, o);
   return launchers_bf16(dyn, key, o);
@@ -146,8 +151,11 @@ static gnmppi_status validate(const gnmppi_problem* p, int32_t batch, const gnmp
     if (N < 1 || N > 100000) return fail(nullptr, GNMPPI_E_ARG, "instance %d: N must be in 1..100000", b);
     if (K < 1 || (p->antithetic && (K % 2 != 0 || K < 2)))
       return fail(nullptr, GNMPPI_E_ARG, "instance %d: K must be >= 1 (even and >= 2 with antithetic pairs)", b);
-    if (p->dynamics == GNMPPI_DYN_CHAIN && (M < 2 || M > kMaxChainF + 1))
-      return fail(nullptr, GNMPPI_E_ARG, "instance %d: chain M must be in 2..%d", b, kMaxChainF + 1);
+    if (p->dynamics == GNMPPI_DYN_CHAIN && (M < 2 || M > kMaxChainGroupF + 1))
+      return fail(nullptr, GNMPPI_E_ARG, "instance %d: chain M must be in 2..%d", b, kMaxChainGroupF + 1);
+    if (p->dynamics == GNMPPI_DYN_CHAIN && M > kMaxChainF + 1 && !p->antithetic)
+      return fail(nullptr, GNMPPI_E_ARG, "instance %d: chains of more than %d masses need antithetic sampling", b,
+                  kMaxChainF + 1);
     if (K > (1 << 26)) return fail(nullptr, GNMPPI_E_ARG, "instance %d: K too large", b);
   }
   return GNMPPI_OK;
@@ -328,7 +336,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     }
     Group& g = h->groups[it->second];
     g.insts.push_back(b);
-    const int per = anti ? kPairsPerBlock : kSamplesPerBlock;
+    const int per = g.fn.pairs_per_block ? g.fn.pairs_per_block : (anti ? kPairsPerBlock : kSamplesPerBlock);
     for (int c = 0; c < (d.Kp + per - 1) / per; ++c) g.bmap.push_back(make_int2(b, c));
     g.smem = std::max(g.smem, (int)(h->szT * (2 * d.n + d.nR + d.nref)));
   }

@@ -14,6 +14,7 @@ constexpr int kSamplesPerBlock = 128;  // one-sided samples per rollout CTA
 constexpr int kPadK = 64;            // sample-dimension padding of dR / W rows
 constexpr int kMaxL = 32;            // largest line-search set
 constexpr int kMaxChainF = 16;       // free masses handled by the thread-per-rollout chain kernels
+constexpr int kMaxChainGroupF = 64;  // free masses handled by the group-per-rollout chain kernels
 
 enum Dyn { kPendulum = 0, kChain = 1, kLinear = 2 };
 enum Prec { kFP64 = 0, kFP32 = 1, kBF16 = 2 };

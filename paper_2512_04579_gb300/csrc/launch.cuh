@@ -8,14 +8,20 @@ namespace gnm {
 struct Launchers {
   cudaError_t (*prepare)(int smem);  // opt the sample kernel into `smem` bytes of shared memory
   void (*samples)(const RollArgs&, int nblocks, int smem, cudaStream_t);
-  void (*line)(const RollArgs&, int nthreads, cudaStream_t);
-  void (*cost64)(const RollArgs&, int nthreads, cudaStream_t);
+  void (*line)(const RollArgs&, int ncand_total, cudaStream_t);   // one rollout per candidate
+  void (*cost64)(const RollArgs&, int ncand_total, cudaStream_t);
+  int pairs_per_block = 0;     // antithetic pairs per sample CTA (0: use the thread-per-rollout defaults)
+  int antithetic_only = 0;     // group kernels support antithetic sampling only
 };
 
 // key: chain -> free masses F; linear -> nx * 16 + nu; pendulum -> 0.
 bool launchers_f64(int dyn, int key, Launchers* out);
 bool launchers_f32(int dyn, int key, Launchers* out);
 bool launchers_bf16(int dyn, int key, Launchers* out);
+// chains of 17..64 free masses: a group of 4 or 8 lanes per rollout
+bool group_launchers_f64(int F, Launchers* out);
+bool group_launchers_f32(int F, Launchers* out);
+bool group_launchers_bf16(int F, Launchers* out);
 
 template <class Model, typename T, typename S>
 void launch_samples(const RollArgs& a, int nb, int smem, cudaStream_t s) {

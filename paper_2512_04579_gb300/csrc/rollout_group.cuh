@@ -1,0 +1,345 @@
+// rollout_group.cuh -- chain rollouts with a group of G lanes per rollout, for
+// chains too long for one thread's registers (F = M - 1 free masses up to
+// G * FL).  Lane l of a group owns masses l*FL + 1 .. l*FL + FL (1-based;
+// masses beyond F are inert placeholders with zero state).  Per right-hand
+// side evaluation a lane needs the position of the mass just before its first
+// one (one shuffle up) and the force of the link just after its last one (one
+// shuffle down); shuffles are width-G so groups never mix.  The two rollouts
+// of an antithetic pair are two adjacent groups (partner lane = lane ^ G).
+// Same outputs as k_samples / k_line (rollout.cuh): dR, W, sample costs and
+// e = dR . r; line-search residuals and costs.
+#pragma once
+#include "rollout.cuh"
+
+namespace gnm {
+
+template <typename T, int FL, int G>
+struct ChainGroup {
+  static constexpr int NXL = 4 * FL;  // lane-local state: p (2FL), v (2FL)
+  T mass_inv, k, k3, c, g, l0, h, h2, h6;
+  int F, lg;
+  unsigned mask;  // lanes that execute this group's shuffles together
+  const T* pref;  // target positions: global row indexed (pref_local false) or lane-local (2FL)
+  bool pref_local;
+  __device__ ChainGroup(const Consts& cs, int F_, int lg_, unsigned mask_)
+      : F(F_), lg(lg_), mask(mask_), pref(nullptr), pref_local(false) {
+    mass_inv = (T)(1.0 / cs.params[0]);
+    k = (T)cs.params[1];
+    k3 = (T)cs.params[2];
+    c = (T)cs.params[3];
+    g = (T)cs.params[4];
+    l0 = (T)(1.0 / (double)F_);
+    h = (T)cs.dt;
+    h2 = (T)(0.5 * cs.dt);
+    h6 = (T)(cs.dt / 6.0);
+  }
+  __device__ __forceinline__ int mass(int j) const { return lg * FL + j + 1; }  // 1-based global index
+  __device__ __forceinline__ void accel(const T* s, const T* u, T* acc) const {
+    const T* v = s + 2 * FL;
+    // position of the mass before this lane's first one (origin for lane 0)
+    T pxp = __shfl_up_sync(mask, s[2 * (FL - 1)], 1, G);
+    T pyp = __shfl_up_sync(mask, s[2 * (FL - 1) + 1], 1, G);
+    if (lg == 0) pxp = pyp = (T)0;
+    T fx[FL], fy[FL];
+#pragma unroll
+    for (int j = 0; j < FL; ++j) {
+      const T px0 = (j == 0) ? pxp : s[2 * (j - 1)];
+      const T py0 = (j == 0) ? pyp : s[2 * (j - 1) + 1];
+      const T dx = s[2 * j] - px0;
+      const T dy = s[2 * j + 1] - py0;
+      const bool real = mass(j) <= F;
+      const T q = real ? dx * dx + dy * dy : (T)1;
+      if constexpr (sizeof(T) == 4) {
+        const T rinv = rsqrtf(q);
+        const T dd = q * rinv - l0;
+        const T fr = real ? (k * dd + k3 * dd * dd * dd) * rinv : (T)0;
+        fx[j] = fr * dx;
+        fy[j] = fr * dy;
+      } else {
+        const T len = sqrt(q);
+        const T dd = len - l0;
+        const T fm = real ? k * dd + k3 * dd * dd * dd : (T)0;
+        fx[j] = fm * dx / len;
+        fy[j] = fm * dy / len;
+      }
+    }
+    // force of the link after this lane's last mass (first link of the next lane)
+    T fxn = __shfl_down_sync(mask, fx[0], 1, G);
+    T fyn = __shfl_down_sync(mask, fy[0], 1, G);
+    if (lg == G - 1) fxn = fyn = (T)0;
+#pragma unroll
+    for (int j = 0; j < FL; ++j) {
+      const T nx = (j + 1 < FL) ? fx[j + 1] : fxn;
+      const T ny = (j + 1 < FL) ? fy[j + 1] : fyn;
+      T ax = -c * v[2 * j] - fx[j] + nx;
+      T ay = -c * v[2 * j + 1] - fy[j] + ny;
+      if (mass(j) == F) {
+        ax += u[0];
+        ay += u[1];
+      }
+      const bool real = mass(j) <= F;
+      acc[2 * j] = real ? ax * mass_inv : (T)0;
+      acc[2 * j + 1] = real ? ay * mass_inv - g : (T)0;
+    }
+  }
+  __device__ __forceinline__ void step(T* x, const T* u) const {
+    constexpr int H = 2 * FL;
+    T a[NXL], t[NXL], acc[H];
+    accel(x, u, acc);
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      a[i] = x[H + i];
+      a[H + i] = acc[i];
+      t[i] = x[i] + h2 * x[H + i];
+      t[H + i] = x[H + i] + h2 * acc[i];
+    }
+    accel(t, u, acc);
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      a[i] = a[i] + (T)2 * t[H + i];
+      a[H + i] = a[H + i] + (T)2 * acc[i];
+      t[i] = x[i] + h2 * t[H + i];
+      t[H + i] = x[H + i] + h2 * acc[i];
+    }
+    accel(t, u, acc);
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      a[i] = a[i] + (T)2 * t[H + i];
+      a[H + i] = a[H + i] + (T)2 * acc[i];
+      t[i] = x[i] + h * t[H + i];
+      t[H + i] = x[H + i] + h * acc[i];
+    }
+    accel(t, u, acc);
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      x[i] = x[i] + h6 * (a[i] + t[H + i]);
+      x[H + i] = x[H + i] + h6 * (a[H + i] + acc[i]);
+    }
+  }
+  // Residual rows of this lane at a stage (its masses' position errors; lane
+  // 0 also the two control rows at 2F, 2F+1) or at the terminal state.  Every
+  // lane calls emit(row, value, valid) the same 2 FL + 2 times, so emitters
+  // may shuffle; slots that belong to no row of this lane come with valid false.
+  template <class E>
+  __device__ __forceinline__ void rows(const T* x, const T* u, bool terminal, E& emit) const {
+#pragma unroll
+    for (int j = 0; j < FL; ++j) {
+      const int i = mass(j);
+      const bool real = i <= F;
+      const int r0 = real ? 2 * (i - 1) : 0;
+      const T px = pref_local ? pref[2 * j] : (real ? pref[r0] : (T)0);
+      const T py = pref_local ? pref[2 * j + 1] : (real ? pref[r0 + 1] : (T)0);
+      emit(r0, x[2 * j] - px, real);
+      emit(r0 + 1, x[2 * j + 1] - py, real);
+    }
+    const bool urow = !terminal && lg == 0;
+    emit(2 * F, (T)0.1 * u[0], urow);
+    emit(2 * F + 1, (T)0.1 * u[1], urow);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int G, unsigned mask) {
+  for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
+// k_samples for groups.  Every lane of a group emits its rows in the same
+// order and the partner group emits the same rows, so the difference is taken
+// row by row with one xor-shuffle per emitted row.
+template <typename T, typename S, int FL, int G>
+__global__ void __launch_bounds__(256) k_samples_group(RollArgs a) {
+  constexpr int PAIRS = 256 / (2 * G);
+  const int2 bm = a.bmap[blockIdx.x];
+  const InstDesc I = a.inst[bm.x];
+  if (a.st[bm.x].status != 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sU = reinterpret_cast<T*>(smem_raw);
+  T* sS = sU + I.n;
+  T* sR = sS + I.n;
+  T* sRef = sR + I.nR;
+  const T* rg = reinterpret_cast<const T*>(a.r) + I.o_R;
+  for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+    sU[j] = (T)a.U[I.o_U + j];
+    sS[j] = (T)a.s[I.o_U + j];
+  }
+  for (int j = threadIdx.x; j < I.nR; j += blockDim.x) sR[j] = rg[j];
+  for (int j = threadIdx.x; j < 2 * I.F; j += blockDim.x) sRef[j] = (T)a.xref[I.o_xref + j];
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const int lg = lane & (G - 1);
+  const bool plus = (lane & G) == 0;
+  const int m = bm.y * PAIRS + (int)(threadIdx.x / (2 * G));
+  const bool active = m < I.Kp;
+  const T sign = plus ? (T)1 : (T)-1;
+  // every lane of a block works on one instance with one horizon, so whole
+  // warps stay converged and shuffles use the full mask
+  ChainGroup<T, FL, G> md(a.cs, I.F, lg, 0xffffffffu);
+  md.pref = sRef;
+  T x[4 * FL];
+#pragma unroll
+  for (int j = 0; j < FL; ++j) {
+    const int i = md.mass(j);
+    const bool real = i <= I.F;
+    x[2 * j] = real ? (T)a.x0[I.o_x0 + 2 * (i - 1)] : (T)0;
+    x[2 * j + 1] = real ? (T)a.x0[I.o_x0 + 2 * (i - 1) + 1] : (T)0;
+    x[2 * FL + 2 * j] = real ? (T)a.x0[I.o_x0 + 2 * I.F + 2 * (i - 1)] : (T)0;
+    x[2 * FL + 2 * j + 1] = real ? (T)a.x0[I.o_x0 + 2 * I.F + 2 * (i - 1) + 1] : (T)0;
+  }
+  S* dR = reinterpret_cast<S*>(a.dR) + I.o_dR;
+  S* Wm = reinterpret_cast<S*>(a.W) + I.o_W;
+  Acc<T> cost, eacc;
+  const uint32_t mm = active ? (uint32_t)m : 0u;
+  const int rps = 2 * I.F + 2;
+  // per-row difference emitter
+  struct Em {
+    S* dR;
+    const T* r;
+    int ldK, m, base;
+    bool active, plus;
+    T sign, csum;
+    Acc<T>* eacc;
+    __device__ __forceinline__ void operator()(int row_local, T v, bool valid) {
+      const T vo = __shfl_xor_sync(0xffffffffu, v, G);
+      if (!valid) return;
+      csum += v * v;
+      if (plus) {
+        const int row = base + row_local;
+        const T d = (v - vo) * (T)0.5;
+        if (active) dR[(int64_t)row * ldK + m] = to_store<S>(d);
+        eacc->add(d * r[row]);
+      }
+    }
+  } em{dR, sR, I.ldK, m, 0, active, plus, sign, (T)0, &eacc};
+  for (int k = 0; k < I.N; ++k) {
+    T z0, z1;
+    box_muller(noise_words(a.cs.seed, (uint32_t)bm.x, a.it, mm, (uint32_t)k), z0, z1);
+    const T w0 = sS[2 * k] * z0, w1 = sS[2 * k + 1] * z1;
+    const T u[2] = {sU[2 * k] + sign * w0, sU[2 * k + 1] + sign * w1};
+    if (active && plus && lg == 0) {
+      Wm[(int64_t)(2 * k) * I.ldK + m] = to_store<S>(w0);
+      Wm[(int64_t)(2 * k + 1) * I.ldK + m] = to_store<S>(w1);
+    }
+    em.base = k * rps;
+    em.csum = (T)0;
+    md.rows(x, u, false, em);
+    cost.add(em.csum);
+    md.step(x, u);
+  }
+  em.base = I.N * rps;
+  em.csum = (T)0;
+  {
+    const T u0[2] = {(T)0, (T)0};
+    md.rows(x, u0, true, em);
+  }
+  cost.add(em.csum);
+  // reduce over the group; exchange with the partner group
+  const double Cself = 0.5 * group_sum(cost.value(), G, 0xffffffffu);
+  double ev = group_sum(eacc.value(), G, 0xffffffffu);
+  const double Cother = __shfl_xor_sync(0xffffffffu, Cself, G);
+  const double evo = __shfl_xor_sync(0xffffffffu, ev, G);  // every lane shuffles
+  ev = plus ? ev : evo;
+  const bool ok = isfinite(Cself) && isfinite(Cother) && isfinite(ev);
+  if (active && lg == 0) {
+    a.C[I.o_C + 2 * m + (plus ? 0 : 1)] = Cself;
+    if (plus) a.e[I.o_C / 2 + m] = ok ? ev : 0.0;
+  }
+  if (active && plus && !ok) {  // dropped pair: its columns leave P and S
+    const int rows = I.N * rps + 2 * I.F;
+    for (int row = lg; row < rows; row += G) dR[(int64_t)row * I.ldK + m] = to_store<S>(0.0f);
+    for (int j = lg; j < I.n; j += G) Wm[(int64_t)j * I.ldK + m] = to_store<S>(0.0f);
+  }
+}
+
+// Line search / nominal / FP64 cost for groups: one group per (instance, candidate).
+template <typename T, int FL, int G>
+__global__ void __launch_bounds__(256) k_line_group(RollArgs a) {
+  const int gid = (int)((blockIdx.x * blockDim.x + threadIdx.x) / G);
+  const int lg = threadIdx.x & (G - 1);
+  const int ncand = a.mode == 0 ? a.ncand : 1;
+  const bool valid = gid < a.count * ncand;
+  const int b = a.list[valid ? gid / ncand : 0];
+  const int j = valid ? gid % ncand : 0;
+  const InstDesc I = a.inst[b];
+  // whole groups leave together (lanes of a group share gid and b)
+  if (!valid) return;
+  if (a.mode != 2 && a.st[b].status != 0) return;
+  double alpha = 0.0;
+  if (a.mode == 0) {
+    alpha = 1.0;
+    for (int q = 0; q < j; ++q) alpha *= a.cs.gamma;
+  }
+  // groups of one warp may run different instances (different horizons):
+  // every shuffle is confined to this group's lanes
+  const unsigned gmask = ((G == 32) ? 0xffffffffu : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
+  ChainGroup<T, FL, G> md(a.cs, I.F, lg, gmask);
+  T ref[2 * FL];
+#pragma unroll
+  for (int q = 0; q < FL; ++q) {
+    const int i = md.mass(q);
+    const bool real = i <= I.F;
+    ref[2 * q] = real ? (T)a.xref[I.o_xref + 2 * (i - 1)] : (T)0;
+    ref[2 * q + 1] = real ? (T)a.xref[I.o_xref + 2 * (i - 1) + 1] : (T)0;
+  }
+  md.pref = ref;
+  md.pref_local = true;
+  T x[4 * FL];
+#pragma unroll
+  for (int q = 0; q < FL; ++q) {
+    const int i = md.mass(q);
+    const bool real = i <= I.F;
+    x[2 * q] = real ? (T)a.x0[I.o_x0 + 2 * (i - 1)] : (T)0;
+    x[2 * q + 1] = real ? (T)a.x0[I.o_x0 + 2 * (i - 1) + 1] : (T)0;
+    x[2 * FL + 2 * q] = real ? (T)a.x0[I.o_x0 + 2 * I.F + 2 * (i - 1)] : (T)0;
+    x[2 * FL + 2 * q + 1] = real ? (T)a.x0[I.o_x0 + 2 * I.F + 2 * (i - 1) + 1] : (T)0;
+  }
+  T* out = nullptr;
+  if (a.mode == 0) out = reinterpret_cast<T*>(a.RL) + I.o_RL + (int64_t)j * I.nR;
+  if (a.mode == 1) out = const_cast<T*>(reinterpret_cast<const T*>(a.r)) + I.o_R;
+  struct Em {
+    T* out;
+    int base;
+    T csum;
+    __device__ __forceinline__ void operator()(int row_local, T v, bool valid) {
+      if (!valid) return;
+      csum += v * v;
+      if (out) out[base + row_local] = v;
+    }
+  } em{out, 0, (T)0};
+  Acc<T> cost;
+  const double* U = a.U + I.o_U;
+  const double* D = a.delta + I.o_U;
+  const int rps = 2 * I.F + 2;
+  for (int k = 0; k < I.N; ++k) {
+    T u[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int q = 2 * k + c;
+      u[c] = (a.mode == 0) ? (T)(U[q] + alpha * D[q]) : (T)U[q];
+    }
+    em.base = k * rps;
+    em.csum = (T)0;
+    md.rows(x, u, false, em);
+    cost.add(em.csum);
+    md.step(x, u);
+  }
+  em.base = I.N * rps;
+  em.csum = (T)0;
+  {
+    const T u0[2] = {(T)0, (T)0};
+    md.rows(x, u0, true, em);
+  }
+  cost.add(em.csum);
+  const double C = 0.5 * group_sum(cost.value(), G, gmask);
+  if (lg == 0) {
+    if (a.mode == 0) a.Cl[(int64_t)b * (kMaxL + 1) + j] = C;
+    if (a.mode == 1) {
+      a.st[b].C_nom = C;
+      a.st[b].C_init = C;
+    }
+    if (a.mode == 2) a.Cout[b] = C;
+  }
+}
+
+}  // namespace gnm

@@ -1,0 +1,48 @@
+// Group-per-rollout chain kernels (FP32 rollouts, BF16 storage).
+#include "launch.cuh"
+#include "rollout_group.cuh"
+
+namespace gnm {
+namespace {
+template <typename T, typename S, int FL, int G>
+cudaError_t prep(int smem) {
+  return cudaFuncSetAttribute(k_samples_group<T, S, FL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+template <typename T, typename S, int FL, int G>
+void samp(const RollArgs& a, int nb, int smem, cudaStream_t s) {
+  k_samples_group<T, S, FL, G><<<nb, 256, smem, s>>>(a);
+}
+template <typename T, int FL, int G>
+void line(const RollArgs& a, int ncand_total, cudaStream_t s) {
+  const long lanes = (long)ncand_total * G;
+  if (lanes > 0) k_line_group<T, FL, G><<<(unsigned)((lanes + 255) / 256), 256, 0, s>>>(a);
+}
+template <typename T, typename S, int FL, int G>
+void fill_group(Launchers* o) {
+  o->prepare = &prep<T, S, FL, G>;
+  o->samples = &samp<T, S, FL, G>;
+  o->line = &line<T, FL, G>;
+  o->cost64 = &line<double, FL, G>;
+  o->pairs_per_block = 256 / (2 * G);
+  o->antithetic_only = 1;
+}
+}  // namespace
+
+bool group_launchers_bf16(int F, Launchers* o) {
+  const int G = F <= 32 ? 4 : 8;
+  const int FL = (F + G - 1) / G;
+  if (F < 17 || F > 64) return false;
+  switch (G * 16 + FL) {
+    case 4 * 16 + 5: fill_group<float, __nv_bfloat16, 5, 4>(o); return true;
+    case 4 * 16 + 6: fill_group<float, __nv_bfloat16, 6, 4>(o); return true;
+    case 4 * 16 + 7: fill_group<float, __nv_bfloat16, 7, 4>(o); return true;
+    case 4 * 16 + 8: fill_group<float, __nv_bfloat16, 8, 4>(o); return true;
+    case 8 * 16 + 5: fill_group<float, __nv_bfloat16, 5, 8>(o); return true;
+    case 8 * 16 + 6: fill_group<float, __nv_bfloat16, 6, 8>(o); return true;
+    case 8 * 16 + 7: fill_group<float, __nv_bfloat16, 7, 8>(o); return true;
+    case 8 * 16 + 8: fill_group<float, __nv_bfloat16, 8, 8>(o); return true;
+    default: return false;
+  }
+}
+
+}  // namespace gnm

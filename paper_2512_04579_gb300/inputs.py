@@ -103,3 +103,18 @@ def uneven_batch(seed: int, batch: int, M_range=(4, 16), N_range=(40, 160), K_ch
     N = g.integers(N_range[0], N_range[1] + 1, size=batch)
     K = np.asarray(K_choices)[g.integers(0, len(K_choices), size=batch)]
     return M, N, K
+
+
+def uneven_chain_instances(seed: int, batch: int):
+    """Uneven batch of chain instances: per instance (M, N, K), x0 = rest state
+    + N(0, 0.05^2) and a target rotated by phi ~ U(pi/16, pi/8), each instance
+    from its own Philox stream."""
+    M, N, K = uneven_batch(seed, batch)
+    x0s, tgts = [], []
+    for b in range(batch):
+        g = stream_rng(seed, 1000 + b)
+        phi = g.uniform(PHI_RANGE[0], PHI_RANGE[1])
+        rest = chain_rest_state(int(M[b]))
+        x0s.append(rest + g.normal(0.0, 0.05, size=rest.size))
+        tgts.append(chain_target(int(M[b]), phi))
+    return M, N, K, x0s, tgts

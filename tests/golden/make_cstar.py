@@ -5,6 +5,8 @@ K=2048, 30 iterations, sigma0 0.2, lambda 1e-3):
   chain_m10        targets rotated by phi ~ U(pi/16, pi/8), seed 2512045790 + 1
   chain_m10_fixed  one target (phi = 3 pi / 32), held-out initial states of the
                    warm-start evaluation stream, seed 2512045790 + 3
+  chain_uneven     per-instance M ~ U{4..16}, N ~ U{40..160}, K ~ U{512..4096}
+                   (inputs.uneven_chain_instances), seed 2512045790 + 2
 For each instance b:
   C_gn  = cost after the oracle's 30-iteration GN-MPPI solve (Algorithm 1),
   C*    = cost after polishing that solution with Method A (central-FD GGN,
@@ -43,8 +45,17 @@ def one(args):
     import numpy as np
 
     from oracle import oracle as O
+    from paper_2512_04579_gb300 import inputs as I
 
     b, workload = args
+    if workload == "chain_uneven":
+        seed = I.BASE_SEED + 2
+        Ms, Ns, Ks, x0s, tgts = I.uneven_chain_instances(seed, BATCH)
+        m = O.chain(M=int(Ms[b]), N=int(Ns[b]))
+        opt = O.Options(K=int(Ks[b]), iterations=T, lam=LAM, seed=seed, threads=1)
+        st, U, Uh, Ch, its = O.solve(m, opt, x0s[b], tgts[b], np.zeros(m.n), SIGMA0, inst=b)
+        stA, UA, CA, itA = O.method_a(m, x0s[b], tgts[b], U.copy(), max_iter=300, lam=LAM)
+        return b, Ch[-1], min(CA, Ch[-1])
     seed, x0, tgt = instances(workload, BATCH)
     m = O.chain(M=M, N=N)
     opt = O.Options(K=K, iterations=T, lam=LAM, seed=seed, threads=1)
@@ -65,7 +76,8 @@ if __name__ == "__main__":
     with ctx.Pool(procs) as pool:
         rows = sorted(pool.map(one, [(b, workload) for b in range(BATCH)], chunksize=1))
     out = os.path.join(HERE, f"{workload}_cstar.txt")
-    seed_note = "2512045790+1" if workload == "chain_m10" else "2512045790+3 (fixed target, eval stream)"
+    seed_note = {"chain_m10": "2512045790+1", "chain_m10_fixed": "2512045790+3 (fixed target, eval stream)",
+                 "chain_uneven": "2512045790+2 (per-instance M, N, K)"}[workload]
     with open(out, "w") as f:
         f.write(f"# {workload}: chain M={M} N={N} K={K} T={T} sigma0={SIGMA0} lambda={LAM} seed={seed_note} "
                 f"batch={BATCH}\n")

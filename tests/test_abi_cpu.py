@@ -67,7 +67,10 @@ def test_invalid_problems_are_rejected_before_any_device_call(lib, kw, msg):
 
 def test_chain_mass_count_and_linear_sizes_are_checked(lib):
     with pytest.raises(G.GnmppiError) as ei:
-        G.gnmppi_create(G.chain_problem(M=40, N=10, K=16), 1)
+        G.gnmppi_create(G.chain_problem(M=70, N=10, K=16), 1)
+    assert ei.value.status == G.E_ARG
+    with pytest.raises(G.GnmppiError) as ei:  # group-per-rollout chains need antithetic pairs
+        G.gnmppi_create(G.chain_problem(M=30, N=10, K=16, antithetic=False), 1)
     assert ei.value.status == G.E_ARG
     p = G.linear_problem(np.eye(3), np.ones((3, 1)), np.ones(3), np.ones(1), np.ones(3), N=5, K=16)
     with pytest.raises(G.GnmppiError) as ei:

@@ -309,3 +309,41 @@ def test_tensor_core_contraction_matches_oracle(prec, tol):
     # Gram A = P^T P on the tensor cores (three TF32 passes): its error is that of P
     assert rel(A, P.T @ P) < 2 * tol
     assert np.allclose(A, A.T, rtol=1e-5, atol=1e-5 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("M,N,K", [(20, 15, 200), (40, 10, 96), (65, 6, 64)])
+def test_fp64_group_rollout_chains_per_iteration(M, N, K):
+    """Chains of 19, 39 and 64 free masses: a group of 4 or 8 lanes per rollout
+    (placeholder masses in the last lane for 19 and 39), ragged pair blocks."""
+    seed = 100 + M
+    x0, tgt = I.chain_instances(seed, 1, M)
+    m = O.chain(M=M, N=N)
+    opt = O.Options(K=K, iterations=2, lam=1e-2, seed=seed, threads=8)
+    gp = G.chain_problem(M=M, N=N, K=K, iterations=2, lam=1e-2, sigma0=0.2, seed=seed)
+    per_iteration_parity(m, gp, opt, x0[0], tgt[0], np.zeros(m.n), 0.2, 2)
+
+
+def test_group_rollout_cost_and_uneven_mix():
+    """FP64 cost of long chains and a batch that mixes thread- and group-per-rollout sizes."""
+    seed = 55
+    shapes = [(12, 8, 64), (10, 33, 96), (8, 61, 64)]
+    x0s, tgts = [], []
+    for i, (N, M, K) in enumerate(shapes):
+        x0, tg = I.chain_instances(seed + i, 1, M)
+        x0s.append(x0[0])
+        tgts.append(tg[0])
+    gp = G.chain_problem(M=8, N=12, K=64, iterations=1, lam=1e-2, sigma0=0.2, seed=seed, precision=G.PREC_FP32)
+    s = G.Solver(gp, 3, shapes=shapes)
+    rng = np.random.default_rng(0)
+    Us = [rng.normal(0, 0.3, size=N * 2) for (N, M, K) in shapes]
+    C = s.cost(np.concatenate(x0s), np.concatenate(tgts), np.concatenate(Us))
+    for i, (N, M, K) in enumerate(shapes):
+        assert C[i] == pytest.approx(O.cost(O.chain(M=M, N=N), x0s[i], tgts[i], Us[i]), rel=1e-12)
+    sig = np.concatenate([np.full(N * 2, 0.2) for (N, M, K) in shapes])
+    st, U, rep = s.step(np.concatenate(x0s), np.concatenate(tgts), np.zeros(sum(N * 2 for N, _, _ in shapes)), sig, 0)
+    for i, (N, M, K) in enumerate(shapes):
+        it = O.iteration(O.chain(M=M, N=N), O.Options(K=K, lam=1e-2, seed=seed), x0s[i], tgts[i], np.zeros(N * 2),
+                         0.2, inst=i, it=0)
+        assert rep[i].C_nom == pytest.approx(it.C_nom, rel=TOLRED)
+        np.testing.assert_allclose(s.debug("C", i), it.C_samp, rtol=TOLRED)
+    s.close()
