@@ -33,12 +33,66 @@ GAP = 1e-6
 METRIC = "OCP solves/s to 1e-6 rel. cost gap"
 CSTAR = os.path.join(ROOT, "tests", "golden", "chain_m10_cstar.txt")
 CSTAR_FIXED = os.path.join(ROOT, "tests", "golden", "chain_m10_fixed_cstar.txt")
+CSTAR_UNEVEN = os.path.join(ROOT, "tests", "golden", "chain_uneven_cstar.txt")
 WORKLOAD = "chain M=10 N=100 nu=2 K=2048 T=30 sigma0=0.2 lambda=1e-3"
 
 
 def load_cstar(path=CSTAR):
     rows = np.loadtxt(path, comments="#")
     return rows[:, 0].astype(int), rows[:, 1], rows[:, 2]
+
+
+def uneven_arm(args, dev, stream):
+    """The uneven batch: 1024 chain instances with M ~ U{4..16}, N ~ U{40..160},
+    K ~ U{512..4096} in one handle and one CUDA graph per solve, FP32 rollouts,
+    BF16 contraction, FP64 Cholesky; solved against the oracle's optima."""
+    import torch
+
+    from paper_2512_04579_gb300 import gnmppi as G
+    from paper_2512_04579_gb300 import inputs as I
+
+    seed = I.BASE_SEED + 2
+    B = 1024
+    Ms, Ns, Ks, x0s, tgts = I.uneven_chain_instances(seed, B)
+    shapes = [(int(Ns[b]), int(Ms[b]), int(Ks[b])) for b in range(B)]
+    prob = G.chain_problem(M=int(Ms[0]), N=int(Ns[0]), K=int(Ks[0]), iterations=T, lam=LAM, sigma0=SIGMA0, seed=seed,
+                           precision=G.PREC_BF16)
+    h = G.gnmppi_create(prob, B, shapes, stream.cuda_stream)
+    dx = torch.tensor(np.concatenate(x0s), dtype=torch.float64, device=dev)
+    dt = torch.tensor(np.concatenate(tgts), dtype=torch.float64, device=dev)
+    nU = int(sum(2 * n for n in Ns))
+    dU = torch.zeros(nU, dtype=torch.float64, device=dev)
+
+    def once():
+        dU.zero_()
+        G.gnmppi_solve(h, G.MEM_DEVICE, dx, dt, dU, None)
+
+    for _ in range(max(1, args.warmup)):
+        once()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        once()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    C = torch.empty(B, dtype=torch.float64, device=dev)
+    G.gnmppi_cost(h, G.MEM_DEVICE, dx, dt, dU, C)
+    phases = G.gnmppi_phase_times(h, T)
+    G.gnmppi_destroy(h)
+    out = {"workload": "%d chain instances, M~U{4..16}, N~U{40..160}, K~U{512,1024,2048,4096}, BF16 contraction" % B,
+           "ms_per_batch": ms, "instances_per_s": B / (ms / 1e3), "phases_ms_per_iteration": phases}
+    if os.path.exists(CSTAR_UNEVEN):
+        _, _, Cs = load_cstar(CSTAR_UNEVEN)
+        g = (C.cpu().numpy()[: len(Cs)] - Cs) / Cs
+        solved = int(np.sum(g <= GAP))
+        out.update({"solved": solved, "checked": len(Cs), "gap_median": float(np.median(g)),
+                    "solves_per_s": solved / len(Cs) * B / (ms / 1e3)})
+    else:
+        out["solved"] = None
+    return out
 
 
 def learned_arm(args, dev, stream):
@@ -327,6 +381,8 @@ def run_gnmppi(args):
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
     }
     out["learned"] = learned_arm(args, dev, stream)
+    if not args.no_uneven:
+        out["uneven"] = uneven_arm(args, dev, stream)
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(out))
@@ -392,6 +448,7 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="instances (default: every instance with a stored C*)")
     ap.add_argument("--plain", type=int, default=8, help="instances for the one-at-a-time plain arm")
     ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch arm")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -347,3 +347,25 @@ def test_group_rollout_cost_and_uneven_mix():
         assert rep[i].C_nom == pytest.approx(it.C_nom, rel=TOLRED)
         np.testing.assert_allclose(s.debug("C", i), it.C_samp, rtol=TOLRED)
     s.close()
+
+
+def test_bf16_long_chain_full_horizon_iteration():
+    """The high-dimensional sweep's size: M = 64 (nx = 252), N = 200 (n = 400),
+    nR = 25726, K = 4096, BF16 contraction, one iteration against the oracle:
+    every sample cost within 1e-4 (checked on all 4096), nominal cost, and a
+    step that lowers the cost like the oracle's."""
+    seed = 64
+    M, N, K = 64, 200, 4096
+    x0, tgt = I.chain_instances(seed, 1, M)
+    m = O.chain(M=M, N=N)
+    it = O.iteration(m, O.Options(K=K, lam=1e-3, seed=seed, threads=16), x0[0], tgt[0], np.zeros(m.n), 0.2)
+    gp = G.chain_problem(M=M, N=N, K=K, iterations=1, lam=1e-3, sigma0=0.2, seed=seed, precision=G.PREC_BF16)
+    s = G.Solver(gp, 1)
+    st, U, rep = s.step(x0[0], tgt[0], np.zeros(m.n), np.full(m.n, 0.2), 0)
+    Cs = s.debug("C")
+    s.close()
+    assert st == 0
+    assert rep[0].C_nom == pytest.approx(it.C_nom, rel=TOLRED)
+    np.testing.assert_allclose(Cs, it.C_samp, rtol=TOLRED)
+    assert rep[0].C_new < rep[0].C_nom and it.C_new < it.C_nom
+    assert rep[0].C_new == pytest.approx(it.C_new, rel=1e-2)
