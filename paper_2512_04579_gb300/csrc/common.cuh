@@ -311,6 +311,104 @@ struct Chain {
   }
 };
 
+// FP32 chain on paired FP32 instructions: a mass's position, velocity and
+// acceleration are float2, updated with FFMA2 / FADD2 / FMUL2 (sm_100+); 1/m
+// is folded into the spring, damping and control constants.  The state array
+// keeps the scalar layout [p_1..p_F, v_1..v_F] (x, y interleaved) and must be
+// 8-byte aligned.
+template <int F>
+struct Chain<float, F> {
+  static constexpr int NX = 4 * F, NU = 2, RPS = 2 * F + 2, RT = 2 * F;
+  float mass_inv, k, k3, l0, h, h2, h6, km, k3m;
+  float2 cneg, grav, two, hh2, hh, hh6, mneg1;
+  const float* pref;
+  __device__ Chain(const Consts& cs) {
+    mass_inv = (float)(1.0 / cs.params[0]);
+    k = (float)cs.params[1];
+    k3 = (float)cs.params[2];
+    km = (float)(cs.params[1] / cs.params[0]);
+    k3m = (float)(cs.params[2] / cs.params[0]);
+    const float cm = (float)(-cs.params[3] / cs.params[0]);
+    cneg = make_float2(cm, cm);
+    grav = make_float2(0.f, (float)(-cs.params[4]));
+    l0 = (float)(1.0 / (double)F);
+    h = (float)cs.dt;
+    h2 = (float)(0.5 * cs.dt);
+    h6 = (float)(cs.dt / 6.0);
+    two = make_float2(2.f, 2.f);
+    hh2 = make_float2(h2, h2);
+    hh = make_float2(h, h);
+    hh6 = make_float2(h6, h6);
+    mneg1 = make_float2(-1.f, -1.f);
+    pref = nullptr;
+  }
+  // acc = (-c v + link forces + u on the last mass) / m - g y
+  __device__ __forceinline__ void accel(const float2* p, const float2* v, float2 um, float2* acc) const {
+#pragma unroll
+    for (int i = 0; i < F; ++i) acc[i] = __ffma2_rn(v[i], cneg, grav);
+    acc[F - 1] = __fadd2_rn(acc[F - 1], um);
+#pragma unroll
+    for (int i = 0; i < F; ++i) {
+      const float2 d = (i == 0) ? p[0] : __ffma2_rn(p[i - 1], mneg1, p[i]);
+      const float q = fmaf(d.x, d.x, d.y * d.y);
+      const float rinv = rsqrtf(q);
+      const float dd = fmaf(q, rinv, -l0);
+      const float fr = fmaf(k3m * dd, dd, km) * dd * rinv;  // (k d + k3 d^3) / (m |d|)
+      const float2 f = __fmul2_rn(make_float2(fr, fr), d);
+      acc[i] = __ffma2_rn(f, mneg1, acc[i]);
+      if (i > 0) acc[i - 1] = __fadd2_rn(acc[i - 1], f);
+    }
+  }
+  __device__ __forceinline__ void step(float* xs, const float* u) const {
+    float2* p = reinterpret_cast<float2*>(xs);
+    float2* v = p + F;
+    const float2 um = make_float2(u[0] * mass_inv, u[1] * mass_inv);
+    float2 ap[F], av[F], tp[F], tv[F], acc[F];
+    accel(p, v, um, acc);
+#pragma unroll
+    for (int i = 0; i < F; ++i) {
+      ap[i] = v[i];
+      av[i] = acc[i];
+      tp[i] = __ffma2_rn(hh2, v[i], p[i]);
+      tv[i] = __ffma2_rn(hh2, acc[i], v[i]);
+    }
+    accel(tp, tv, um, acc);
+#pragma unroll
+    for (int i = 0; i < F; ++i) {
+      ap[i] = __ffma2_rn(two, tv[i], ap[i]);
+      av[i] = __ffma2_rn(two, acc[i], av[i]);
+      tp[i] = __ffma2_rn(hh2, tv[i], p[i]);
+      tv[i] = __ffma2_rn(hh2, acc[i], v[i]);
+    }
+    accel(tp, tv, um, acc);
+#pragma unroll
+    for (int i = 0; i < F; ++i) {
+      ap[i] = __ffma2_rn(two, tv[i], ap[i]);
+      av[i] = __ffma2_rn(two, acc[i], av[i]);
+      tp[i] = __ffma2_rn(hh, tv[i], p[i]);
+      tv[i] = __ffma2_rn(hh, acc[i], v[i]);
+    }
+    accel(tp, tv, um, acc);
+#pragma unroll
+    for (int i = 0; i < F; ++i) {
+      p[i] = __ffma2_rn(hh6, __fadd2_rn(ap[i], tv[i]), p[i]);
+      v[i] = __ffma2_rn(hh6, __fadd2_rn(av[i], acc[i]), v[i]);
+    }
+  }
+  template <class E>
+  __device__ __forceinline__ void stage(const float* x, const float* u, E& emit) const {
+#pragma unroll
+    for (int i = 0; i < 2 * F; ++i) emit(i, x[i] - pref[i]);
+    emit(2 * F, 0.1f * u[0]);
+    emit(2 * F + 1, 0.1f * u[1]);
+  }
+  template <class E>
+  __device__ __forceinline__ void terminal(const float* x, E& emit) const {
+#pragma unroll
+    for (int i = 0; i < 2 * F; ++i) emit(i, x[i] - pref[i]);
+  }
+};
+
 // Discrete linear model x+ = A x + B u with diagonal residual weights.
 template <typename T, int NXv, int NUv>
 struct Linear {

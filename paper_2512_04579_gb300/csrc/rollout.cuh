@@ -65,29 +65,30 @@ struct StageSum {
 
 // Emitter for the sample kernel: antithetic difference across the pair lanes,
 // dR / e written by the lane whose parity matches the row.
+// Emitter for the sample kernel: antithetic difference across the pair lanes,
+// dR written and e = dR . r accumulated by the lane whose parity matches the
+// row.  csum and esum are plain per-stage partial sums, folded into the
+// compensated totals once per stage; dR addresses advance by one row of ldK.
 template <typename T, typename S, bool ANTI>
 struct SampleEmit {
-  S* dR;
-  const T* r;
-  int ldK, m, base, par;
+  S* col;        // this sample's column of dR at the stage's first row
+  const T* r;    // nominal residual at the stage's first row
+  int ldK, par;
   bool active;
-  T sign;
-  T csum;
-  Acc<T>* eacc;
+  T sign, csum, esum;
   __device__ __forceinline__ void operator()(int i, T v) {
     csum += v * v;
-    const int row = base + i;
     if (ANTI) {
       const T vo = __shfl_xor_sync(0xffffffffu, v, 1);
-      if (par == (row & 1)) {
+      if (par == (i & 1)) {
         const T d = sign * (v - vo) * (T)0.5;
-        if (active) dR[(int64_t)row * ldK + m] = to_store<S>(d);
-        eacc->add(d * r[row]);
+        if (active) col[(int64_t)i * ldK] = to_store<S>(d);
+        esum += d * r[i];
       }
     } else {
-      const T d = v - r[row];
-      if (active) dR[(int64_t)row * ldK + m] = to_store<S>(d);
-      eacc->add(d * r[row]);
+      const T d = v - r[i];
+      if (active) col[(int64_t)i * ldK] = to_store<S>(d);
+      esum += d * r[i];
     }
   }
 };
@@ -122,42 +123,76 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
 
   Model md(a.cs);
   bind_model(md, (const T*)sRef);
-  T x[NX];
+  alignas(16) T x[NX];
 #pragma unroll
   for (int i = 0; i < NX; ++i) x[i] = (T)a.x0[I.o_x0 + i];
 
-  S* dR = reinterpret_cast<S*>(a.dR) + I.o_dR;
+  S* dR = reinterpret_cast<S*>(a.dR) + I.o_dR + m;  // this sample's column
   S* Wm = reinterpret_cast<S*>(a.W) + I.o_W;
-  const T* r = sR;
   Acc<T> cost, eacc;
-  SampleEmit<T, S, ANTI> em{dR, r, I.ldK, m, 0, par, active, sign, (T)0, &eacc};
+  SampleEmit<T, S, ANTI> em{dR, sR, I.ldK, par, active, sign, (T)0, (T)0};
   const uint32_t mm = active ? (uint32_t)m : 0u;
+  const int64_t stage_stride = (int64_t)Model::RPS * I.ldK;
+  // Two controls per step (nu = 2) with antithetic pairs: the normals of steps
+  // k and k+1 come from Philox calls q = k and q = k + 1; each lane of the pair
+  // draws one of the two and the partner's arrives by shuffle.
+  constexpr bool SHARE = ANTI && NU == 2;
   int qc = -1;
-  T z0 = (T)0, z1 = (T)0;
+  T z0 = (T)0, z1 = (T)0, y0 = (T)0, y1 = (T)0;
   for (int k = 0; k < I.N; ++k) {
     T u[NU];
-#pragma unroll
-    for (int c = 0; c < NU; ++c) {
-      const int j = k * NU + c;
-      const int q = j >> 1;
-      if (q != qc) {
-        box_muller(noise_words(a.cs.seed, (uint32_t)bm.x, a.it, mm, (uint32_t)q), z0, z1);
-        qc = q;
+    if (SHARE) {
+      if ((k & 1) == 0) {
+        T a0, a1;
+        box_muller(noise_words(a.cs.seed, (uint32_t)bm.x, a.it, mm, (uint32_t)(k + par)), a0, a1);
+        const T b0 = __shfl_xor_sync(0xffffffffu, a0, 1);
+        const T b1 = __shfl_xor_sync(0xffffffffu, a1, 1);
+        z0 = par ? b0 : a0;
+        z1 = par ? b1 : a1;
+        y0 = par ? a0 : b0;
+        y1 = par ? a1 : b1;
+      } else {
+        z0 = y0;
+        z1 = y1;
       }
-      const T w = sS[j] * ((j & 1) ? z1 : z0);
-      u[c] = sU[j] + sign * w;
-      if (active && par == (ANTI ? (j & 1) : 0)) Wm[(int64_t)j * I.ldK + m] = to_store<S>(w);
+#pragma unroll
+      for (int c = 0; c < NU; ++c) {
+        const int j = k * NU + c;
+        const T w = sS[j] * (c ? z1 : z0);
+        u[c] = sU[j] + sign * w;
+        if (active && par == c) Wm[(int64_t)j * I.ldK + m] = to_store<S>(w);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NU; ++c) {
+        const int j = k * NU + c;
+        const int q = j >> 1;
+        if (q != qc) {
+          box_muller(noise_words(a.cs.seed, (uint32_t)bm.x, a.it, mm, (uint32_t)q), z0, z1);
+          qc = q;
+        }
+        const T w = sS[j] * ((j & 1) ? z1 : z0);
+        u[c] = sU[j] + sign * w;
+        if (active && par == (ANTI ? (j & 1) : 0)) Wm[(int64_t)j * I.ldK + m] = to_store<S>(w);
+      }
     }
-    em.base = k * Model::RPS;
+    em.col = dR + k * stage_stride;
+    em.r = sR + k * Model::RPS;
     em.csum = (T)0;
+    em.esum = (T)0;
     md.stage(x, u, em);
     cost.add(em.csum);
+    eacc.add(em.esum);
     md.step(x, u);
   }
-  em.base = I.N * Model::RPS;
+  em.col = dR + I.N * stage_stride;
+  em.r = sR + I.N * Model::RPS;
   em.csum = (T)0;
+  em.esum = (T)0;
   md.terminal(x, em);
   cost.add(em.csum);
+  eacc.add(em.esum);
+  dR -= m;
 
   const double Cself = 0.5 * cost.value();
   double ev = eacc.value();
@@ -212,7 +247,7 @@ __global__ void __launch_bounds__(128) k_line(RollArgs a) {
 #pragma unroll
   for (int i = 0; i < RefSize<Model>::value; ++i) ref[i] = (T)a.xref[I.o_xref + i];
   bind_model(md, (const T*)ref);
-  T x[NX];
+  alignas(16) T x[NX];
 #pragma unroll
   for (int i = 0; i < NX; ++i) x[i] = (T)a.x0[I.o_x0 + i];
   T* out = nullptr;
