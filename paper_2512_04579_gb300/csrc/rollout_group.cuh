@@ -138,6 +138,117 @@ struct ChainGroup {
   }
 };
 
+// FP32 group chain on paired FP32 instructions (FFMA2 / FADD2 / FMUL2),
+// 1/m folded into the constants; same interface and layout as above.
+template <int FL, int G>
+struct ChainGroup<float, FL, G> {
+  static constexpr int NXL = 4 * FL;
+  float mass_inv, l0, km, k3m;
+  float2 cneg, grav, two, hh2, hh, hh6, mneg1;
+  int F, lg;
+  unsigned mask;
+  const float* pref;
+  bool pref_local;
+  __device__ ChainGroup(const Consts& cs, int F_, int lg_, unsigned mask_)
+      : F(F_), lg(lg_), mask(mask_), pref(nullptr), pref_local(false) {
+    mass_inv = (float)(1.0 / cs.params[0]);
+    km = (float)(cs.params[1] / cs.params[0]);
+    k3m = (float)(cs.params[2] / cs.params[0]);
+    const float cm = (float)(-cs.params[3] / cs.params[0]);
+    cneg = make_float2(cm, cm);
+    grav = make_float2(0.f, (float)(-cs.params[4]));
+    l0 = (float)(1.0 / (double)F_);
+    const float h = (float)cs.dt, h2 = (float)(0.5 * cs.dt), h6 = (float)(cs.dt / 6.0);
+    two = make_float2(2.f, 2.f);
+    hh2 = make_float2(h2, h2);
+    hh = make_float2(h, h);
+    hh6 = make_float2(h6, h6);
+    mneg1 = make_float2(-1.f, -1.f);
+  }
+  __device__ __forceinline__ int mass(int j) const { return lg * FL + j + 1; }
+  __device__ __forceinline__ void accel(const float2* p, const float2* v, float2 um, float2* acc) const {
+    float2 prev;
+    prev.x = __shfl_up_sync(mask, p[FL - 1].x, 1, G);
+    prev.y = __shfl_up_sync(mask, p[FL - 1].y, 1, G);
+    if (lg == 0) prev = make_float2(0.f, 0.f);
+    float2 f[FL];
+#pragma unroll
+    for (int j = 0; j < FL; ++j) {
+      const float2 d = __ffma2_rn((j == 0) ? prev : p[j - 1], mneg1, p[j]);
+      const bool real = mass(j) <= F;
+      const float q = real ? fmaf(d.x, d.x, d.y * d.y) : 1.f;
+      const float rinv = rsqrtf(q);
+      const float dd = fmaf(q, rinv, -l0);
+      const float fr = real ? fmaf(k3m * dd, dd, km) * dd * rinv : 0.f;
+      f[j] = __fmul2_rn(make_float2(fr, fr), d);
+    }
+    float2 fn;
+    fn.x = __shfl_down_sync(mask, f[0].x, 1, G);
+    fn.y = __shfl_down_sync(mask, f[0].y, 1, G);
+    if (lg == G - 1) fn = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < FL; ++j) {
+      float2 a = __ffma2_rn(v[j], cneg, grav);
+      a = __ffma2_rn(f[j], mneg1, a);
+      a = __fadd2_rn(a, (j + 1 < FL) ? f[j + 1] : fn);
+      if (mass(j) == F) a = __fadd2_rn(a, um);
+      acc[j] = (mass(j) <= F) ? a : make_float2(0.f, 0.f);
+    }
+  }
+  __device__ __forceinline__ void step(float* xs, const float* u) const {
+    float2* p = reinterpret_cast<float2*>(xs);
+    float2* v = p + FL;
+    const float2 um = make_float2(u[0] * mass_inv, u[1] * mass_inv);
+    float2 ap[FL], av[FL], tp[FL], tv[FL], acc[FL];
+    accel(p, v, um, acc);
+#pragma unroll
+    for (int i = 0; i < FL; ++i) {
+      ap[i] = v[i];
+      av[i] = acc[i];
+      tp[i] = __ffma2_rn(hh2, v[i], p[i]);
+      tv[i] = __ffma2_rn(hh2, acc[i], v[i]);
+    }
+    accel(tp, tv, um, acc);
+#pragma unroll
+    for (int i = 0; i < FL; ++i) {
+      ap[i] = __ffma2_rn(two, tv[i], ap[i]);
+      av[i] = __ffma2_rn(two, acc[i], av[i]);
+      tp[i] = __ffma2_rn(hh2, tv[i], p[i]);
+      tv[i] = __ffma2_rn(hh2, acc[i], v[i]);
+    }
+    accel(tp, tv, um, acc);
+#pragma unroll
+    for (int i = 0; i < FL; ++i) {
+      ap[i] = __ffma2_rn(two, tv[i], ap[i]);
+      av[i] = __ffma2_rn(two, acc[i], av[i]);
+      tp[i] = __ffma2_rn(hh, tv[i], p[i]);
+      tv[i] = __ffma2_rn(hh, acc[i], v[i]);
+    }
+    accel(tp, tv, um, acc);
+#pragma unroll
+    for (int i = 0; i < FL; ++i) {
+      p[i] = __ffma2_rn(hh6, __fadd2_rn(ap[i], tv[i]), p[i]);
+      v[i] = __ffma2_rn(hh6, __fadd2_rn(av[i], acc[i]), v[i]);
+    }
+  }
+  template <class E>
+  __device__ __forceinline__ void rows(const float* x, const float* u, bool terminal, E& emit) const {
+#pragma unroll
+    for (int j = 0; j < FL; ++j) {
+      const int i = mass(j);
+      const bool real = i <= F;
+      const int r0 = real ? 2 * (i - 1) : 0;
+      const float px = pref_local ? pref[2 * j] : (real ? pref[r0] : 0.f);
+      const float py = pref_local ? pref[2 * j + 1] : (real ? pref[r0 + 1] : 0.f);
+      emit(r0, x[2 * j] - px, real);
+      emit(r0 + 1, x[2 * j + 1] - py, real);
+    }
+    const bool urow = !terminal && lg == 0;
+    emit(2 * F, 0.1f * u[0], urow);
+    emit(2 * F + 1, 0.1f * u[1], urow);
+  }
+};
+
 template <typename T>
 __device__ __forceinline__ T group_sum(T v, int G, unsigned mask) {
   for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(mask, v, o);
@@ -148,7 +259,7 @@ __device__ __forceinline__ T group_sum(T v, int G, unsigned mask) {
 // order and the partner group emits the same rows, so the difference is taken
 // row by row with one xor-shuffle per emitted row.
 template <typename T, typename S, int FL, int G>
-__global__ void __launch_bounds__(256) k_samples_group(RollArgs a) {
+__global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   constexpr int PAIRS = 256 / (2 * G);
   const int2 bm = a.bmap[blockIdx.x];
   const InstDesc I = a.inst[bm.x];
@@ -177,7 +288,7 @@ __global__ void __launch_bounds__(256) k_samples_group(RollArgs a) {
   // warps stay converged and shuffles use the full mask
   ChainGroup<T, FL, G> md(a.cs, I.F, lg, 0xffffffffu);
   md.pref = sRef;
-  T x[4 * FL];
+  alignas(16) T x[4 * FL];
 #pragma unroll
   for (int j = 0; j < FL; ++j) {
     const int i = md.mass(j);
@@ -212,9 +323,15 @@ __global__ void __launch_bounds__(256) k_samples_group(RollArgs a) {
       }
     }
   } em{dR, sR, I.ldK, m, 0, active, plus, sign, (T)0, &eacc};
+  // The 2G lanes of a pair draw the normals of 2G consecutive steps at once
+  // (lane l of the pair: Philox call q = k + l) and hand them round by shuffle.
+  const int pl = lane & (2 * G - 1);
+  T na0 = (T)0, na1 = (T)0;
   for (int k = 0; k < I.N; ++k) {
-    T z0, z1;
-    box_muller(noise_words(a.cs.seed, (uint32_t)bm.x, a.it, mm, (uint32_t)k), z0, z1);
+    if (k % (2 * G) == 0)
+      box_muller(noise_words(a.cs.seed, (uint32_t)bm.x, a.it, mm, (uint32_t)(k + pl)), na0, na1);
+    const T z0 = __shfl_sync(0xffffffffu, na0, k % (2 * G), 2 * G);
+    const T z1 = __shfl_sync(0xffffffffu, na1, k % (2 * G), 2 * G);
     const T w0 = sS[2 * k] * z0, w1 = sS[2 * k + 1] * z1;
     const T u[2] = {sU[2 * k] + sign * w0, sU[2 * k + 1] + sign * w1};
     if (active && plus && lg == 0) {
@@ -284,7 +401,7 @@ __global__ void __launch_bounds__(256) k_line_group(RollArgs a) {
   }
   md.pref = ref;
   md.pref_local = true;
-  T x[4 * FL];
+  alignas(16) T x[4 * FL];
 #pragma unroll
   for (int q = 0; q < FL; ++q) {
     const int i = md.mass(q);
