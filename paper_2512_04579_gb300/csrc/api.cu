@@ -56,7 +56,8 @@ struct gnmppi_s {
   int ntiles[3] = {0, 0, 0};
   std::vector<Group> groups;
   int* d_all = nullptr;  // 0..batch-1
-  int smem_n_max = 0;
+  std::vector<int> order;  // k_solve instance order
+  int* d_order = nullptr;
   int solve_smem = 0;
   bool use_tc = false;
   TcPlan tc{};
@@ -251,32 +252,23 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     d.o_RL = orl; orl += (int64_t)p.L * d.nR;
     h->desc[b] = d;
   }
-  // k_solve keeps rhs, x, res, 1/diag (4 n_max doubles) and, when it fits, the packed
-  // Cholesky factor (n(n+1)/2 doubles) in shared memory; larger factors live
-  // in a global scratch.
+  // k_solve keeps rhs, x, res, 1/diag and the float split of y (5 n doubles)
+  // in shared memory; the packed factor plus the inverted diagonal blocks,
+  // and the packed copy of the system, live in global scratch (o_L).
   int n_all_max = 0;
   for (auto& d : h->desc) n_all_max = std::max(n_all_max, d.n);
-  int dev = 0, optin = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  cudaFuncAttributes fa{};
-  if (prec == kFP64) CK(cudaFuncGetAttributes(&fa, k_solve<double>));
-  else CK(cudaFuncGetAttributes(&fa, k_solve<float>));
-  const int64_t solve_budget = (int64_t)optin - (int64_t)fa.sharedSizeBytes - 256;
-  int nmax_smem = 0;
-  while (8 * ((int64_t)4 * n_all_max + (int64_t)(nmax_smem + 1) * (nmax_smem + 2) / 2) <= solve_budget) ++nmax_smem;
-  h->smem_n_max = nmax_smem;
-  int n_solve_max = 0;
   for (int b = 0; b < h->batch; ++b) {
-    const InstDesc& d = h->desc[b];
-    if (d.n > nmax_smem) {
-      offL[b] = oL;
-      oL += (int64_t)d.n * (d.n + 1) / 2;
-    } else {
-      n_solve_max = std::max(n_solve_max, d.n);
-    }
+    const int n = h->desc[b].n;
+    offL[b] = oL;
+    oL += (int64_t)n * (n + 1) / 2 + (int64_t)((n + 15) / 16) * 256;
+    oL = (oL + 31) / 32 * 32;  // 256-byte aligned per instance
   }
-  h->solve_smem = (int)(8 * ((int64_t)4 * n_all_max + (int64_t)n_solve_max * (n_solve_max + 1) / 2));
+  h->solve_smem = (int)(8 * (int64_t)5 * n_all_max);
+  // solve order: largest systems first (longest-processing-time scheduling)
+  h->order.resize(h->batch);
+  for (int b = 0; b < h->batch; ++b) h->order[b] = b;
+  std::stable_sort(h->order.begin(), h->order.end(),
+                   [&](int x, int y) { return h->desc[x].n > h->desc[y].n; });
   h->n_x0 = oX; h->n_xref = oR; h->n_U = oU; h->n_dR = odR; h->n_W = oW; h->n_C = oC; h->n_P = oP;
   h->n_nn = onn; h->n_R = orr; h->n_RL = orl; h->n_L = oL;
 
@@ -297,7 +289,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   AL(h->d_C, 8 * h->n_C);
   AL(h->d_A, 8 * h->n_nn);
   AL(h->d_S2, 8 * h->n_nn);
-  AL(h->d_H, 8 * h->n_nn);
+  AL(h->d_H, 8 * h->n_L);
   AL(h->d_Cl, 8 * (int64_t)h->batch * (kMaxL + 1));
   AL(h->d_Cout, 8 * (int64_t)h->batch);
   AL(h->d_dR, h->szS * h->n_dR);
@@ -307,6 +299,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   AL(h->d_RL, h->szT * h->n_RL);
   AL(h->d_Lg, 8 * h->n_L);
   AL(h->d_oL, 8 * (int64_t)h->batch);
+  AL(h->d_order, 4 * (int64_t)h->batch);
   AL(h->d_all, 4 * (int64_t)h->batch);
   if (p.dynamics == GNMPPI_DYN_LINEAR) {
     AL(h->d_lin, 8 * (int64_t)p.n_lin);
@@ -314,6 +307,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   }
   CK(cudaMemcpyAsync(h->d_desc, h->desc.data(), sizeof(InstDesc) * h->batch, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->d_oL, offL.data(), 8 * (size_t)h->batch, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_order, h->order.data(), 4 * (size_t)h->batch, cudaMemcpyHostToDevice, h->stream));
   std::vector<int> all(h->batch);
   for (int b = 0; b < h->batch; ++b) all[b] = b;
   CK(cudaMemcpyAsync(h->d_all, all.data(), 4 * (size_t)h->batch, cudaMemcpyHostToDevice, h->stream));
@@ -390,12 +384,23 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     for (void* q : h->tc.allocs) h->allocs.push_back(q);
     if (st != GNMPPI_OK) return st;
   }
-  // the Cholesky kernel keeps its factor in up to the opt-in shared-memory limit
-  if (8 * (int64_t)4 * n_all_max > solve_budget) return fail(h, GNMPPI_E_ARG, "N*nu too large for the solver");
-  if (prec == kFP64) {
-    CK(cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
-  } else {
-    CK(cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
+  // the Cholesky kernel: vectors only in shared memory, two CTAs per SM, the
+  // rest of the carveout left to L1 (which caches the factor's panels)
+  {
+    int dev = 0, optin = 0, smsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    CK(cudaDeviceGetAttribute(&smsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    if (h->solve_smem + 1024 > optin) return fail(h, GNMPPI_E_ARG, "N*nu too large for the solver");
+    const int need = 2 * (h->solve_smem + 2048);
+    const int pct = std::min(100, (int)(100.0 * need / std::max(1, smsm)) + 5);
+    if (prec == kFP64) {
+      CK(cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
+      CK(cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    } else {
+      CK(cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
+      CK(cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    }
   }
   CK(cudaStreamSynchronize(h->stream));
   return GNMPPI_OK;
@@ -501,7 +506,7 @@ static SolveArgs solve_args(gnmppi_t h, int shrink) {
   a.RL = h->d_RL;
   a.Cl = h->d_Cl;
   a.shrink = shrink;
-  a.smem_n_max = h->smem_n_max;
+  a.order = h->d_order;
   return a;
 }
 

@@ -7,14 +7,15 @@
 //   * k_gemm_nt: SIMT batched C = A B^T with the reduction dimension contiguous
 //     in both operands, used for the contraction [P^T | S] = W^T [dR | W]
 //     (Eq. 7), the Gram A = P^T P and S^2 in FP64/FP32 modes;
-//   * k_solve: (A + lambda S_used^2) y = -b by Cholesky in FP64 with iterative
-//     refinement and tenfold damping retries, delta = S_used y, which equals
+//   * k_solve: (A + lambda S_used^2) y = -b by Cholesky in FP64 (chol.cuh) with
+//     iterative refinement and tenfold damping retries, delta = S_used y, which equals
 //     the damped GGN step (J^T J + lambda I) delta = -J^T r for J = P S_used^-1;
 //   * k_update: argmin of the line search (Eq. 11), U += alpha* delta (Eq. 10),
 //     r <- R(U_{k+1}) and the covariance shrink Sigma <- beta Sigma.
 // Internal; instantiated once in solver.cu.
 #pragma once
 #include "common.cuh"
+#include "chol.cuh"
 
 namespace gnm {
 
@@ -35,14 +36,14 @@ struct SolveArgs {
   const void* P;   // [n][ldP] accumulation type
   double* A;       // [n][n]
   double* S2;      // [n][n]
-  double* H;       // [n][n]
-  double* Lg;      // global Cholesky scratch (packed lower) for large n, or nullptr
-  const int64_t* o_L;  // per-instance offsets into Lg
+  double* H;       // packed lower copy of the damped system, at o_L[b]
+  double* Lg;      // Cholesky scratch: packed lower factor then the inverted diagonal blocks
+  const int64_t* o_L;  // per-instance offsets into Lg and H
+  const int* order;    // solve order of the instances (largest n first)
   void* r;         // nominal residual [nR] scalar type
   const void* RL;  // [L][nR]
   double* Cl;      // [kMaxL+1]
   int shrink;      // apply the covariance shrink after the update
-  int smem_n_max;  // largest n whose packed factor fits in shared memory
 };
 
 // ---------------------------------------------------------------- reductions
@@ -255,213 +256,100 @@ __global__ void __launch_bounds__(256) k_gemm_nt(GemmArgs g) {
   }
 }
 
-// ----------------------------------------------------------- Cholesky solve
-__device__ __forceinline__ int64_t pk(int i, int j) { return (int64_t)i * (i + 1) / 2 + j; }  // j <= i
-
-constexpr int CNB = 16;  // Cholesky panel width
-
-// Blocked right-looking Cholesky of a packed lower matrix, in place (256
-// threads): per panel of CNB columns, warp 0 factors the diagonal block,
-// every thread solves one panel row against it, and the trailing lower
-// triangle is updated in 4 x 4 register tiles (two DFMAs per shared-memory
-// load).  Returns false, uniformly across the CTA, on a non-positive pivot.
-__device__ bool chol_blocked(double* L, double* invd, int n, int* fail) {
-  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
-  const double* inv = nullptr;  // reciprocals of the current panel's diagonal
-  if (tid == 0) *fail = 0;
-  __syncthreads();
-  for (int p0 = 0; p0 < n; p0 += CNB) {
-    const int nb = min(CNB, n - p0);
-    inv = invd + p0;
-    if (warp == 0) {
-      for (int c = 0; c < nb; ++c) {
-        const int pc = p0 + c;
-        const double d = L[pk(pc, pc)];
-        const double rj = rsqrt(d);
-        const double ljj = d * rj;
-        __syncwarp();
-        if (lane == 0) {
-          L[pk(pc, pc)] = ljj;
-          invd[pc] = rj;
-          if (!(d > 0.0) || !isfinite(d)) *fail = 1;
-        }
-        if (lane > c && lane < nb) L[pk(p0 + lane, pc)] *= rj;
-        __syncwarp();
-        if (lane > c && lane < nb) {
-          const double lrc = L[pk(p0 + lane, pc)];
-          for (int k = c + 1; k <= lane; ++k) L[pk(p0 + lane, p0 + k)] -= lrc * L[pk(p0 + k, pc)];
-        }
-        __syncwarp();
-      }
+// ------------------------------------------------------- damped GGN solve
+// H = A + lambda T (T = S^2 in LSQ mode, diag((K' s^2)^2) in SIGMA mode),
+// taken from its lower triangle into the packed copy Hp (kept for the
+// refinement residual) and the factor scratch L.  Coalesced along the packed
+// index.
+__device__ __forceinline__ void build_system(const double* __restrict__ A, const double* __restrict__ S2,
+                                             const double* __restrict__ s, bool lsq, double Keff, double lam,
+                                             double* __restrict__ Hp, double* __restrict__ L, int n) {
+  const int np = n * (n + 1) / 2;
+#pragma unroll 4
+  for (int u = threadIdx.x; u < np; u += blockDim.x) {
+    int r = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= u) ++r;
+    while (r * (r + 1) / 2 > u) --r;
+    const int c = u - r * (r + 1) / 2;
+    const int64_t i = (int64_t)r * n + c;
+    double t;
+    if (lsq) {
+      t = S2[i];
+    } else {
+      const double sc = Keff * s[r] * s[r];
+      t = (r == c) ? sc * sc : 0.0;
     }
-    __syncthreads();
-    if (*fail) return false;
-    // panel rows: L21 = A21 L11^-T, one row per thread
-    for (int i = p0 + nb + tid; i < n; i += nt) {
-      double* Li = L + pk(i, p0);
-      double v[CNB];
-#pragma unroll
-      for (int c = 0; c < CNB; ++c) v[c] = (c < nb) ? Li[c] : 0.0;
-#pragma unroll
-      for (int c = 0; c < CNB; ++c) {
-        if (c < nb) {
-          double sacc = v[c];
-          const double* Lc = L + pk(p0 + c, p0);
-#pragma unroll
-          for (int q = 0; q < CNB; ++q)
-            if (q < c) sacc -= v[q] * Lc[q];
-          v[c] = sacc * inv[c];
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < CNB; ++c)
-        if (c < nb) Li[c] = v[c];
-    }
-    __syncthreads();
-    // trailing update A22 -= L21 L21^T on the lower triangle, 4 x 4 tiles
-    const int r0 = p0 + nb, m = n - r0;
-    if (m > 0) {
-      const int Tt = (m + 3) / 4, ntile = Tt * (Tt + 1) / 2;
-      for (int t = tid; t < ntile; t += nt) {
-        int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-        while ((I + 1) * (I + 2) / 2 <= t) ++I;
-        while (I * (I + 1) / 2 > t) --I;
-        const int Kt = t - I * (I + 1) / 2;
-        const int i0 = r0 + 4 * I, k0 = r0 + 4 * Kt;
-        double acc[4][4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[p][q] = 0.0;
-        const double* ra[4];
-        const double* rb[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          ra[p] = L + pk(min(i0 + p, n - 1), p0);
-          rb[p] = L + pk(min(k0 + p, n - 1), p0);
-        }
-        for (int c = 0; c < nb; ++c) {
-          double a[4], b[4];
-#pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            a[p] = ra[p][c];
-            b[p] = rb[p][c];
-          }
-#pragma unroll
-          for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
-        }
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int i = i0 + p, k = k0 + q;
-            if (i < n && k <= i) L[pk(i, k)] -= acc[p][q];
-          }
-      }
-    }
-    __syncthreads();
-  }
-  return true;
-}
-
-// Solve L L^T x = x in place (packed lower L, invd = 1 / diag(L)), blocked
-// like the factorisation.
-__device__ void chol_subst(const double* L, const double* invd, double* x, int n) {
-  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
-  __syncthreads();
-  // forward: L z = x
-  for (int p0 = 0; p0 < n; p0 += CNB) {
-    const int nb = min(CNB, n - p0);
-    if (warp == 0) {
-      for (int c = 0; c < nb; ++c) {
-        double zc = x[p0 + c];
-        __syncwarp();
-        zc *= invd[p0 + c];
-        if (lane == 0) x[p0 + c] = zc;
-        if (lane > c && lane < nb) x[p0 + lane] -= L[pk(p0 + lane, p0 + c)] * zc;
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    for (int i = p0 + nb + tid; i < n; i += nt) {
-      const double* Li = L + pk(i, p0);
-      double sacc = 0.0;
-      for (int c = 0; c < nb; ++c) sacc += Li[c] * x[p0 + c];
-      x[i] -= sacc;
-    }
-    __syncthreads();
-  }
-  // backward: L^T x = z
-  const int last = ((n - 1) / CNB) * CNB;
-  for (int p0 = last; p0 >= 0; p0 -= CNB) {
-    const int nb = min(CNB, n - p0);
-    if (warp == 0) {
-      for (int c = nb - 1; c >= 0; --c) {
-        double xc = x[p0 + c];
-        __syncwarp();
-        xc *= invd[p0 + c];
-        if (lane == 0) x[p0 + c] = xc;
-        if (lane < c) x[p0 + lane] -= L[pk(p0 + c, p0 + lane)] * xc;
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    for (int i = tid; i < p0; i += nt) {
-      double sacc = 0.0;
-      for (int c = 0; c < nb; ++c) sacc += L[pk(p0 + c, i)] * x[p0 + c];
-      x[i] -= sacc;
-    }
-    __syncthreads();
+    const double h = A[i] + lam * t;
+    Hp[u] = h;
+    L[u] = h;
   }
 }
 
-// One CTA (256 threads) per instance.  Packed lower factor in shared memory
-// when n <= smem_n_max, otherwise in the global scratch.
+// delta_i = sum_c S[i][c] y_c for one row of S (FP64 operands).
+__device__ __forceinline__ double srow_dot(const double* S, const double* y, const float*, const float*, int n) {
+  double acc = 0.0;
+  for (int c = 0; c < n; ++c) acc = fma(S[c], y[c], acc);
+  return acc;
+}
+// FP32 rows of S: y split into float hi + lo parts, products and partial sums
+// in FP32 (S itself carries FP32 accuracy), the partial sums added in FP64.
+__device__ __forceinline__ double srow_dot(const float* S, const double*, const float* yh, const float* yl, int n) {
+  float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+  int c = 0;
+  for (; c + 4 <= n; c += 4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float sv = S[c + k];
+      h[k] = fmaf(sv, yh[c + k], h[k]);
+      l[k] = fmaf(sv, yl[c + k], l[k]);
+    }
+  }
+  for (; c < n; ++c) {
+    h[0] = fmaf(S[c], yh[c], h[0]);
+    l[0] = fmaf(S[c], yl[c], l[0]);
+  }
+  return (((double)h[0] + (double)h[1]) + ((double)h[2] + (double)h[3])) +
+         (((double)l[0] + (double)l[1]) + ((double)l[2] + (double)l[3]));
+}
+
+// One CTA (256 threads) per instance, two CTAs per SM.  The packed factor and
+// the inverted diagonal blocks live in a per-instance global scratch (L1/L2
+// resident); shared memory holds only the vectors, so a second instance on
+// the SM keeps the FP64 pipe busy through this one's latency-bound steps.
+// Instances run in the order a.order gives (largest n first).
 template <typename TA>
-__global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
-  const int b = blockIdx.x;
+__global__ void __launch_bounds__(256, 2) k_solve(SolveArgs a) {
+  const int b = a.order[blockIdx.x];
   InstState& st = a.st[b];
   if (st.status != 0) return;
   const InstDesc I = a.inst[b];
   const int n = I.n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* vec = reinterpret_cast<double*>(smem_raw);  // rhs, x, res, 1/diag(L)
-  double* rhs = vec;
-  double* x = vec + n;
-  double* res = vec + 2 * n;
-  double* invd = vec + 3 * n;
-  double* L = (n <= a.smem_n_max) ? vec + 4 * n : a.Lg + a.o_L[b];
+  double* rhs = reinterpret_cast<double*>(smem_raw);
+  double* x = rhs + n;
+  double* res = rhs + 2 * n;
+  double* invd = rhs + 3 * n;
+  float* yh = reinterpret_cast<float*>(rhs + 4 * n);
+  float* yl = yh + n;
   __shared__ int fail;
+  __shared__ double red[32];
+  const int tid = threadIdx.x;
+  double* L = a.Lg + a.o_L[b];
+  double* Y = L + (int64_t)n * (n + 1) / 2;
+  double* Hp = a.H + a.o_L[b];
   const double* A = a.A + I.o_nn;
   const double* S2 = a.S2 + I.o_nn;
-  double* H = a.H + I.o_nn;
   const TA* P = reinterpret_cast<const TA*>(a.P) + I.o_P;
   const double* s = a.s + I.o_U;
   const double Keff = (double)(I.Kp - st.n_masked);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) rhs[j] = -a.g[I.o_U + j];
+  for (int j = tid; j < n; j += blockDim.x) rhs[j] = -a.g[I.o_U + j];
   double lam = a.cs.lambda;
   int retries = 0;
   bool ok = false;
   for (; retries <= 6; ++retries) {
-    // H = A + lam * S_used^2
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-      const int r = i / n, c = i - r * n;
-      double t;
-      if (I.lsq) {
-        t = S2[i];
-      } else {
-        const double sc = Keff * s[r] * s[r];
-        t = (r == c) ? sc * sc : 0.0;
-      }
-      H[i] = A[i] + lam * t;
-    }
+    build_system(A, S2, s, I.lsq != 0, Keff, lam, Hp, L, n);
     __syncthreads();
-    for (int r = threadIdx.x; r < n; r += blockDim.x)
-      for (int c = 0; c <= r; ++c) L[pk(r, c)] = H[(int64_t)r * n + c];
-    __syncthreads();
-    if (chol_blocked(L, invd, n, &fail)) {
+    if (chol_factor(L, invd, Y, n, &fail)) {
       ok = true;
       break;
     }
@@ -469,7 +357,7 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
     __syncthreads();
   }
   if (!ok) {
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       st.status = -3;
       st.chol_retries = 7;
       st.lambda_used = lam;
@@ -477,45 +365,45 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
     return;
   }
   // y = H^-1 rhs with iterative refinement (residual in FP64 against H)
-  for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = rhs[j];
-  __syncthreads();
-  chol_subst(L, invd, x, n);
+  for (int j = tid; j < n; j += blockDim.x) x[j] = rhs[j];
+  chol_forward(L, Y, x, n);
+  chol_backward(L, Y, x, n);
   for (int t = 0; t < a.cs.ir_steps; ++t) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < n; i += 8) {
+    // res = rhs - H x, H symmetric from its lower triangle; one row per thread
+    for (int i = tid; i < n; i += blockDim.x) {
+      const int64_t ri = pk(i, 0);
+      int64_t cb = 0;  // pk(c, 0)
       double acc = 0.0;
-      for (int c = lane; c < n; c += 32) acc += H[(int64_t)i * n + c] * x[c];
-      acc = warp_sum(acc);
-      if (lane == 0) res[i] = rhs[i] - acc;
+      for (int c = 0; c < n; ++c) {
+        const double h = (c <= i) ? Hp[ri + c] : Hp[cb + i];
+        acc = fma(h, x[c], acc);
+        cb += c + 1;
+      }
+      res[i] = rhs[i] - acc;
     }
-    __syncthreads();
-    chol_subst(L, invd, res, n);
-    for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] += res[j];
+    chol_forward(L, Y, res, n);
+    chol_backward(L, Y, res, n);
+    for (int j = tid; j < n; j += blockDim.x) x[j] += res[j];
     __syncthreads();
   }
   // delta = S_used y
-  double dsq = 0.0;
-  {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < n; i += 8) {
-      double acc = 0.0;
-      if (I.lsq) {
-        const TA* Srow = P + (int64_t)i * I.ldP + I.nR;
-        for (int c = lane; c < n; c += 32) acc += (double)Srow[c] * x[c];
-        acc = warp_sum(acc);
-      } else {
-        acc = Keff * s[i] * s[i] * x[i];
-      }
-      if (lane == 0) {
-        a.delta[I.o_U + i] = acc;
-        a.y[I.o_U + i] = x[i];
-        dsq += acc * acc;
-      }
-    }
+  for (int j = tid; j < n; j += blockDim.x) {
+    const float h = (float)x[j];
+    yh[j] = h;
+    yl[j] = (float)(x[j] - (double)h);
   }
-  __shared__ double red[32];
+  __syncthreads();
+  double dsq = 0.0;
+  for (int i = tid; i < n; i += blockDim.x) {
+    double acc;
+    if (I.lsq) acc = srow_dot(P + (int64_t)i * I.ldP + I.nR, x, yh, yl, n);
+    else acc = Keff * s[i] * s[i] * x[i];
+    a.delta[I.o_U + i] = acc;
+    a.y[I.o_U + i] = x[i];
+    dsq += acc * acc;
+  }
   dsq = block_sum(dsq, red);
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     st.chol_retries = retries;
     st.lambda_used = lam;
     st.step_norm = sqrt(dsq);
