@@ -558,7 +558,8 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
   }
   MARK(3);
   if (h->use_tc) {
-    CK(tc_gram_launch(h->tc, h->d_desc, h->d_st, reinterpret_cast<const float*>(h->d_P), h->d_A, h->stream));
+    CK(tc_gram_launch(h->tc, h->d_desc, h->d_st, reinterpret_cast<const float*>(h->d_P), h->d_A, h->d_S2,
+                      h->stream));
     h->launches += 2;
   } else {
     ga.tiles = h->d_tiles[1];
@@ -567,7 +568,7 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
     h->launches++;
   }
   MARK(4);
-  if (h->ntiles[2] > 0) {
+  if (!h->use_tc && h->ntiles[2] > 0) {  // the tensor-core Gram launch already formed S2
     ga.tiles = h->d_tiles[2];
     k_gemm_nt<kS2, TA, TC, double><<<h->ntiles[2], 256, 0, h->stream>>>(ga);
     CKL();

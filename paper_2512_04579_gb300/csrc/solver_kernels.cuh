@@ -83,13 +83,18 @@ __device__ __forceinline__ double block_min(double v, double* red) {
   return t;
 }
 
-// One CTA (256 threads) per instance.
+// One CTA (256 threads) per instance.  Outside FP64 mode the weights are taken
+// in FP32 and e, w+ - w- are staged once per chunk in shared memory in the
+// accumulation type, so the row loop runs on the FP32 pipe only (GB300's FP64
+// pipe retires conversions at the DFMA rate).
 template <typename S, typename TA>
 __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
+  constexpr int CH = 2048;  // samples staged per chunk
   const int b = blockIdx.x;
   const InstDesc I = a.inst[b];
   if (a.st[b].status != 0) return;
   __shared__ double red[32];
+  __shared__ TA se[CH], sw[CH];
   const bool anti = a.cs.antithetic != 0;
   const double* C = a.C + I.o_C;
   const double* e = a.e + I.o_C / 2;
@@ -113,32 +118,63 @@ __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
     const double c0 = C[anti ? 2 * m : m];
     const double c1 = anti ? C[2 * m + 1] : c0;
     const bool ok = isfinite(c0) && isfinite(c1) && isfinite(cmin);
-    const double w0 = ok ? exp(-(c0 - cmin) * itau) : 0.0;
-    const double w1 = (ok && anti) ? exp(-(c1 - cmin) * itau) : 0.0;
+    double w0 = 0.0, w1 = 0.0;
+    if constexpr (sizeof(TA) == 8) {
+      w0 = ok ? exp(-(c0 - cmin) * itau) : 0.0;
+      w1 = (ok && anti) ? exp(-(c1 - cmin) * itau) : 0.0;
+    } else {
+      w0 = ok ? (double)expf((float)(-(c0 - cmin) * itau)) : 0.0;
+      w1 = (ok && anti) ? (double)expf((float)(-(c1 - cmin) * itau)) : 0.0;
+    }
     s1 += w0 + w1;
     s2 += w0 * w0 + w1 * w1;
     wt[m] = w0 - w1;
   }
   s1 = block_sum(s1, red);
   s2 = block_sum(s2, red);
-  __syncthreads();  // wt visible to every warp
   // 3. rows of W: b_j = sum_m W[j][m] e_m, mppi_j = sum_m W[j][m] wt_m / sum w
   const S* W = reinterpret_cast<const S*>(a.W) + I.o_W;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int m0 = 0; m0 < I.Kp; m0 += CH) {
+    const int mc = min(CH, I.Kp - m0);
+    __syncthreads();  // wt written above / previous chunk consumed
+    for (int m = threadIdx.x; m < mc; m += blockDim.x) {
+      se[m] = (TA)e[m0 + m];
+      sw[m] = (TA)wt[m0 + m];
+    }
+    __syncthreads();
+    for (int j = warp; j < I.n; j += nw) {
+      const S* row = W + (int64_t)j * I.ldK + m0;
+      TA ag = (TA)0, am = (TA)0;
+#pragma unroll 8
+      for (int m = lane; m < mc; m += 32) {
+        TA w;
+        if constexpr (sizeof(TA) == 8) w = to_d(row[m]);
+        else w = to_f(row[m]);
+        ag += w * se[m];
+        am += w * sw[m];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ag += __shfl_xor_sync(0xffffffffu, ag, o);
+        am += __shfl_xor_sync(0xffffffffu, am, o);
+      }
+      if (lane == 0) {
+        if (m0 == 0) {
+          a.g[I.o_U + j] = (double)ag;
+          a.mppi[I.o_U + j] = (double)am;
+        } else {
+          a.g[I.o_U + j] += (double)ag;
+          a.mppi[I.o_U + j] += (double)am;
+        }
+      }
+    }
+  }
   double gsq = 0.0;
   for (int j = warp; j < I.n; j += nw) {
-    const S* row = W + (int64_t)j * I.ldK;
-    TA ag = (TA)0, am = (TA)0;
-    for (int m = lane; m < I.Kp; m += 32) {
-      const TA w = (TA)to_d(row[m]);
-      ag += w * (TA)e[m];
-      am += w * (TA)wt[m];
-    }
-    const double G = warp_sum((double)ag);
-    const double Mp = warp_sum((double)am);
     if (lane == 0) {
-      a.g[I.o_U + j] = G;
-      a.mppi[I.o_U + j] = s1 > 0.0 ? Mp / s1 : 0.0;
+      const double G = a.g[I.o_U + j];
+      a.mppi[I.o_U + j] = s1 > 0.0 ? a.mppi[I.o_U + j] / s1 : 0.0;
       gsq += G * G;
     }
   }

@@ -13,7 +13,9 @@
 //   warps 0-3      read TMEM back (tcgen05.ld 32x32b) and store FP32 rows.
 //  (2) the Gram product A = P^T P of Eq. 9 in FP32-level accuracy from three
 //      TF32 passes, A ~ Ph Ph^T + Ph Pl^T + Pl Ph^T with P^T = Ph + Pl split into
-//      a TF32 head and its FP32 remainder (k_split_tf32 writes [Ph; Pl] rows).
+//      a TF32 head and its FP32 remainder (k_split_tf32 writes [Ph; Pl] rows),
+//      and in the same launch S2 = S S^T for the scaled LSQ system: the S
+//      columns sit in the same split rows from a 32-aligned column on.
 // Both use the same kernel, driven by per-instance job descriptors.
 // Every mbarrier wait is bounded by the global timer; a wait that runs out
 // sets the plan's error word and the CTA winds down without a trap.
@@ -146,7 +148,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
 template <bool BF16, bool SPLIT3, typename TOut>
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
                                                     const InstState* __restrict__ st, const int4* __restrict__ tiles,
-                                                    TOut* __restrict__ D, int* __restrict__ err) {
+                                                    TOut* __restrict__ D, TOut* __restrict__ D2,
+                                                    int* __restrict__ err) {
   constexpr int KBLK = BF16 ? 64 : 32;   // elements per k-block
   constexpr int KSTEP = BF16 ? 16 : 8;   // elements per MMA
   constexpr int NSUB = KBLK / KSTEP;     // MMAs per k-block and operand pair (4)
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
       mbar_expect_tx(full, STAGE_BYTES);
       const uint32_t a_dst = su32(base + s * STAGE_BYTES);
       const uint32_t b_dst = a_dst + PARTS * A_BYTES;
-      const int x = kb * KBLK;
+      const int x = J.x0 + kb * KBLK;
 #pragma unroll
       for (int p = 0; p < PARTS; ++p) {
         const int off = p * J.lo_off;
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
   // tcgen05.ld is warp-collective: the whole warp takes the same branch
   if (__all_sync(0xffffffffu, ok && !*abort)) {
     const int row = tl.y * BM + warp * 32 + lane;
-    TOut* out = D + J.out_off + (int64_t)row * J.ldc;
+    TOut* out = (J.out_sel ? D2 : D) + J.out_off + (int64_t)row * J.ldc;
 #pragma unroll 1
     for (int c = 0; c < BN / 32; ++c) {
       uint32_t v[32];
@@ -268,8 +271,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
   }
 }
 
-// [Ph; Pl] rows of the Gram operand: Ph = P^T rounded to TF32 (cvt.rna),
-// Pl = P^T - Ph (exact in FP32).  One CTA row-block per instance row.
+// [Ph; Pl] rows of the Gram operand: Ph = [P^T | S] rounded to TF32
+// (cvt.rna), Pl = [P^T | S] - Ph (exact in FP32).  The P^T columns go to
+// [0, nR), the S columns (LSQ mode) to [nRp, nRp + n) with nRp = nR rounded
+// up to a k-block; the gap stays zero.  One CTA per instance row.
 __global__ void __launch_bounds__(256) k_split_tf32(const InstDesc* __restrict__ inst, const InstState* __restrict__ st,
                                                     const int2* __restrict__ rows, const float* __restrict__ P,
                                                     float* __restrict__ G, const int64_t* __restrict__ g_off,
@@ -280,13 +285,16 @@ __global__ void __launch_bounds__(256) k_split_tf32(const InstDesc* __restrict__
   const float* src = P + I.o_P + (int64_t)rb.y * I.ldP;
   float* hi = G + g_off[rb.x] + (int64_t)rb.y * g_ld[rb.x];
   float* lo = hi + (int64_t)I.n * g_ld[rb.x];
-  for (int k = threadIdx.x; k < I.nR; k += blockDim.x) {
+  const int nRp = (I.nR + 31) / 32 * 32;
+  const int ncol = I.nR + (I.lsq ? I.n : 0);
+  for (int k = threadIdx.x; k < ncol; k += blockDim.x) {
     const float x = src[k];
     uint32_t h;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
     const float hf = __uint_as_float(h);
-    hi[k] = hf;
-    lo[k] = x - hf;
+    const int c = k < I.nR ? k : nRp + (k - I.nR);
+    hi[c] = hf;
+    lo[c] = x - hf;
   }
 }
 
@@ -332,12 +340,13 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
   const size_t esz = bf16 ? 2 : 4;
   const int kblk = bf16 ? 64 : 32;
   const int nb = (int)desc.size();
-  // Gram operand blocks [Ph; Pl], rows of ldG = nR rounded to 32 floats
+  // Gram operand blocks [Ph; Pl], rows of ldG = nR rounded to 32 floats plus,
+  // in LSQ mode, n rounded to 32 floats for the S columns
   std::vector<int64_t> g_off(nb);
   std::vector<int> g_ld(nb);
   int64_t g_total = 0;
   for (int b = 0; b < nb; ++b) {
-    g_ld[b] = (int)((desc[b].nR + 31) / 32 * 32);
+    g_ld[b] = (int)((desc[b].nR + 31) / 32 * 32) + (desc[b].lsq ? (int)((desc[b].n + 31) / 32 * 32) : 0);
     g_off[b] = g_total;
     g_total += 2 * (int64_t)desc[b].n * g_ld[b];
   }
@@ -346,7 +355,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     return GNMPPI_E_NOMEM;
   }
   std::vector<CUtensorMap> maps(2 * (size_t)nb);
-  std::vector<TcJob> jobs(2 * (size_t)nb);
+  std::vector<TcJob> jobs(3 * (size_t)nb);
   std::vector<int4> tc, tg;
   std::vector<int2> rows;
   for (int b = 0; b < nb; ++b) {
@@ -372,10 +381,12 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     jc.nkb = d.ldK / kblk;
     jc.out_off = d.o_P;
     jc.ldc = d.ldP;
+    jc.x0 = 0;
+    jc.out_sel = 0;
     for (int i = 0; i < (d.n + BM - 1) / BM; ++i)
       for (int j = 0; j < (d.nR + d.n + BN - 1) / BN; ++j) tc.push_back(make_int4(b, i, j, 0));
-    // Gram: one FP32 map over [Ph; Pl] (2n rows, nR columns)
-    if (!encode_rows(encode, &maps[nb + b], plan->d_G + g_off[b], false, d.nR, g_ld[b], 2 * (int64_t)d.n)) {
+    // Gram: one FP32 map over [Ph; Pl] (2n rows, ldG columns)
+    if (!encode_rows(encode, &maps[nb + b], plan->d_G + g_off[b], false, g_ld[b], g_ld[b], 2 * (int64_t)d.n)) {
       err = "cuTensorMapEncodeTiled failed (Gram, instance " + std::to_string(b) + ")";
       return GNMPPI_E_CUDA;
     }
@@ -390,8 +401,19 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     jg.nkb = (d.nR + 31) / 32;
     jg.out_off = d.o_nn;
     jg.ldc = d.n;
+    jg.x0 = 0;
+    jg.out_sel = 0;
     for (int i = 0; i < (d.n + BM - 1) / BM; ++i)
       for (int j = 0; j < (d.n + BN - 1) / BN; ++j) tg.push_back(make_int4(nb + b, i, j, 0));
+    // S2 = S S^T over the S columns of the same split rows (LSQ mode)
+    TcJob& js = jobs[2 * nb + b];
+    js = jg;
+    js.x0 = (d.nR + 31) / 32 * 32;
+    js.nkb = (d.n + 31) / 32;
+    js.out_sel = 1;
+    if (d.lsq)
+      for (int i = 0; i < (d.n + BM - 1) / BM; ++i)
+        for (int j = 0; j < (d.n + BN - 1) / BN; ++j) tg.push_back(make_int4(2 * nb + b, i, j, 0));
     for (int r = 0; r < d.n; ++r) rows.push_back(make_int2(b, r));
   }
   if (!plan_alloc(plan, &plan->d_maps, sizeof(CUtensorMap) * maps.size()) ||
@@ -445,21 +467,21 @@ cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float*
   if (plan.ntiles_c == 0) return cudaSuccess;
   if (plan.bf16)
     k_gemm_tc<true, false, float><<<plan.ntiles_c, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
-                                                                             plan.d_tiles_c, P, plan.d_err);
+                                                                             plan.d_tiles_c, P, P, plan.d_err);
   else
     k_gemm_tc<false, false, float><<<plan.ntiles_c, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
-                                                                              plan.d_tiles_c, P, plan.d_err);
+                                                                              plan.d_tiles_c, P, P, plan.d_err);
   return cudaGetLastError();
 }
 
 cudaError_t tc_gram_launch(const TcPlan& plan, const InstDesc* d_desc, const InstState* d_st, const float* P, double* A,
-                           cudaStream_t stream) {
+                           double* S2, cudaStream_t stream) {
   if (plan.ntiles_g == 0) return cudaSuccess;
   k_split_tf32<<<plan.nrows, 256, 0, stream>>>(d_desc, d_st, plan.d_rows, P, plan.d_G, plan.d_goff, plan.d_gld);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_gemm_tc<false, true, double><<<plan.ntiles_g, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
-                                                                            plan.d_tiles_g, A, plan.d_err);
+                                                                            plan.d_tiles_g, A, S2, plan.d_err);
   return cudaGetLastError();
 }
 

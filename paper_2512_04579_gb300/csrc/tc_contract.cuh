@@ -15,13 +15,14 @@ namespace gnm {
 
 // One batched NT GEMM per instance: D[i][j] = sum_k A[i][k] B[j][k] with A
 // rows a_row0.., B rows b_row0.. of tensor map `map` (and, for the three-pass
-// TF32 split, remainder rows lo_off further down).
+// TF32 split, remainder rows lo_off further down), k from column x0 over nkb
+// k-blocks; the output goes to the launch's first (out_sel 0) or second array.
 struct TcJob {
   int32_t inst, map;
   int32_t a_row0, b_row0, lo_off;
   int32_t M, Nc, nkb;
   int64_t out_off;
-  int32_t ldc, pad;
+  int32_t ldc, x0, out_sel, pad;
 };
 
 struct TcPlan {
@@ -30,7 +31,7 @@ struct TcPlan {
   int4* d_tiles_c = nullptr;      // (job, m tile, n tile, -) of the contraction
   int4* d_tiles_g = nullptr;      // ... of the Gram product
   int2* d_rows = nullptr;         // (instance, row) of the TF32 split
-  float* d_G = nullptr;           // Gram operands [Ph; Pl] per instance
+  float* d_G = nullptr;           // Gram operands [Ph; Pl] per instance (P^T columns, then S columns)
   int64_t* d_goff = nullptr;
   int* d_gld = nullptr;
   int ntiles_c = 0, ntiles_g = 0, nrows = 0;
@@ -49,8 +50,9 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
 // [P^T | S] = W^T [dR | W] into P (FP32).
 cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float* P, cudaStream_t stream);
 
-// A = P^T P (FP64 output) from three TF32 passes over the split of P^T.
+// A = P^T P and, for instances in LSQ mode, S2 = S S^T (FP64 outputs) from
+// three TF32 passes over the split of [P^T | S], in one launch.
 cudaError_t tc_gram_launch(const TcPlan& plan, const InstDesc* d_desc, const InstState* d_st, const float* P, double* A,
-                           cudaStream_t stream);
+                           double* S2, cudaStream_t stream);
 
 }  // namespace gnm
