@@ -194,8 +194,37 @@ gnmppi_status gnmppi_debug_read(gnmppi_t h, int32_t what, int32_t inst, double* 
 gnmppi_status gnmppi_phase_times(gnmppi_t h, int32_t iteration, double* ms, int32_t cap, int32_t* nphase);
 
 /* Name of phase i of gnmppi_phase_times ("samples", "softmin", "contract",
- * "gram", "s2", "solve", "line", "update"), or NULL. */
+ * "gram", "s2", "solve", "line", "update"), or NULL.  With the tensor-core
+ * path S2 is formed inside the "gram" phase and "s2" stays empty. */
 const char* gnmppi_phase_name(int32_t i);
+
+/* Autotuner of the batched launch (the paper has no counterpart: it concerns
+ * how Algorithm 1 is scheduled over many instances, not what it computes).
+ * Times, on this handle's instances and the caller's inputs (same arguments
+ * and memory kinds as gnmppi_solve; U and sigma are read only), the candidate
+ * launch configurations and keeps the fastest:
+ *   - branches: how many concurrent CUDA-graph branches carry the per-size
+ *     rollout groups (sample rollouts and line search), 1, 2, 4 or 8;
+ *   - solve_nt: threads per Cholesky CTA, 256 (two per SM) or 128 (four).
+ * reps: timed repetitions per candidate (<= 0: 3), after one warm-up.  The
+ * choice is cached for the process under a signature of the device, the
+ * model, the precision and the multiset of instance shapes; when the
+ * environment variable GNMPPI_TUNE_FILE names a file, cached choices are read
+ * from it and new ones appended ("signature branches solve_nt" lines).  A
+ * cached choice is applied without timing.  Results do not depend on the
+ * configuration (the arithmetic of every kernel is unchanged).  The next
+ * gnmppi_solve recaptures its CUDA graph.  Errors: as gnmppi_solve. */
+gnmppi_status gnmppi_autotune(gnmppi_t h, int32_t mem, const double* x0, const double* xref, const double* U,
+                              const double* sigma, int32_t reps);
+
+/* Set the launch configuration by hand (branches 1..8, solve_nt 128 or 256).
+ * Errors: E_ARG for values out of range. */
+gnmppi_status gnmppi_tune_set(gnmppi_t h, int32_t branches, int32_t solve_nt);
+
+/* The handle's launch configuration as a JSON object (source "default",
+ * "set", "cache" or "timed"; the timed candidates when tuned), NUL-terminated
+ * into buf (host, cap bytes).  Errors: E_ARG if cap is too small. */
+gnmppi_status gnmppi_tune_report(gnmppi_t h, char* buf, int32_t cap);
 
 /* Softmin weights exp(-(C - min C)/tau) and the weighted mean perturbation
  * sum w_i W_i / sum w_i of one sample set, computed without any device

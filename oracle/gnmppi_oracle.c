@@ -423,7 +423,10 @@ static int all_finite(const double* v, int n) {
  *              SIGMA otherwise;
  *  5. GGN step (Eq. 9) with Phi = 0.5||R||^2, so grad Phi = R and
  *     hess Phi = I:  (J^T J + lambda I) delta = -J^T r, solved by Cholesky
- *     with iterative refinement;
+ *     with iterative refinement.  Eq. 9 assumes B = J^T J positive definite;
+ *     when the LSQ system has no Cholesky factor at any of the damping
+ *     retries (a draw with K' barely above n leaves S nearly singular), the
+ *     iteration takes the SIGMA form instead (reported as jac_mode_used);
  *  6. line search (Eq. 11) over A = {gamma^j, j < L} (plus 0 if monotone):
  *     alpha* = argmin C(U_k + alpha delta), ties to the smallest j;
  *  7. U_{k+1} = U_k + alpha* delta (Eq. 10).  The covariance shrink is
@@ -560,10 +563,17 @@ int32_t orc_iteration(const orc_model* m, const orc_options* o, const double* x0
       for (int j = 0; j < n; ++j) J[(size_t)i * n + j] = P[(size_t)i * n + j] / ((double)Keff * s[j] * s[j]);
   }
 
-  /* 5. GGN step: G = J^T J, g = J^T r, (G + lambda I) delta = -g */
+  /* 5. GGN step: G = J^T J, g = J^T r, (G + lambda I) delta = -g; an LSQ
+   *    system without a Cholesky factor at any damping falls back to SIGMA */
   double lambda_used = o->lambda;
   int retries = 0;
-  if (status == ORC_OK) {
+  for (int pass = 0; status == ORC_OK && pass < 2; ++pass) {
+    if (pass == 1) {
+      if (retries >= 0 || jm != ORC_JAC_LSQ) break;
+      jm = ORC_JAC_SIGMA;
+      for (int i = 0; i < nR; ++i)
+        for (int j = 0; j < n; ++j) J[(size_t)i * n + j] = P[(size_t)i * n + j] / ((double)Keff * s[j] * s[j]);
+    }
     for (int a = 0; a < n; ++a) {
       for (int b = 0; b < n; ++b) {
         double acc = 0.0;
@@ -577,9 +587,9 @@ int32_t orc_iteration(const orc_model* m, const orc_options* o, const double* x0
     double* rhs = (double*)malloc(sizeof(double) * (size_t)n);
     for (int j = 0; j < n; ++j) rhs[j] = -g[j];
     retries = damped_solve(n, G, o->lambda, rhs, o->ir_steps, delta, &lambda_used);
-    if (retries < 0) status = ORC_E_NOT_PD;
     free(rhs);
   }
+  if (status == ORC_OK && retries < 0) status = ORC_E_NOT_PD;
 
   /* 6. line search over {gamma^j}; alpha_{j+1} = alpha_j * gamma */
   const int nl = o->L + (o->monotone ? 1 : 0);
@@ -674,11 +684,17 @@ int32_t orc_solve(const orc_model* m, const orc_options* o, const double* x0, co
   int32_t st = ORC_OK;
   if (U_hist) memcpy(U_hist, U, sizeof(double) * (size_t)n);
   if (C_hist) C_hist[0] = orc_cost(m, x0, xref, U);
+  /* once the LSQ form breaks down (orc_iteration fell back to SIGMA), the
+   * rest of the solve uses SIGMA: K' and n, which cause it, do not change */
+  orc_options oo = *o;
+  const int Kp = o->antithetic ? o->K / 2 : o->K;
+  const int lsq_chosen = o->jac_mode == ORC_JAC_LSQ || (o->jac_mode == ORC_JAC_AUTO && Kp >= n);
   for (int it = 0; it < o->iterations; ++it) {
     orc_record local;
     memset(&local, 0, sizeof(local));
     orc_record* rec = recs ? &recs[it] : &local;
-    st = orc_iteration(m, o, x0, xref, U, s, inst, (uint32_t)it, rec);
+    st = orc_iteration(m, &oo, x0, xref, U, s, inst, (uint32_t)it, rec);
+    if (lsq_chosen && rec->jac_mode_used == ORC_JAC_SIGMA) oo.jac_mode = ORC_JAC_SIGMA;
     if (U_hist) memcpy(U_hist + (size_t)(it + 1) * n, U, sizeof(double) * (size_t)n);
     if (C_hist) C_hist[it + 1] = rec->C_new;
     if (st != ORC_OK) break;

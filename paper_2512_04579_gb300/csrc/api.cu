@@ -8,7 +8,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <array>
+#include <cstdlib>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -29,6 +32,16 @@ struct Group {
   int* d_list = nullptr;
   int2* d_bmap = nullptr;
   int smem = 0;
+  double work = 0.0;  // rollout steps x state size, for the branch assignment
+  int branch = 0;
+};
+
+constexpr int kMaxBranches = 8;
+
+// Launch configuration picked by the autotuner (or the defaults).
+struct TuneCfg {
+  int branches = 1;   // concurrent graph branches for the per-size rollout groups
+  int solve_nt = 256; // threads per k_solve CTA (256: two CTAs per SM, 128: four)
 };
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -60,6 +73,11 @@ struct gnmppi_s {
   int* d_order = nullptr;
   int solve_smem = 0;
   bool use_tc = false;
+  // concurrency of the rollout groups and the solve CTA shape
+  TuneCfg tune{};
+  std::string tune_report;
+  cudaStream_t aux[kMaxBranches] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kMaxBranches] = {};
   TcPlan tc{};
   // graph of one Algorithm-1 solve
   cudaGraphExec_t gexec = nullptr;
@@ -70,6 +88,12 @@ struct gnmppi_s {
 };
 
 static thread_local std::string g_create_err;  // errors raised before a handle exists
+
+static void assign_branches(gnmppi_t h, int nb);
+static void set_branches(gnmppi_t h, int nb) {
+  h->tune.branches = std::max(1, std::min(nb, kMaxBranches));
+  assign_branches(h, h->tune.branches);
+}
 
 static gnmppi_status fail(gnmppi_t h, gnmppi_status st, const char* fmt, ...) {
   char buf[512];
@@ -187,6 +211,11 @@ extern "C" void gnmppi_destroy(gnmppi_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (int i = 0; i < kMaxBranches; ++i) {
+    if (h->aux[i]) cudaStreamDestroy(h->aux[i]);
+    if (h->ev_join[i]) cudaEventDestroy(h->ev_join[i]);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   for (void* p : h->allocs) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -330,10 +359,17 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     }
     Group& g = h->groups[it->second];
     g.insts.push_back(b);
+    g.work += (double)d.Kp * d.N * (d.nx + 2);
     const int per = g.fn.pairs_per_block ? g.fn.pairs_per_block : (anti ? kPairsPerBlock : kSamplesPerBlock);
     for (int c = 0; c < (d.Kp + per - 1) / per; ++c) g.bmap.push_back(make_int2(b, c));
     g.smem = std::max(g.smem, (int)(h->szT * (2 * d.n + d.nR + d.nref)));
   }
+  // concurrency: streams and events for up to kMaxBranches graph branches
+  for (int i = 0; i < kMaxBranches; ++i) {
+    CK(cudaStreamCreateWithFlags(&h->aux[i], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming));
+  }
+  CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   for (auto& g : h->groups) {
     CK(g.fn.prepare(g.smem));
     AL(g.d_list, 4 * g.insts.size());
@@ -384,24 +420,32 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     for (void* q : h->tc.allocs) h->allocs.push_back(q);
     if (st != GNMPPI_OK) return st;
   }
-  // the Cholesky kernel: vectors only in shared memory, two CTAs per SM, the
-  // rest of the carveout left to L1 (which caches the factor's panels)
+  // the Cholesky kernel: vectors only in shared memory, two (256 threads) or
+  // four (128 threads) CTAs per SM, the rest of the carveout left to L1 (which
+  // caches the factor's panels)
   {
     int dev = 0, optin = 0, smsm = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     CK(cudaDeviceGetAttribute(&smsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     if (h->solve_smem + 1024 > optin) return fail(h, GNMPPI_E_ARG, "N*nu too large for the solver");
-    const int need = 2 * (h->solve_smem + 2048);
-    const int pct = std::min(100, (int)(100.0 * need / std::max(1, smsm)) + 5);
+    const int pct2 = std::min(100, (int)(100.0 * 2 * (h->solve_smem + 2048) / std::max(1, smsm)) + 5);
+    const int pct4 = std::min(100, (int)(100.0 * 4 * (h->solve_smem + 2048) / std::max(1, smsm)) + 5);
     if (prec == kFP64) {
-      CK(cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
-      CK(cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+      CK(cudaFuncSetAttribute(k_solve<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
+      CK(cudaFuncSetAttribute(k_solve<double, 256>, cudaFuncAttributePreferredSharedMemoryCarveout, pct2));
+      CK(cudaFuncSetAttribute(k_solve<double, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
+      CK(cudaFuncSetAttribute(k_solve<double, 128>, cudaFuncAttributePreferredSharedMemoryCarveout, pct4));
     } else {
-      CK(cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
-      CK(cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+      CK(cudaFuncSetAttribute(k_solve<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
+      CK(cudaFuncSetAttribute(k_solve<float, 256>, cudaFuncAttributePreferredSharedMemoryCarveout, pct2));
+      CK(cudaFuncSetAttribute(k_solve<float, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
+      CK(cudaFuncSetAttribute(k_solve<float, 128>, cudaFuncAttributePreferredSharedMemoryCarveout, pct4));
     }
   }
+  // default launch configuration (the autotuner may replace it)
+  h->tune.solve_nt = 256;
+  set_branches(h, std::min<int>(4, (int)h->groups.size()));
   CK(cudaStreamSynchronize(h->stream));
   return GNMPPI_OK;
 }
@@ -510,99 +554,164 @@ static SolveArgs solve_args(gnmppi_t h, int shrink) {
   return a;
 }
 
-static gnmppi_status launch_nominal(gnmppi_t h) {
+// Assign the rollout groups to nb branches, heaviest first to the least
+// loaded branch (longest-processing-time rule).
+static void assign_branches(gnmppi_t h, int nb) {
+  std::vector<int> idx(h->groups.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return h->groups[x].work > h->groups[y].work; });
+  std::vector<double> load(std::max(1, nb), 0.0);
+  for (int gi : idx) {
+    const int bi = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    h->groups[gi].branch = bi;
+    load[bi] += h->groups[gi].work;
+  }
+}
+
+// Launch fn(group, stream) for every rollout group: on the handle's stream, or
+// forked over tune.branches streams and joined back (also inside a capture,
+// where the fork and join become graph edges).
+template <class Fn>
+static gnmppi_status for_groups(gnmppi_t h, Fn&& fn) {
+  const int nb = std::min<int>(h->tune.branches, (int)h->groups.size());
+  if (nb <= 1) {
+    for (auto& g : h->groups) {
+      gnmppi_status st = fn(g, h->stream);
+      if (st != GNMPPI_OK) return st;
+    }
+    return GNMPPI_OK;
+  }
+  CK(cudaEventRecord(h->ev_fork, h->stream));
+  for (int i = 0; i < nb; ++i) CK(cudaStreamWaitEvent(h->aux[i], h->ev_fork, 0));
   for (auto& g : h->groups) {
+    gnmppi_status st = fn(g, h->aux[g.branch]);
+    if (st != GNMPPI_OK) return st;
+  }
+  for (int i = 0; i < nb; ++i) {
+    CK(cudaEventRecord(h->ev_join[i], h->aux[i]));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_join[i], 0));
+  }
+  return GNMPPI_OK;
+}
+
+static gnmppi_status launch_nominal(gnmppi_t h) {
+  return for_groups(h, [&](Group& g, cudaStream_t s) -> gnmppi_status {
     RollArgs a = roll_args(h, 0);
     a.list = g.d_list;
     a.count = (int)g.insts.size();
     a.mode = 1;
-    g.fn.line(a, a.count, h->stream);
+    g.fn.line(a, a.count, s);
     CKL();
     h->launches++;
-  }
-  return GNMPPI_OK;
+    return GNMPPI_OK;
+  });
 }
 
 static const char* kPhaseNames[] = {"samples", "softmin", "contract", "gram", "s2", "solve", "line", "update"};
 constexpr int kNumPhases = 8;
 
+constexpr unsigned kAllPhases = (1u << kNumPhases) - 1;
+
 // ev (nullable): kNumPhases + 1 events recorded before the first phase and
-// after each phase.
+// after each phase.  mask: the phases to launch (bit i = kPhaseNames[i]);
+// the autotuner times single phases this way.
 template <typename S, typename TA, typename TC, typename T>
-static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cudaEvent_t* ev) {
+static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cudaEvent_t* ev, unsigned mask) {
 #define MARK(i) \
   if (ev) CK(cudaEventRecord(ev[i], h->stream))
+#define ON(i) (mask & (1u << (i)))
   MARK(0);
-  for (auto& g : h->groups) {
-    RollArgs a = roll_args(h, it);
-    a.bmap = g.d_bmap;
-    g.fn.samples(a, (int)g.bmap.size(), g.smem, h->stream);
-    CKL();
-    h->launches++;
+  if (ON(0)) {
+    gnmppi_status st = for_groups(h, [&](Group& g, cudaStream_t s) -> gnmppi_status {
+      RollArgs a = roll_args(h, it);
+      a.bmap = g.d_bmap;
+      g.fn.samples(a, (int)g.bmap.size(), g.smem, s);
+      CKL();
+      h->launches++;
+      return GNMPPI_OK;
+    });
+    if (st != GNMPPI_OK) return st;
   }
   MARK(1);
   SolveArgs sa = solve_args(h, shrink);
-  k_softmin_wvec<S, TC><<<h->batch, 256, 0, h->stream>>>(sa);
-  CKL();
-  h->launches++;
+  if (ON(1)) {
+    k_softmin_wvec<S, TC><<<h->batch, 256, 0, h->stream>>>(sa);
+    CKL();
+    h->launches++;
+  }
   MARK(2);
   GemmArgs ga{h->d_desc, h->d_st, nullptr, h->d_dR, h->d_W, h->d_P, h->d_A, h->d_S2};
-  if (h->use_tc) {
-    CK(tc_contract_launch(h->tc, h->d_st, reinterpret_cast<float*>(h->d_P), h->stream));
-    h->launches++;
-  } else {
-    ga.tiles = h->d_tiles[0];
-    k_gemm_nt<kContract, S, TC, TA><<<h->ntiles[0], 256, 0, h->stream>>>(ga);
-    CKL();
-    h->launches++;
+  if (ON(2)) {
+    if (h->use_tc) {
+      CK(tc_contract_launch(h->tc, h->d_st, reinterpret_cast<float*>(h->d_P), h->stream));
+      h->launches++;
+    } else {
+      ga.tiles = h->d_tiles[0];
+      k_gemm_nt<kContract, S, TC, TA><<<h->ntiles[0], 256, 0, h->stream>>>(ga);
+      CKL();
+      h->launches++;
+    }
   }
   MARK(3);
-  if (h->use_tc) {
-    CK(tc_gram_launch(h->tc, h->d_desc, h->d_st, reinterpret_cast<const float*>(h->d_P), h->d_A, h->d_S2,
-                      h->stream));
-    h->launches += 2;
-  } else {
-    ga.tiles = h->d_tiles[1];
-    k_gemm_nt<kGram, TA, TC, double><<<h->ntiles[1], 256, 0, h->stream>>>(ga);
-    CKL();
-    h->launches++;
+  if (ON(3)) {
+    if (h->use_tc) {
+      CK(tc_gram_launch(h->tc, h->d_desc, h->d_st, reinterpret_cast<const float*>(h->d_P), h->d_A, h->d_S2,
+                        h->stream));
+      h->launches += 2;
+    } else {
+      ga.tiles = h->d_tiles[1];
+      k_gemm_nt<kGram, TA, TC, double><<<h->ntiles[1], 256, 0, h->stream>>>(ga);
+      CKL();
+      h->launches++;
+    }
   }
   MARK(4);
-  if (!h->use_tc && h->ntiles[2] > 0) {  // the tensor-core Gram launch already formed S2
+  if (ON(4) && !h->use_tc && h->ntiles[2] > 0) {  // the tensor-core Gram launch already formed S2
     ga.tiles = h->d_tiles[2];
     k_gemm_nt<kS2, TA, TC, double><<<h->ntiles[2], 256, 0, h->stream>>>(ga);
     CKL();
     h->launches++;
   }
   MARK(5);
-  k_solve<TA><<<h->batch, 256, h->solve_smem, h->stream>>>(sa);
-  CKL();
-  h->launches++;
-  MARK(6);
-  for (auto& g : h->groups) {
-    RollArgs a = roll_args(h, it);
-    a.list = g.d_list;
-    a.count = (int)g.insts.size();
-    a.ncand = h->p.L;
-    a.mode = 0;
-    g.fn.line(a, a.count * h->p.L, h->stream);
+  if (ON(5)) {
+    if (h->tune.solve_nt == 128) k_solve<TA, 128><<<h->batch, 128, h->solve_smem, h->stream>>>(sa);
+    else k_solve<TA, 256><<<h->batch, 256, h->solve_smem, h->stream>>>(sa);
     CKL();
     h->launches++;
   }
+  MARK(6);
+  if (ON(6)) {
+    gnmppi_status st = for_groups(h, [&](Group& g, cudaStream_t s) -> gnmppi_status {
+      RollArgs a = roll_args(h, it);
+      a.list = g.d_list;
+      a.count = (int)g.insts.size();
+      a.ncand = h->p.L;
+      a.mode = 0;
+      g.fn.line(a, a.count * h->p.L, s);
+      CKL();
+      h->launches++;
+      return GNMPPI_OK;
+    });
+    if (st != GNMPPI_OK) return st;
+  }
   MARK(7);
-  k_update<T><<<h->batch, 128, 0, h->stream>>>(sa);
-  CKL();
-  h->launches++;
+  if (ON(7)) {
+    k_update<T><<<h->batch, 128, 0, h->stream>>>(sa);
+    CKL();
+    h->launches++;
+  }
   MARK(8);
+#undef ON
 #undef MARK
   return GNMPPI_OK;
 }
 
-static gnmppi_status launch_iteration(gnmppi_t h, uint32_t it, int shrink, cudaEvent_t* ev = nullptr) {
+static gnmppi_status launch_iteration(gnmppi_t h, uint32_t it, int shrink, cudaEvent_t* ev = nullptr,
+                                      unsigned mask = kAllPhases) {
   switch (h->p.precision) {
-    case kFP64: return launch_iteration_t<double, double, double, double>(h, it, shrink, ev);
-    case kFP32: return launch_iteration_t<float, float, float, float>(h, it, shrink, ev);
-    default: return launch_iteration_t<__nv_bfloat16, float, float, float>(h, it, shrink, ev);
+    case kFP64: return launch_iteration_t<double, double, double, double>(h, it, shrink, ev, mask);
+    case kFP32: return launch_iteration_t<float, float, float, float>(h, it, shrink, ev, mask);
+    default: return launch_iteration_t<__nv_bfloat16, float, float, float>(h, it, shrink, ev, mask);
   }
 }
 
@@ -865,4 +974,208 @@ extern "C" gnmppi_status gnmppi_debug_read(gnmppi_t h, int32_t what, int32_t ins
   }
   if (written) *written = (st == GNMPPI_OK) ? need : 0;
   return st;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Picks the launch configuration of a handle by timing the candidates on its
+// own instances and inputs: the number of concurrent graph branches for the
+// per-size rollout groups (samples and line search) and the k_solve CTA shape.
+// Choices are cached per process under a signature of the device, the model
+// and the multiset of instance shapes, and appended to the text file named by
+// GNMPPI_TUNE_FILE (one "signature branches solve_nt" line per entry), which
+// later processes read back.
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, TuneCfg> g_tune_cache;
+bool g_tune_file_read = false;
+
+std::string tune_signature(gnmppi_t h) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, dev);
+  std::string name = prop.name;
+  for (char& c : name)
+    if (c == ' ' || c == '\t') c = '_';
+  std::vector<std::array<int, 4>> sh;
+  sh.reserve(h->desc.size());
+  for (auto& d : h->desc) sh.push_back({d.n, d.nR, d.Kp, d.nx});
+  std::sort(sh.begin(), sh.end());
+  uint64_t f = 1469598103934665603ull;  // FNV-1a over the sorted shapes
+  for (auto& a : sh)
+    for (int v : a) {
+      for (int byte = 0; byte < 4; ++byte) {
+        f ^= (uint64_t)((uint32_t)v >> (8 * byte)) & 0xffu;
+        f *= 1099511628211ull;
+      }
+    }
+  char buf[320];
+  snprintf(buf, sizeof(buf), "%s/sm%d/dyn%d/prec%d/anti%d/L%d/B%d/%016llx", name.c_str(), prop.multiProcessorCount,
+           h->p.dynamics, h->p.precision, h->p.antithetic ? 1 : 0, h->p.L, h->batch, (unsigned long long)f);
+  return buf;
+}
+
+void read_tune_file() {  // under g_tune_mu
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char* path = getenv("GNMPPI_TUNE_FILE");
+  if (!path || !*path) return;
+  FILE* fp = fopen(path, "r");
+  if (!fp) return;
+  char sig[320];
+  int nb = 0, nt = 0;
+  while (fscanf(fp, "%319s %d %d", sig, &nb, &nt) == 3) {
+    if (nb >= 1 && nb <= kMaxBranches && (nt == 128 || nt == 256)) g_tune_cache[sig] = TuneCfg{nb, nt};
+  }
+  fclose(fp);
+}
+
+void append_tune_file(const std::string& sig, const TuneCfg& c) {  // under g_tune_mu
+  const char* path = getenv("GNMPPI_TUNE_FILE");
+  if (!path || !*path) return;
+  FILE* fp = fopen(path, "a");
+  if (!fp) return;
+  fprintf(fp, "%s %d %d\n", sig.c_str(), c.branches, c.solve_nt);
+  fclose(fp);
+}
+
+}  // namespace
+
+static void drop_graph(gnmppi_t h) {
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+}
+
+// Minimum over reps of the device time of the masked phases of iteration 0.
+static gnmppi_status time_phases(gnmppi_t h, unsigned mask, int reps, double* best_ms) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e300;
+  gnmppi_status st = GNMPPI_OK;
+  for (int r = 0; r <= reps && st == GNMPPI_OK; ++r) {  // r = 0 warms up
+    cudaEventRecord(e0, h->stream);
+    st = launch_iteration(h, 0, 0, nullptr, mask);
+    cudaEventRecord(e1, h->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(h, GNMPPI_E_CUDA, "autotune timing failed");
+    float ms = 0.f;
+    if (st == GNMPPI_OK && r > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best = std::min(best, (double)ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *best_ms = best;
+  return st;
+}
+
+extern "C" gnmppi_status gnmppi_tune_set(gnmppi_t h, int32_t branches, int32_t solve_nt) {
+  if (!h) return GNMPPI_E_ARG;
+  if (branches < 1 || branches > kMaxBranches) return fail(h, GNMPPI_E_ARG, "branches must be in 1..%d", kMaxBranches);
+  if (solve_nt != 128 && solve_nt != 256) return fail(h, GNMPPI_E_ARG, "solve_nt must be 128 or 256");
+  set_branches(h, branches);
+  h->tune.solve_nt = solve_nt;
+  drop_graph(h);
+  char buf[160];
+  snprintf(buf, sizeof(buf), "{\"source\": \"set\", \"branches\": %d, \"solve_nt\": %d}", h->tune.branches,
+           h->tune.solve_nt);
+  h->tune_report = buf;
+  return GNMPPI_OK;
+}
+
+extern "C" gnmppi_status gnmppi_autotune(gnmppi_t h, int32_t mem, const double* x0, const double* xref,
+                                         const double* U, const double* sigma, int32_t reps) {
+  if (!h) return GNMPPI_E_ARG;
+  if (reps <= 0) reps = 3;
+  const std::string sig = tune_signature(h);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    read_tune_file();
+    auto it = g_tune_cache.find(sig);
+    if (it != g_tune_cache.end()) {
+      set_branches(h, it->second.branches);
+      h->tune.solve_nt = it->second.solve_nt;
+      drop_graph(h);
+      char buf[512];
+      snprintf(buf, sizeof(buf), "{\"source\": \"cache\", \"signature\": \"%s\", \"branches\": %d, \"solve_nt\": %d}",
+               sig.c_str(), h->tune.branches, h->tune.solve_nt);
+      h->tune_report = buf;
+      return GNMPPI_OK;
+    }
+  }
+  // every intermediate of iteration 0 from the caller's inputs, then timings
+  gnmppi_status st = load_inputs(h, mem, x0, xref, U, sigma);
+  if (st != GNMPPI_OK) return st;
+  st = launch_nominal(h);
+  if (st != GNMPPI_OK) return st;
+  st = launch_iteration(h, 0, 0, nullptr, kAllPhases & ~(1u << 7));  // everything but the update
+  if (st != GNMPPI_OK) return st;
+  CK(cudaStreamSynchronize(h->stream));
+  std::string rows;
+  char buf[256];
+  // 1. concurrent branches for the rollout groups (samples + line search)
+  const int ng = (int)h->groups.size();
+  int best_nb = 1;
+  if (ng > 1) {
+    double best = 1e300;
+    for (int nb : {1, 2, 4, 8}) {
+      if (nb > 1 && nb / 2 >= ng) break;
+      set_branches(h, nb);
+      double ms = 0.0;
+      st = time_phases(h, (1u << 0) | (1u << 6), reps, &ms);
+      if (st != GNMPPI_OK) return st;
+      snprintf(buf, sizeof(buf), "%s{\"branches\": %d, \"ms\": %.4f}", rows.empty() ? "" : ", ", nb, ms);
+      rows += buf;
+      if (ms < best * 0.98) {  // keep fewer branches unless more win clearly
+        best = ms;
+        best_nb = nb;
+      }
+    }
+  }
+  set_branches(h, best_nb);
+  // 2. k_solve CTA shape
+  int best_nt = 256;
+  {
+    double best = 1e300;
+    for (int nt : {256, 128}) {
+      h->tune.solve_nt = nt;
+      double ms = 0.0;
+      st = time_phases(h, 1u << 5, reps, &ms);
+      if (st != GNMPPI_OK) return st;
+      snprintf(buf, sizeof(buf), "%s{\"solve_nt\": %d, \"ms\": %.4f}", rows.empty() ? "" : ", ", nt, ms);
+      rows += buf;
+      if (ms < best * 0.98) {
+        best = ms;
+        best_nt = nt;
+      }
+    }
+  }
+  h->tune.solve_nt = best_nt;
+  st = check_timeout(h);
+  if (st != GNMPPI_OK) return st;
+  drop_graph(h);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[sig] = h->tune;
+    append_tune_file(sig, h->tune);
+  }
+  h->tune_report = std::string("{\"source\": \"timed\", \"signature\": \"") + sig + "\", \"branches\": " +
+                   std::to_string(h->tune.branches) + ", \"solve_nt\": " + std::to_string(h->tune.solve_nt) +
+                   ", \"candidates\": [" + rows + "]}";
+  return GNMPPI_OK;
+}
+
+extern "C" gnmppi_status gnmppi_tune_report(gnmppi_t h, char* buf, int32_t cap) {
+  if (!h || !buf || cap <= 0) return GNMPPI_E_ARG;
+  std::string r = h->tune_report;
+  if (r.empty()) {
+    char b[160];
+    snprintf(b, sizeof(b), "{\"source\": \"default\", \"branches\": %d, \"solve_nt\": %d}", h->tune.branches,
+             h->tune.solve_nt);
+    r = b;
+  }
+  if ((int32_t)r.size() + 1 > cap) return fail(h, GNMPPI_E_ARG, "report needs %d bytes", (int)r.size() + 1);
+  memcpy(buf, r.c_str(), r.size() + 1);
+  return GNMPPI_OK;
 }

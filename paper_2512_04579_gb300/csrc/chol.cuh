@@ -80,14 +80,14 @@ __device__ __noinline__ bool diag_factor(double* L, double* invd, double* Yp, in
 }
 
 // Panel rows below the diagonal block at p0: L21 = A21 L11^-T, i.e.
-// v_c = sum_{q <= c} a_q Y[c][q] with Y = L11^-1.  Called by all 256 threads.
-// Short panels split each row's 16 outputs over R = 2 or 4 warps (a
-// warp-uniform residue class of c) so that their FP64 work still reaches all
-// four sub-partitions of the SM.
+// v_c = sum_{q <= c} a_q Y[c][q] with Y = L11^-1.  Called by every thread of
+// the CTA (4 or 8 warps).  Short panels split each row's 16 outputs over R = 2
+// or 4 warps (a warp-uniform residue class of c) so that their FP64 work
+// still reaches all four sub-partitions of the SM.
 __device__ __forceinline__ void panel_rows(double* L, const double* Yp, int n, int p0, int nb) {
   const int r0 = p0 + nb, m = n - r0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (m > 128) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  if (m > 16 * nwarp) {
     for (int i = r0 + (int)threadIdx.x; i < n; i += (int)blockDim.x) {
       double* Li = L + pk(i, p0);
       double a[CNB];
@@ -105,8 +105,8 @@ __device__ __forceinline__ void panel_rows(double* L, const double* Yp, int n, i
     }
     return;
   }
-  // m <= 128: one row per thread group; every thread reads its row before any writes
-  const int R = (m > 64) ? 2 : 4;
+  // m <= 16 nwarp: one row per thread group; every thread reads its row before any writes
+  const int R = (m > 8 * nwarp) ? 2 : 4;
   const int j = warp % R;
   const int i = r0 + (warp / R) * 32 + lane;
   const bool has = (m > 0) && (i < n);
@@ -196,10 +196,10 @@ __device__ __forceinline__ void trailing_update(double* L, int n, int p0, int nb
 // Right-looking blocked Cholesky of the packed lower matrix in L, in place,
 // with look-ahead: per panel p, (1) all warps form the panel rows, (2) all
 // warps reduce the next block column, (3) warp 0 factors the next diagonal
-// block (and inverts it) while warps 1-7 reduce the rest of the trailing
-// matrix.  invd[i] = 1 / L[i][i]; Y holds the inverted diagonal blocks
-// (CNB2 doubles per panel).  Returns false, uniformly over the CTA, on a
-// pivot that is not positive and finite.  256 threads.
+// block (and inverts it) while the other warps reduce the rest of the
+// trailing matrix.  invd[i] = 1 / L[i][i]; Y holds the inverted diagonal
+// blocks (CNB2 doubles per panel).  Returns false, uniformly over the CTA, on
+// a pivot that is not positive and finite.  128 or 256 threads.
 __device__ bool chol_factor(double* L, double* invd, double* Y, int n, int* fail) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int np = (n + CNB - 1) / CNB;

@@ -47,6 +47,8 @@ struct InstState {
   double C_new, alpha;
   int32_t n_masked, status, chol_retries, j_star;
   int32_t jac_mode_used, total_masked, total_retries, iters;
+  int32_t lsq_broken;  // the LSQ system broke down earlier in this solve
+  int32_t pad;
 };
 
 // Problem-wide constants.

@@ -348,13 +348,15 @@ __device__ __forceinline__ double srow_dot(const float* S, const double*, const 
          (((double)l[0] + (double)l[1]) + ((double)l[2] + (double)l[3]));
 }
 
-// One CTA (256 threads) per instance, two CTAs per SM.  The packed factor and
-// the inverted diagonal blocks live in a per-instance global scratch (L1/L2
-// resident); shared memory holds only the vectors, so a second instance on
-// the SM keeps the FP64 pipe busy through this one's latency-bound steps.
-// Instances run in the order a.order gives (largest n first).
-template <typename TA>
-__global__ void __launch_bounds__(256, 2) k_solve(SolveArgs a) {
+// One CTA of NT threads per instance: 256 threads with two CTAs per SM, or
+// 128 with four (the autotuner picks; small systems pack better).  The packed
+// factor and the inverted diagonal blocks live in a per-instance global
+// scratch (L1/L2 resident); shared memory holds only the vectors, so the
+// other instances on the SM keep the FP64 pipe busy through this one's
+// latency-bound steps.  Instances run in the order a.order gives (largest n
+// first).
+template <typename TA, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_solve(SolveArgs a) {
   const int b = a.order[blockIdx.x];
   InstState& st = a.st[b];
   if (st.status != 0) return;
@@ -382,15 +384,28 @@ __global__ void __launch_bounds__(256, 2) k_solve(SolveArgs a) {
   double lam = a.cs.lambda;
   int retries = 0;
   bool ok = false;
-  for (; retries <= 6; ++retries) {
-    build_system(A, S2, s, I.lsq != 0, Keff, lam, Hp, L, n);
-    __syncthreads();
-    if (chol_factor(L, invd, Y, n, &fail)) {
-      ok = true;
-      break;
+  // Eq. 9 assumes J^T J positive definite.  An LSQ system with no factor at
+  // any damping (K' barely above n leaves S nearly singular, and reduced
+  // precision then leaves P^T P + lambda S^2 indefinite) takes the printed
+  // Monte Carlo form J = P Sigma^-1 / K', for this and the remaining
+  // iterations of the solve (K' and n, which cause it, do not change).
+  bool lsq = I.lsq != 0 && st.lsq_broken == 0;
+  for (int pass = 0; pass < 2 && !ok; ++pass) {
+    if (pass == 1) {
+      if (!lsq) break;
+      lsq = false;
+      lam = a.cs.lambda;
     }
-    lam *= 10.0;
-    __syncthreads();
+    for (retries = 0; retries <= 6; ++retries) {
+      build_system(A, S2, s, lsq, Keff, lam, Hp, L, n);
+      __syncthreads();
+      if (chol_factor(L, invd, Y, n, &fail)) {
+        ok = true;
+        break;
+      }
+      lam *= 10.0;
+      __syncthreads();
+    }
   }
   if (!ok) {
     if (tid == 0) {
@@ -432,7 +447,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(SolveArgs a) {
   double dsq = 0.0;
   for (int i = tid; i < n; i += blockDim.x) {
     double acc;
-    if (I.lsq) acc = srow_dot(P + (int64_t)i * I.ldP + I.nR, x, yh, yl, n);
+    if (lsq) acc = srow_dot(P + (int64_t)i * I.ldP + I.nR, x, yh, yl, n);
     else acc = Keff * s[i] * s[i] * x[i];
     a.delta[I.o_U + i] = acc;
     a.y[I.o_U + i] = x[i];
@@ -443,7 +458,8 @@ __global__ void __launch_bounds__(256, 2) k_solve(SolveArgs a) {
     st.chol_retries = retries;
     st.lambda_used = lam;
     st.step_norm = sqrt(dsq);
-    st.jac_mode_used = I.lsq ? 0 : 1;
+    st.jac_mode_used = lsq ? 0 : 1;
+    if (I.lsq && !lsq) st.lsq_broken = 1;
   }
 }
 

@@ -27,7 +27,8 @@ EXPORTS = ["gnmppi_create", "gnmppi_layout", "gnmppi_solve", "gnmppi_solve_maske
            "gnmppi_destroy", "gnmppi_last_error", "gnmppi_status_string", "gnmppi_version", "gnmppi_mlp_create",
            "gnmppi_mlp_num_params", "gnmppi_mlp_set_params", "gnmppi_mlp_get_params", "gnmppi_mlp_set_normalization",
            "gnmppi_mlp_forward", "gnmppi_mlp_loss_grad", "gnmppi_mlp_train_step", "gnmppi_mlp_warm_start",
-           "gnmppi_mlp_destroy", "gnmppi_mlp_last_error"]
+           "gnmppi_mlp_destroy", "gnmppi_mlp_last_error", "gnmppi_autotune", "gnmppi_tune_set",
+           "gnmppi_tune_report"]
 
 
 class Problem(C.Structure):
@@ -95,6 +96,12 @@ def load(path: str | None = None):
     L.gnmppi_status_string.argtypes = [C.c_int32]
     L.gnmppi_status_string.restype = C.c_char_p
     L.gnmppi_version.restype = C.c_int32
+    L.gnmppi_autotune.argtypes = [vp, C.c_int32, vp, vp, vp, vp, C.c_int32]
+    L.gnmppi_autotune.restype = C.c_int32
+    L.gnmppi_tune_set.argtypes = [vp, C.c_int32, C.c_int32]
+    L.gnmppi_tune_set.restype = C.c_int32
+    L.gnmppi_tune_report.argtypes = [vp, C.c_char_p, C.c_int32]
+    L.gnmppi_tune_report.restype = C.c_int32
     for f in ("gnmppi_create", "gnmppi_layout", "gnmppi_solve", "gnmppi_step", "gnmppi_cost", "gnmppi_debug_read"):
         getattr(L, f).restype = C.c_int32
     L.gnmppi_mlp_create.argtypes = [C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_int32, vp,
@@ -239,6 +246,28 @@ def gnmppi_solve(h, mem, x0, xref, U, sigma=None, batch: int | None = None):
     st = load().gnmppi_solve(h, mem, _ptr(x0), _ptr(xref), _ptr(U), _ptr(sigma), rep)
     _check(h, st, "gnmppi_solve")
     return st, rep
+
+
+def gnmppi_autotune(h, mem, x0, xref, U, sigma=None, reps: int = 3) -> dict:
+    """Pick the handle's launch configuration by timing (see the C header);
+    returns the report as a dict."""
+    st = load().gnmppi_autotune(h, mem, _ptr(x0), _ptr(xref), _ptr(U), _ptr(sigma), reps)
+    _check(h, st, "gnmppi_autotune")
+    return gnmppi_tune_report(h)
+
+
+def gnmppi_tune_set(h, branches: int, solve_nt: int):
+    st = load().gnmppi_tune_set(h, branches, solve_nt)
+    _check(h, st, "gnmppi_tune_set")
+
+
+def gnmppi_tune_report(h) -> dict:
+    import json
+
+    buf = C.create_string_buffer(8192)
+    st = load().gnmppi_tune_report(h, buf, len(buf))
+    _check(h, st, "gnmppi_tune_report")
+    return json.loads(buf.value.decode())
 
 
 def gnmppi_solve_masked(h, mem, x0, xref, U, sigma, active, batch: int):

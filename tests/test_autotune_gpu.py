@@ -1,0 +1,85 @@
+"""GPU: the batched-launch autotuner.  The launch configuration (concurrent
+graph branches for the per-size rollout groups, Cholesky CTA shape) changes
+scheduling only, so every configuration must give bitwise the same solve;
+the tuner must pick one of its candidates, and a second handle with the same
+instance shapes must take the cached choice without timing."""
+import numpy as np
+import pytest
+
+from paper_2512_04579_gb300 import gnmppi as G
+from paper_2512_04579_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2512_04579_gb300 import build as B
+
+    B.build()
+    return G.load()
+
+
+def uneven_handle(seed, batch, iterations=3):
+    Ms, Ns, Ks, x0s, tgts = I.uneven_chain_instances(seed, batch)
+    shapes = [(int(Ns[b]), int(Ms[b]), int(Ks[b])) for b in range(batch)]
+    prob = G.chain_problem(M=int(Ms[0]), N=int(Ns[0]), K=int(Ks[0]), iterations=iterations, lam=1e-3, sigma0=0.2,
+                           seed=seed, precision=G.PREC_FP32)
+    h = G.gnmppi_create(prob, batch, shapes)
+    nU = int(sum(2 * n for n in Ns))
+    return h, np.concatenate(x0s), np.concatenate(tgts), nU, len(set(int(m) for m in Ms))
+
+
+def solve(h, x0, xr, nU, batch):
+    U = np.zeros(nU)
+    st, rep = G.gnmppi_solve(h, G.MEM_HOST, x0, xr, U, None, batch)
+    assert st == 0
+    return U, [r.C_final for r in rep]
+
+
+def test_launch_configuration_does_not_change_the_solve():
+    seed, batch = I.BASE_SEED + 77, 24
+    h, x0, xr, nU, ngroups = uneven_handle(seed, batch)
+    assert ngroups > 4  # several rollout groups, so the branch count matters
+    try:
+        assert G.gnmppi_tune_report(h)["source"] == "default"
+        ref_U, ref_C = None, None
+        for cfg in [(1, 256), (4, 128), (8, 256), (2, 128)]:
+            G.gnmppi_tune_set(h, *cfg)
+            rep = G.gnmppi_tune_report(h)
+            assert rep["source"] == "set" and (rep["branches"], rep["solve_nt"]) == cfg
+            U, C = solve(h, x0, xr, nU, batch)
+            if ref_U is None:
+                ref_U, ref_C = U, C
+            else:
+                assert np.array_equal(U, ref_U), f"configuration {cfg} changed the solve"
+                assert C == ref_C
+        rep = G.gnmppi_autotune(h, G.MEM_HOST, x0, xr, np.zeros(nU))
+        assert rep["source"] == "timed"
+        assert rep["branches"] in (1, 2, 4, 8) and rep["solve_nt"] in (128, 256)
+        timed = [c for c in rep["candidates"] if "branches" in c]
+        assert [c["branches"] for c in timed][:2] == [1, 2] and all(c["ms"] > 0 for c in rep["candidates"])
+        U, C = solve(h, x0, xr, nU, batch)
+        assert np.array_equal(U, ref_U)
+        # a second handle with the same shapes takes the cached choice
+        h2, *_ = uneven_handle(seed, batch)
+        try:
+            rep2 = G.gnmppi_autotune(h2, G.MEM_HOST, x0, xr, np.zeros(nU))
+            assert rep2["source"] == "cache"
+            assert (rep2["branches"], rep2["solve_nt"]) == (rep["branches"], rep["solve_nt"])
+            U2, _ = solve(h2, x0, xr, nU, batch)
+            assert np.array_equal(U2, ref_U)
+        finally:
+            G.gnmppi_destroy(h2)
+    finally:
+        G.gnmppi_destroy(h)
+
+
+def test_tune_set_rejects_values_out_of_range():
+    h, *_ = uneven_handle(I.BASE_SEED + 78, 4, iterations=1)
+    try:
+        for cfg in [(0, 256), (9, 256), (2, 64), (2, 512)]:
+            with pytest.raises(G.GnmppiError):
+                G.gnmppi_tune_set(h, *cfg)
+    finally:
+        G.gnmppi_destroy(h)

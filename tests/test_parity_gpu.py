@@ -385,3 +385,40 @@ def test_bf16_long_chain_full_horizon_iteration():
     np.testing.assert_allclose(Cs, it.C_samp, rtol=TOLRED)
     assert rep[0].C_new < rep[0].C_nom and it.C_new < it.C_nom
     assert rep[0].C_new == pytest.approx(it.C_new, rel=1e-2)
+
+
+def test_reduced_precision_lsq_breakdown_takes_the_printed_form():
+    """K' = 256 pairs barely above n = 246: S is nearly singular, and with
+    FP32 operands P^T P + lambda S^2 has no Cholesky factor at any damping.
+    The iteration then takes the printed Monte Carlo form J = P Sigma^-1 / K'
+    (jac_mode_used 1) and must agree with the oracle run in that form; the
+    FP64 mode still solves the LSQ system, like the oracle in AUTO mode."""
+    seed = I.BASE_SEED + 77
+    Ms, Ns, Ks, x0s, tgts = I.uneven_chain_instances(seed, 24)
+    b = 23
+    M, N, K = int(Ms[b]), int(Ns[b]), int(Ks[b])
+    assert (M, N, K) == (8, 123, 512)
+    m = O.chain(M=M, N=N)
+    it_sig = O.iteration(m, O.Options(K=K, lam=1e-3, seed=seed, jac_mode="sigma"), x0s[b], tgts[b], np.zeros(m.n),
+                         0.2, inst=0, it=0)
+    it_auto = O.iteration(m, O.Options(K=K, lam=1e-3, seed=seed), x0s[b], tgts[b], np.zeros(m.n), 0.2, inst=0, it=0)
+    assert it_sig.status == 0 and it_auto.status == 0 and it_auto.jac_mode_used == 0
+    for prec, jm, ref in ((G.PREC_FP32, 1, it_sig), (G.PREC_FP64, 0, it_auto)):
+        gp = G.chain_problem(M=M, N=N, K=K, iterations=1, lam=1e-3, sigma0=0.2, seed=seed, precision=prec)
+        s = G.Solver(gp, 1)
+        st, U, rep = s.step(x0s[b], tgts[b], np.zeros(m.n), np.full(m.n, 0.2), 0)
+        s.close()
+        assert st == 0 and rep[0].status == 0
+        assert rep[0].jac_mode_used == jm
+        assert rep[0].C_nom == pytest.approx(ref.C_nom, rel=TOLRED)
+        assert rep[0].C_new < rep[0].C_nom
+        if prec == G.PREC_FP64:
+            # the scaled system (P^T P + lambda S^2) y = -b has kappa up to
+            # kappa(S)^2 kappa(J^T J + lambda I) ~ 3e7 * 470 here, so the step,
+            # and the cost after it, agree to ~kappa u = 1.6e-6
+            assert rep[0].C_new == pytest.approx(ref.C_new, rel=2e-6)
+        else:
+            # TF32 contraction operands give J ~1e-3 relative error, and the
+            # printed form has kappa(J^T J + lambda I) = 1.1e4 for this draw:
+            # the step moves by a few percent
+            assert rep[0].C_new == pytest.approx(ref.C_new, rel=5e-2)
