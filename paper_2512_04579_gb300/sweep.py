@@ -12,6 +12,7 @@ once), the FP64 Cholesky against the FP64 pipe (2 DFMA per clock per SM).
 Orchestration only; every kernel runs in libgnmppi.so.
 
   python -m paper_2512_04579_gb300.sweep [--prec bf16|fp32|fp64] [--budget-gb 60]
+  python -m paper_2512_04579_gb300.sweep --gap --prec bf16   (cost gap vs the FP64 mode)
 """
 from __future__ import annotations
 
@@ -87,12 +88,42 @@ def run_point(M, K, prec, N=200, budget_gb=60.0, iters=3, seed=I.BASE_SEED + 4):
     }
 
 
+def run_gap(M, K, prec, N=200, batch=4, T=10, seed=I.BASE_SEED + 4):
+    """Cost gap of a reduced-precision solve against the FP64 reference mode:
+    the same instances, seeds and Philox noise, T iterations in each mode; the
+    final costs are re-evaluated in FP64.  gap = (C_prec - C_fp64) / C_fp64."""
+    import torch
+
+    x0, tgt = I.chain_instances(seed, batch, M)
+    dx = torch.tensor(x0.ravel(), dtype=torch.float64, device="cuda")
+    dt = torch.tensor(tgt.ravel(), dtype=torch.float64, device="cuda")
+    out = {}
+    for name, pr in (("fp64", G.PREC_FP64), ("prec", prec)):
+        prob = G.chain_problem(M=M, N=N, K=K, iterations=T, lam=1e-3, sigma0=0.2, seed=seed, precision=pr)
+        h = G.gnmppi_create(prob, batch)
+        dU = torch.zeros(batch * 2 * N, dtype=torch.float64, device="cuda")
+        G.gnmppi_solve(h, G.MEM_DEVICE, dx, dt, dU, None)
+        C = torch.empty(batch, dtype=torch.float64, device="cuda")
+        G.gnmppi_cost(h, G.MEM_DEVICE, dx, dt, dU, C)
+        out[name] = C.cpu().numpy()
+        G.gnmppi_destroy(h)
+    g = (out["prec"] - out["fp64"]) / out["fp64"]
+    return {"M": M, "K": K, "N": N, "batch": batch, "iterations": T,
+            "precision": {G.PREC_BF16: "bf16", G.PREC_FP32: "fp32"}[prec],
+            "C_fp64": out["fp64"].tolist(), "C_prec": out["prec"].tolist(),
+            "gap_median": float(np.median(g)), "gap_max_abs": float(np.max(np.abs(g)))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32", "fp64"])
     ap.add_argument("--budget-gb", type=float, default=60.0)
     ap.add_argument("--M", type=int, nargs="*", default=[16, 32, 64])
     ap.add_argument("--K", type=int, nargs="*", default=[4096, 16384, 65536])
+    ap.add_argument("--gap", action="store_true",
+                    help="cost gap of --prec solves against the FP64 reference mode instead of timings")
+    ap.add_argument("--gap-batch", type=int, default=4)
+    ap.add_argument("--gap-iters", type=int, default=10)
     args = ap.parse_args()
     from . import build as B
 
@@ -101,7 +132,10 @@ def main():
     prec = {"bf16": G.PREC_BF16, "fp32": G.PREC_FP32, "fp64": G.PREC_FP64}[args.prec]
     for M in args.M:
         for K in args.K:
-            print(json.dumps(run_point(M, K, prec, budget_gb=args.budget_gb)), flush=True)
+            if args.gap:
+                print(json.dumps(run_gap(M, K, prec, batch=args.gap_batch, T=args.gap_iters)), flush=True)
+            else:
+                print(json.dumps(run_point(M, K, prec, budget_gb=args.budget_gb)), flush=True)
 
 
 if __name__ == "__main__":
