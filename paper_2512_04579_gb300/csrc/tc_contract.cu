@@ -242,23 +242,32 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
   }
   __syncwarp();
 
-  // ---------------- epilogue: TMEM -> registers -> global rows of D
+  // ---------------- epilogue: TMEM -> registers -> shared -> coalesced rows of D
+  // Once `done` fires every stage has been consumed, so the operand ring is
+  // free: each warp transposes its 32 x 32 slices through a padded staging
+  // block and writes whole rows (lane = column) instead of one column of 32
+  // rows per store.
   const bool ok = mbar_wait(done, 0, abort, false);
   tc_fence_after();
   // tcgen05.ld is warp-collective: the whole warp takes the same branch
   if (__all_sync(0xffffffffu, ok && !*abort)) {
-    const int row = tl.y * BM + warp * 32 + lane;
-    TOut* out = (J.out_sel ? D2 : D) + J.out_off + (int64_t)row * J.ldc;
+    TOut* stg = reinterpret_cast<TOut*>(base) + warp * 32 * 33;
+    const int row0 = tl.y * BM + warp * 32;
+    TOut* out = (J.out_sel ? D2 : D) + J.out_off;
 #pragma unroll 1
     for (int c = 0; c < BN / 32; ++c) {
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-      const int col0 = tl.z * BN + c * 32;
-      if (row < J.M) {
 #pragma unroll
-        for (int q = 0; q < 32; ++q)
-          if (col0 + q < J.Nc) out[col0 + q] = (TOut)__uint_as_float(v[q]);
+      for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = (TOut)__uint_as_float(v[q]);
+      __syncwarp();
+      const int col = tl.z * BN + c * 32 + lane;
+      if (col < J.Nc) {
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr)
+          if (row0 + rr < J.M) out[(int64_t)(row0 + rr) * J.ldc + col] = stg[rr * 33 + lane];
       }
+      __syncwarp();
     }
   } else if (threadIdx.x == 0) {
     atomicExch(err, 1);
