@@ -37,6 +37,11 @@ CSTAR_UNEVEN = os.path.join(ROOT, "tests", "golden", "chain_uneven_cstar.txt")
 WORKLOAD = "chain M=10 N=100 nu=2 K=2048 T=30 sigma0=0.2 lambda=1e-3"
 
 
+# DRAM read + write of one k_samples launch of the default workload (256 instances), from one
+# full-size ncu capture of this command (one-pass metrics); null for other batch sizes.
+K_SAMPLES_TRAFFIC_B256 = 2.2796e9
+
+
 def load_cstar(path=CSTAR):
     rows = np.loadtxt(path, comments="#")
     return rows[:, 0].astype(int), rows[:, 1], rows[:, 2]
@@ -400,7 +405,9 @@ def run_gnmppi(args):
         "phases_ms_per_iteration": phases,
         "roofline": {"kernel": "k_samples (RK4 rollouts + residual/cost/dR/W)", "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": None,
+                     "traffic": K_SAMPLES_TRAFFIC_B256 if batch == 256 else None,
+                     "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size k_samples "
+                                     "launch at 256 instances, bytes per launch",
                      "peak_note": "FP32 152 SMs x 128 lanes x 2 flop/FMA at the %.0f MHz maximum SM clock" % sm_max},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
     }
