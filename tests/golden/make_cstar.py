@@ -78,8 +78,10 @@ if __name__ == "__main__":
     out = os.path.join(HERE, f"{workload}_cstar.txt")
     seed_note = {"chain_m10": "2512045790+1", "chain_m10_fixed": "2512045790+3 (fixed target, eval stream)",
                  "chain_uneven": "2512045790+2 (per-instance M, N, K)"}[workload]
+    shape = ("chain M, N, K per instance (inputs.uneven_chain_instances)" if workload == "chain_uneven"
+             else f"chain M={M} N={N} K={K}")
     with open(out, "w") as f:
-        f.write(f"# {workload}: chain M={M} N={N} K={K} T={T} sigma0={SIGMA0} lambda={LAM} seed={seed_note} "
+        f.write(f"# {workload}: {shape} T={T} sigma0={SIGMA0} lambda={LAM} seed={seed_note} "
                 f"batch={BATCH}\n")
         f.write("# written by tests/golden/make_cstar.py from the FP64 oracle: b C_gn C_star\n")
         for b, cg, cs in rows:
