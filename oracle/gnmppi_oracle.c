@@ -435,10 +435,16 @@ static int all_finite(const double* v, int n) {
 int32_t orc_iteration(const orc_model* m, const orc_options* o, const double* x0, const double* xref,
                       double* U, const double* s, uint32_t inst, uint32_t it, orc_record* rec) {
   const int n = orc_n(m), nR = orc_nR(m);
-  if (n <= 0 || nR <= 0 || o->K <= 0 || o->L <= 0) return ORC_E_ARG;
+  const int sigma_pts = o->sampling == ORC_SAMPLE_SIGMA;
+  if (n <= 0 || nR <= 0 || (o->K <= 0 && !sigma_pts) || o->L <= 0) return ORC_E_ARG;
   const int anti = o->antithetic ? 1 : 0;
-  const int Kp = anti ? o->K / 2 : o->K; /* pairs (antithetic) or samples */
+  if (sigma_pts && !anti) return ORC_E_ARG;
+  /* pairs (antithetic) or samples; the sigma points are the n pairs +-sqrt(n) s_i e_i */
+  const int Kp = sigma_pts ? n : (anti ? o->K / 2 : o->K);
   if (Kp <= 0) return ORC_E_ARG;
+  const int mppi_step = o->method == ORC_METHOD_MPPI;
+  const int Lc = mppi_step ? 1 : o->L; /* MPPI takes its step whole: alpha = 1 */
+  const int mono = mppi_step ? 0 : o->monotone;
   const int nsamp = anti ? 2 * Kp : Kp;
 
   double* r = (double*)calloc((size_t)nR, sizeof(double));
@@ -470,7 +476,11 @@ int32_t orc_iteration(const orc_model* m, const orc_options* o, const double* x0
     double* Up = (double*)malloc(sizeof(double) * (size_t)n);
     double* Rp = (double*)malloc(sizeof(double) * (size_t)nR);
     double* Rm = (double*)malloc(sizeof(double) * (size_t)nR);
-    orc_normals(o->seed, inst, it, (uint32_t)mi, n, z);
+    if (sigma_pts) {
+      for (int j = 0; j < n; ++j) z[j] = (j == mi) ? sqrt((double)n) : 0.0;
+    } else {
+      orc_normals(o->seed, inst, it, (uint32_t)mi, n, z);
+    }
     double* Wm = W + (size_t)mi * n;
     for (int j = 0; j < n; ++j) Wm[j] = s[j] * z[j];
     for (int j = 0; j < n; ++j) Up[j] = U[j] + Wm[j];
@@ -515,20 +525,20 @@ int32_t orc_iteration(const orc_model* m, const orc_options* o, const double* x0
   /* 3. softmin diagnostics over every evaluated sample cost */
   double st4[4] = {0, 0, 0, 0};
   orc_softmin(nsamp, Cs, valid, o->tau, wts, st4);
-  if (rec && rec->mppi_dir) {
-    for (int j = 0; j < n; ++j) rec->mppi_dir[j] = 0.0;
-    if (st4[1] > 0.0) {
-      for (int mi = 0; mi < Kp; ++mi) {
-        const double* Wm = W + (size_t)mi * n;
-        const double wsum = anti ? (wts[2 * mi] - wts[2 * mi + 1]) : wts[mi];
-        for (int j = 0; j < n; ++j) rec->mppi_dir[j] += wsum * Wm[j];
-      }
-      for (int j = 0; j < n; ++j) rec->mppi_dir[j] /= st4[1];
+  double* mppi = (double*)calloc((size_t)n, sizeof(double));
+  if (st4[1] > 0.0) {
+    for (int mi = 0; mi < Kp; ++mi) {
+      const double* Wm = W + (size_t)mi * n;
+      const double wsum = anti ? (wts[2 * mi] - wts[2 * mi + 1]) : wts[mi];
+      for (int j = 0; j < n; ++j) mppi[j] += wsum * Wm[j];
     }
+    for (int j = 0; j < n; ++j) mppi[j] /= st4[1];
   }
+  if (rec && rec->mppi_dir) memcpy(rec->mppi_dir, mppi, sizeof(double) * (size_t)n);
 
-  /* 4. P = sum dR_m W_m^T, S = sum W_m W_m^T (sums in sample order) */
-  for (int mi = 0; mi < Kp; ++mi) {
+  /* 4. P = sum dR_m W_m^T, S = sum W_m W_m^T (sums in sample order);
+   *    the MPPI step (Method C) needs neither */
+  for (int mi = 0; mi < (mppi_step ? 0 : Kp); ++mi) {
     const double* Wm = W + (size_t)mi * n;
     const double* dRm = dR + (size_t)mi * nR;
     for (int i = 0; i < nR; ++i) {
@@ -540,7 +550,7 @@ int32_t orc_iteration(const orc_model* m, const orc_options* o, const double* x0
       for (int j = 0; j < n; ++j) S[(size_t)i * n + j] += a * Wm[j];
     }
   }
-  int jm = o->jac_mode;
+  int jm = mppi_step ? -1 : o->jac_mode; /* -1: no Jacobian (MPPI step) */
   if (jm == ORC_JAC_AUTO) jm = (Kp >= n) ? ORC_JAC_LSQ : ORC_JAC_SIGMA;
   if (Keff == 0) status = ORC_E_NONFINITE;
   if (status == ORC_OK && jm == ORC_JAC_LSQ) {
@@ -567,7 +577,7 @@ int32_t orc_iteration(const orc_model* m, const orc_options* o, const double* x0
    *    system without a Cholesky factor at any damping falls back to SIGMA */
   double lambda_used = o->lambda;
   int retries = 0;
-  for (int pass = 0; status == ORC_OK && pass < 2; ++pass) {
+  for (int pass = 0; status == ORC_OK && !mppi_step && pass < 2; ++pass) {
     if (pass == 1) {
       if (retries >= 0 || jm != ORC_JAC_LSQ) break;
       jm = ORC_JAC_SIGMA;
@@ -590,31 +600,32 @@ int32_t orc_iteration(const orc_model* m, const orc_options* o, const double* x0
     free(rhs);
   }
   if (status == ORC_OK && retries < 0) status = ORC_E_NOT_PD;
+  if (status == ORC_OK && mppi_step) memcpy(delta, mppi, sizeof(double) * (size_t)n); /* Eq. 5 step */
 
-  /* 6. line search over {gamma^j}; alpha_{j+1} = alpha_j * gamma */
-  const int nl = o->L + (o->monotone ? 1 : 0);
+  /* 6. line search over {gamma^j}; alpha_{j+1} = alpha_j * gamma (MPPI: alpha = 1 only) */
+  const int nl = Lc + (mono ? 1 : 0);
   double* Cl = (double*)malloc(sizeof(double) * (size_t)nl);
   int jstar = -1;
   double alpha_star = 0.0, C_new = C_nom;
   if (status == ORC_OK) {
     double* Ut = (double*)malloc(sizeof(double) * (size_t)n);
     double alpha = 1.0;
-    for (int j = 0; j < o->L; ++j) {
+    for (int j = 0; j < Lc; ++j) {
       for (int i = 0; i < n; ++i) Ut[i] = U[i] + alpha * delta[i];
       Cl[j] = orc_cost(m, x0, xref, Ut);
       alpha *= o->gamma;
     }
-    if (o->monotone) Cl[o->L] = C_nom;
+    if (mono) Cl[Lc] = C_nom;
     double best = INFINITY;
     alpha = 1.0;
     for (int j = 0; j < nl; ++j) {
-      const double aj = (j < o->L) ? alpha : 0.0;
+      const double aj = (j < Lc) ? alpha : 0.0;
       if (Cl[j] < best) { /* strict: ties keep the smaller j */
         best = Cl[j];
         jstar = j;
         alpha_star = aj;
       }
-      if (j < o->L) alpha *= o->gamma;
+      if (j < Lc) alpha *= o->gamma;
     }
     if (jstar < 0) { /* every candidate non-finite */
       status = ORC_E_NONFINITE;
@@ -669,6 +680,7 @@ int32_t orc_iteration(const orc_model* m, const orc_options* o, const double* x0
   free(g);
   free(delta);
   free(wts);
+  free(mppi);
   return status;
 }
 
@@ -687,8 +699,9 @@ int32_t orc_solve(const orc_model* m, const orc_options* o, const double* x0, co
   /* once the LSQ form breaks down (orc_iteration fell back to SIGMA), the
    * rest of the solve uses SIGMA: K' and n, which cause it, do not change */
   orc_options oo = *o;
-  const int Kp = o->antithetic ? o->K / 2 : o->K;
-  const int lsq_chosen = o->jac_mode == ORC_JAC_LSQ || (o->jac_mode == ORC_JAC_AUTO && Kp >= n);
+  const int Kp = o->sampling == ORC_SAMPLE_SIGMA ? n : (o->antithetic ? o->K / 2 : o->K);
+  const int lsq_chosen = o->method == ORC_METHOD_GN &&
+                         (o->jac_mode == ORC_JAC_LSQ || (o->jac_mode == ORC_JAC_AUTO && Kp >= n));
   for (int it = 0; it < o->iterations; ++it) {
     orc_record local;
     memset(&local, 0, sizeof(local));

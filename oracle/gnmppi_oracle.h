@@ -33,6 +33,12 @@ enum {
 };
 
 enum { ORC_JAC_LSQ = 0, ORC_JAC_SIGMA = 1, ORC_JAC_AUTO = 2 };
+/* perturbations: random Philox normals (Method D) or the symmetric sigma
+ * points +-sqrt(n) s_i e_i of a Dirac mixture (Method E, Sec. 5) */
+enum { ORC_SAMPLE_RANDOM = 0, ORC_SAMPLE_SIGMA = 1 };
+/* step: Gauss-Newton (Algorithm 1) or the deterministic MPPI step of Eq. 3/5
+ * (Method C, Sec. 3) */
+enum { ORC_METHOD_GN = 0, ORC_METHOD_MPPI = 1 };
 
 enum {
   ORC_OK = 0,
@@ -65,6 +71,8 @@ typedef struct {
   double gamma;       /* step-length ratio                                  */
   double tau;         /* softmin temperature                                */
   uint64_t seed;
+  int32_t sampling;   /* ORC_SAMPLE_*; sigma points need antithetic, K = 2n */
+  int32_t method;     /* ORC_METHOD_*                                       */
 } orc_options;
 
 /* One Algorithm-1 iteration's outputs.  Array pointers are optional. */

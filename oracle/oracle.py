@@ -52,7 +52,7 @@ class OrcOptions(C.Structure):
     _fields_ = [("K", C.c_int32), ("iterations", C.c_int32), ("L", C.c_int32), ("jac_mode", C.c_int32),
                 ("antithetic", C.c_int32), ("monotone", C.c_int32), ("threads", C.c_int32),
                 ("ir_steps", C.c_int32), ("lam", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
-                ("tau", C.c_double), ("seed", C.c_uint64)]
+                ("tau", C.c_double), ("seed", C.c_uint64), ("sampling", C.c_int32), ("method", C.c_int32)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -190,6 +190,8 @@ class Options:
     gamma: float = 0.5
     tau: float = 1.0
     seed: int = 0
+    sampling: str = "random"  # "random" (Method D) or "sigma" (sigma points, Method E)
+    method: str = "gn"  # "gn" (Algorithm 1) or "mppi" (the MPPI step of Eq. 5, Method C)
 
     def c(self) -> OrcOptions:
         o = OrcOptions()
@@ -198,7 +200,15 @@ class Options:
         o.antithetic, o.monotone, o.threads, o.ir_steps = int(self.antithetic), int(self.monotone), self.threads, \
             self.ir_steps
         o.lam, o.beta, o.gamma, o.tau, o.seed = self.lam, self.beta, self.gamma, self.tau, self.seed
+        o.sampling = {"random": 0, "sigma": 1}[self.sampling]
+        o.method = {"gn": 0, "mppi": 1}[self.method]
         return o
+
+    def pairs(self, n: int) -> int:
+        """Sample pairs (antithetic) or samples per iteration for n unknowns."""
+        if self.sampling == "sigma":
+            return n
+        return self.K // 2 if self.antithetic else self.K
 
 
 # ---------------------------------------------------------------------------
@@ -324,7 +334,7 @@ class Iter:
 
 def _rec(model: Model, opt: Options, want_big: bool):
     n, nR = model.n, model.nR
-    Kp = opt.K // 2 if opt.antithetic else opt.K
+    Kp = opt.pairs(n)
     nl = opt.L + (1 if opt.monotone else 0)
     bufs = {"delta": np.zeros(n), "C_line": np.zeros(nl), "mppi_dir": np.zeros(n),
             "C_samp": np.zeros(2 * Kp if opt.antithetic else Kp)}
@@ -351,8 +361,10 @@ def iteration(model: Model, opt: Options, x0, xref, U, s, inst=0, it=0, want_big
     U = np.array(U, float, copy=True)
     s = np.ascontiguousarray(np.broadcast_to(np.asarray(s, float), (model.n,)), float)
     rec, bufs = _rec(model, opt, want_big)
-    lib().orc_iteration(C.byref(model.c()), C.byref(opt.c()), _p(x0), _p(_xref(model, xref)), _p(U), _p(s), inst,
-                        it, C.byref(rec))
+    st = lib().orc_iteration(C.byref(model.c()), C.byref(opt.c()), _p(x0), _p(_xref(model, xref)), _p(U), _p(s),
+                             inst, it, C.byref(rec))
+    if st != 0 and rec.status == 0:  # rejected before the record was written
+        rec.status = st
     return _to_iter(rec, bufs, U)
 
 

@@ -483,3 +483,71 @@ def test_covariance_shrinks_by_sqrt_beta():
     st, U, Uh, Ch, its = O.solve(m, opt, None, None, [0.2, 0.1], 0.5)
     it2 = O.iteration(m, opt, None, None, Uh[2], 0.5 * 0.36, it=2, want_big=True)
     np.testing.assert_allclose(it2.delta, its[2].delta, rtol=1e-12)
+
+
+# ------------------------------------------- Method E: sigma points (Sec. 5) ---
+def test_sigma_point_jacobian_exact_for_quadratic_rosenbrock():
+    """The symmetric sigma points +-sqrt(n) s_i e_i turn the smoothed Jacobian of
+    Eq. 7 into central differences, exact for a quadratic residual at any step."""
+    m = O.testfun("rosenbrock")
+    u = np.array([0.3, -0.2])
+    it = O.iteration(m, O.Options(K=2, sampling="sigma", seed=2), None, None, u, np.array([0.4, 0.7]),
+                     want_big=True)
+    assert it.status == 0 and it.W.shape == (2, 2)
+    Jex = np.array([[-math.sqrt(2), 0.0], [-2 * math.sqrt(200) * u[0], math.sqrt(200)]])
+    np.testing.assert_allclose(it.J, Jex, rtol=1e-12, atol=1e-12)
+
+
+def test_sigma_point_jacobian_is_central_differences_with_step_sqrt_n_sigma():
+    """Nonlinear pendulum: column i of the Dirac-mixture Jacobian equals
+    (R(U + h_i e_i) - R(U - h_i e_i)) / (2 h_i) with h_i = sqrt(n) s_i,
+    evaluated here directly from the residual; the perturbations are
+    W_i = h_i e_i and the softmin sees all 2n costs."""
+    N = 10
+    m = O.pendulum(N=N)
+    n = m.n
+    x0 = np.array([0.3, -0.1])
+    rng = np.random.default_rng(4)
+    U = rng.normal(0, 0.5, n)
+    s = 0.05 + 0.1 * rng.random(n)
+    it = O.iteration(m, O.Options(K=999, sampling="sigma", seed=9), x0, None, U, s, want_big=True)
+    assert it.status == 0
+    h = math.sqrt(n) * s
+    np.testing.assert_allclose(it.W, np.diag(h), rtol=1e-15, atol=0)
+    Jcd = np.empty((m.nR, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = h[i]
+        Jcd[:, i] = (O.residual(m, x0, None, U + e) - O.residual(m, x0, None, U - e)) / (2 * h[i])
+    np.testing.assert_allclose(it.J, Jcd, rtol=1e-10, atol=1e-12)
+    assert len(it.C_samp) == 2 * n
+
+
+def test_sigma_points_require_antithetic_pairs():
+    m = O.testfun("rosenbrock")
+    it = O.iteration(m, O.Options(K=8, sampling="sigma", antithetic=False), None, None, [0.1, 0.2], 0.3)
+    assert it.status == -1  # ORC_E_ARG
+
+
+# ---------------------------------------------- Method C: MPPI step (Sec. 3) ---
+def test_mppi_step_matches_the_tilted_gaussian_mean_on_a_quadratic_cost():
+    """For C(U) = 1/2 ||G U + h||^2 (Problem IV's affine residual) the MPPI step
+    of Eq. 3 has the closed form (Sigma^-1 + H/tau)^-1 (H/tau)(U* - U), H = G^T G,
+    U* the least-squares minimiser; the empirical step of Eq. 5 over 2e5
+    antithetic pairs must agree within Monte Carlo error, and the iterate takes
+    the step whole (alpha = 1)."""
+    N = 4
+    m, A, B, wq, wr, wqN = _lq_problem(N=N)
+    x0 = np.array([1.0, 0.0])
+    G, hv = _lq_affine_map(A, B, wq, wr, wqN, N, x0)
+    H = G.T @ G
+    Ustar = np.linalg.lstsq(G, -hv, rcond=None)[0]
+    U = np.array([0.4, -0.2, 0.1, 0.3])
+    sig, tau = 0.3, 1.0
+    exact = np.linalg.solve(np.eye(N) / sig ** 2 + H / tau, (H / tau) @ (Ustar - U))
+    it = O.iteration(m, O.Options(K=400000, method="mppi", tau=tau, seed=12, threads=8), x0, None, U, sig)
+    assert it.status == 0 and it.alpha == 1.0 and it.j_star == 0
+    np.testing.assert_allclose(it.delta, it.mppi_dir, rtol=0, atol=0)
+    assert np.linalg.norm(it.delta - exact) <= 1e-2 * np.linalg.norm(exact)
+    np.testing.assert_allclose(it.U_next, U + it.delta, rtol=0, atol=1e-15)
+    assert it.C_new == pytest.approx(O.cost(m, x0, None, U + it.delta), rel=1e-14)
