@@ -76,6 +76,20 @@ enum { GNMPPI_JAC_LSQ = 0, GNMPPI_JAC_SIGMA = 1, GNMPPI_JAC_AUTO = 2 };
 
 enum { GNMPPI_MEM_HOST = 0, GNMPPI_MEM_DEVICE = 1 };
 
+/* Perturbations of the Jacobian estimate (Eq. 7, Sec. 5).
+ *   RANDOM: W_m = s .* z_m, z_m from Philox4x32-10 + Box-Muller (Method D).
+ *   SIGMA:  the symmetric sigma points of a Dirac mixture, W_m = sqrt(n) s_m e_m
+ *           for m < n (K' = n antithetic pairs, K ignored; antithetic required)
+ *           (Method E).  J is then central differences with step sqrt(n) s_m. */
+enum { GNMPPI_SAMPLE_RANDOM = 0, GNMPPI_SAMPLE_SIGMA = 1 };
+
+/* Step of an iteration.
+ *   GN:   Algorithm 1, the damped GGN step with a line search (Eq. 9-11).
+ *   MPPI: the deterministic MPPI step of Eq. 3, estimated by Eq. 5 over the
+ *         same samples and taken whole (alpha = 1, no line search, no
+ *         contraction or Cholesky) (Method C, Sec. 3). */
+enum { GNMPPI_METHOD_GN = 0, GNMPPI_METHOD_MPPI = 1 };
+
 /* Problem and Algorithm-1 options shared by every instance of a handle. */
 typedef struct {
   int32_t dynamics;   /* GNMPPI_DYN_*                                              */
@@ -99,6 +113,8 @@ typedef struct {
   double gamma;       /* step-length ratio in (0, 1)                               */
   double tau;         /* softmin temperature of the sample weights (Eq. 5)         */
   uint64_t seed;      /* Philox key of the noise stream                            */
+  int32_t sampling;   /* GNMPPI_SAMPLE_* (0: random, Method D)                     */
+  int32_t method;     /* GNMPPI_METHOD_* (0: Gauss-Newton, Algorithm 1)            */
 } gnmppi_problem;
 
 /* Per-instance shape of an uneven batch; fields <= 0 take the problem's value. */

@@ -161,6 +161,12 @@ static gnmppi_status validate(const gnmppi_problem* p, int32_t batch, const gnmp
   if (p->iterations < 0) return fail(nullptr, GNMPPI_E_ARG, "iterations must be >= 0");
   if (p->ir_steps < 0 || p->ir_steps > 10) return fail(nullptr, GNMPPI_E_ARG, "ir_steps must be in 0..10");
   if (p->dynamics != GNMPPI_DYN_LINEAR && !(p->dt > 0.0)) return fail(nullptr, GNMPPI_E_ARG, "dt must be > 0");
+  if (p->sampling != GNMPPI_SAMPLE_RANDOM && p->sampling != GNMPPI_SAMPLE_SIGMA)
+    return fail(nullptr, GNMPPI_E_ARG, "unknown sampling");
+  if (p->sampling == GNMPPI_SAMPLE_SIGMA && !p->antithetic)
+    return fail(nullptr, GNMPPI_E_ARG, "sigma points need antithetic pairs");
+  if (p->method != GNMPPI_METHOD_GN && p->method != GNMPPI_METHOD_MPPI)
+    return fail(nullptr, GNMPPI_E_ARG, "unknown method");
   if (p->dynamics == GNMPPI_DYN_LINEAR) {
     const int nx = p->nx, nu = p->nu;
     const int key = nx * 16 + nu;
@@ -172,7 +178,9 @@ static gnmppi_status validate(const gnmppi_problem* p, int32_t batch, const gnmp
   for (int b = 0; b < batch; ++b) {
     const int N = (shapes && shapes[b].N > 0) ? shapes[b].N : p->N;
     const int M = (shapes && shapes[b].M > 0) ? shapes[b].M : p->M;
-    const int K = (shapes && shapes[b].K > 0) ? shapes[b].K : p->K;
+    const int nu_b = p->dynamics == GNMPPI_DYN_CHAIN ? 2 : (p->dynamics == GNMPPI_DYN_PENDULUM ? 1 : p->nu);
+    const int K = p->sampling == GNMPPI_SAMPLE_SIGMA ? 2 * N * nu_b
+                                                      : ((shapes && shapes[b].K > 0) ? shapes[b].K : p->K);
     if (N < 1 || N > 100000) return fail(nullptr, GNMPPI_E_ARG, "instance %d: N must be in 1..100000", b);
     if (K < 1 || (p->antithetic && (K % 2 != 0 || K < 2)))
       return fail(nullptr, GNMPPI_E_ARG, "instance %d: K must be >= 1 (even and >= 2 with antithetic pairs)", b);
@@ -260,7 +268,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
       d.nref = 1;
     }
     d.n = d.N * d.nu;
-    d.Kp = anti ? K / 2 : K;
+    d.Kp = p.sampling == GNMPPI_SAMPLE_SIGMA ? d.n : (anti ? K / 2 : K);  // sigma points: n pairs
     d.ldK = (int)round_up(d.Kp, kPadK);
     d.ldP = (int)round_up(d.nR + d.n, 8);
     if (p.jac_mode == GNMPPI_JAC_LSQ) d.lsq = 1;
@@ -410,6 +418,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   c.monotone = p.monotone ? 1 : 0;
   c.ir_steps = p.ir_steps;
   c.antithetic = anti;
+  c.sampling = p.sampling;
   c.nx_lin = p.nx;
   c.nu_lin = p.nu;
   c.lin = h->d_lin;
@@ -480,6 +489,10 @@ extern "C" gnmppi_status gnmppi_create(const gnmppi_problem* p, int32_t batch, c
     h->own_stream = true;
   }
   h->p = *p;
+  if (h->p.method == GNMPPI_METHOD_MPPI) {  // the MPPI step is taken whole: one step length, alpha = 1
+    h->p.L = 1;
+    h->p.monotone = 0;
+  }
   st = build(h, shapes);
   h->p.lin = nullptr;
   if (st != GNMPPI_OK) {
@@ -640,6 +653,9 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
     h->launches++;
   }
   MARK(2);
+  // Method C needs no Jacobian: no contraction, Gram or Cholesky
+  const bool gn = h->p.method == GNMPPI_METHOD_GN;
+  if (!gn) mask &= ~((1u << 2) | (1u << 3) | (1u << 4));
   GemmArgs ga{h->d_desc, h->d_st, nullptr, h->d_dR, h->d_W, h->d_P, h->d_A, h->d_S2};
   if (ON(2)) {
     if (h->use_tc) {
@@ -674,7 +690,8 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
   }
   MARK(5);
   if (ON(5)) {
-    if (h->tune.solve_nt == 128) k_solve<TA, 128><<<h->batch, 128, h->solve_smem, h->stream>>>(sa);
+    if (!gn) k_mppi_step<<<h->batch, 256, 0, h->stream>>>(sa);
+    else if (h->tune.solve_nt == 128) k_solve<TA, 128><<<h->batch, 128, h->solve_smem, h->stream>>>(sa);
     else k_solve<TA, 256><<<h->batch, 256, h->solve_smem, h->stream>>>(sa);
     CKL();
     h->launches++;
@@ -1011,8 +1028,9 @@ std::string tune_signature(gnmppi_t h) {
       }
     }
   char buf[320];
-  snprintf(buf, sizeof(buf), "%s/sm%d/dyn%d/prec%d/anti%d/L%d/B%d/%016llx", name.c_str(), prop.multiProcessorCount,
-           h->p.dynamics, h->p.precision, h->p.antithetic ? 1 : 0, h->p.L, h->batch, (unsigned long long)f);
+  snprintf(buf, sizeof(buf), "%s/sm%d/dyn%d/prec%d/anti%d/L%d/meth%d/B%d/%016llx", name.c_str(),
+           prop.multiProcessorCount, h->p.dynamics, h->p.precision, h->p.antithetic ? 1 : 0, h->p.L, h->p.method,
+           h->batch, (unsigned long long)f);
   return buf;
 }
 

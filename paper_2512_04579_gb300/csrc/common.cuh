@@ -59,6 +59,8 @@ struct Consts {
   int32_t L, monotone, ir_steps, antithetic;
   int32_t nx_lin, nu_lin;
   const double* lin;  // device copy of the linear model data
+  int32_t sampling;   // 0: Philox normals (Method D), 1: sigma points sqrt(n) e_m (Method E)
+  int32_t pad;
 };
 
 // ------------------------------------------------------------------------

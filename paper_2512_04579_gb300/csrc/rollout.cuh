@@ -137,11 +137,22 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
   // k and k+1 come from Philox calls q = k and q = k + 1; each lane of the pair
   // draws one of the two and the partner's arrives by shuffle.
   constexpr bool SHARE = ANTI && NU == 2;
+  // Sigma points (Method E): pair m perturbs control m alone, by sqrt(n) s_m.
+  const bool sigma_pts = ANTI && a.cs.sampling != 0;
+  const T sqrtn = sqrt((T)I.n);
   int qc = -1;
   T z0 = (T)0, z1 = (T)0, y0 = (T)0, y1 = (T)0;
   for (int k = 0; k < I.N; ++k) {
     T u[NU];
-    if (SHARE) {
+    if (sigma_pts) {
+#pragma unroll
+      for (int c = 0; c < NU; ++c) {
+        const int j = k * NU + c;
+        const T w = (j == m) ? sS[j] * sqrtn : (T)0;
+        u[c] = sU[j] + sign * w;
+        if (active && par == 0) Wm[(int64_t)j * I.ldK + m] = to_store<S>(w);
+      }
+    } else if (SHARE) {
       if ((k & 1) == 0) {
         T a0, a1;
         box_muller(noise_words(a.cs.seed, (uint32_t)bm.x, a.it, mm, (uint32_t)(k + par)), a0, a1);

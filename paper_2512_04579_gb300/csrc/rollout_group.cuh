@@ -325,13 +325,22 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   } em{dR, sR, I.ldK, m, 0, active, plus, sign, (T)0, &eacc};
   // The 2G lanes of a pair draw the normals of 2G consecutive steps at once
   // (lane l of the pair: Philox call q = k + l) and hand them round by shuffle.
+  // Sigma points (Method E): pair m perturbs control m alone, by sqrt(n) s_m.
   const int pl = lane & (2 * G - 1);
+  const bool sigma_pts = a.cs.sampling != 0;
+  const T sqrtn = sqrt((T)I.n);
   T na0 = (T)0, na1 = (T)0;
   for (int k = 0; k < I.N; ++k) {
-    if (k % (2 * G) == 0)
-      box_muller(noise_words(a.cs.seed, (uint32_t)bm.x, a.it, mm, (uint32_t)(k + pl)), na0, na1);
-    const T z0 = __shfl_sync(0xffffffffu, na0, k % (2 * G), 2 * G);
-    const T z1 = __shfl_sync(0xffffffffu, na1, k % (2 * G), 2 * G);
+    T z0, z1;
+    if (sigma_pts) {
+      z0 = (2 * k == m) ? sqrtn : (T)0;
+      z1 = (2 * k + 1 == m) ? sqrtn : (T)0;
+    } else {
+      if (k % (2 * G) == 0)
+        box_muller(noise_words(a.cs.seed, (uint32_t)bm.x, a.it, mm, (uint32_t)(k + pl)), na0, na1);
+      z0 = __shfl_sync(0xffffffffu, na0, k % (2 * G), 2 * G);
+      z1 = __shfl_sync(0xffffffffu, na1, k % (2 * G), 2 * G);
+    }
     const T w0 = sS[2 * k] * z0, w1 = sS[2 * k + 1] * z1;
     const T u[2] = {sU[2 * k] + sign * w0, sU[2 * k + 1] + sign * w1};
     if (active && plus && lg == 0) {

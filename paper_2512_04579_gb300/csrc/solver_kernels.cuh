@@ -463,6 +463,31 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_solve(SolveArgs a) {
   }
 }
 
+// Method C (deterministic MPPI, Sec. 3): the weighted mean perturbation of
+// Eq. 5, already formed by k_softmin_wvec, is the step; the line search then
+// evaluates the single step length alpha = 1.  One CTA (256 threads) per instance.
+__global__ void __launch_bounds__(256) k_mppi_step(SolveArgs a) {
+  const int b = blockIdx.x;
+  InstState& st = a.st[b];
+  if (st.status != 0) return;
+  const InstDesc I = a.inst[b];
+  __shared__ double red[32];
+  double dsq = 0.0;
+  for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+    const double d = a.mppi[I.o_U + j];
+    a.delta[I.o_U + j] = d;
+    a.y[I.o_U + j] = 0.0;
+    dsq += d * d;
+  }
+  dsq = block_sum(dsq, red);
+  if (threadIdx.x == 0) {
+    st.chol_retries = 0;
+    st.lambda_used = 0.0;
+    st.step_norm = sqrt(dsq);
+    st.jac_mode_used = -1;  // no Jacobian
+  }
+}
+
 // One CTA (128 threads) per instance: line-search argmin (ties to the smallest
 // j; alpha = 0 last when monotone), U += alpha* delta, r <- R(U + alpha* delta),
 // and, in Algorithm-1 solves, s <- sqrt(beta) s.

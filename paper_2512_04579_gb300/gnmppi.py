@@ -21,6 +21,8 @@ DYN_PENDULUM, DYN_CHAIN, DYN_LINEAR = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
 JAC_LSQ, JAC_SIGMA, JAC_AUTO = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
+SAMPLE_RANDOM, SAMPLE_SIGMA = 0, 1
+METHOD_GN, METHOD_MPPI = 0, 1
 
 EXPORTS = ["gnmppi_create", "gnmppi_layout", "gnmppi_solve", "gnmppi_solve_masked", "gnmppi_step", "gnmppi_cost", "gnmppi_debug_read",
            "gnmppi_phase_times", "gnmppi_phase_name", "gnmppi_softmin_noalloc", "gnmppi_launch_count",
@@ -37,7 +39,8 @@ class Problem(C.Structure):
                 ("lin", C.POINTER(C.c_double)), ("K", C.c_int32), ("iterations", C.c_int32), ("L", C.c_int32),
                 ("precision", C.c_int32), ("jac_mode", C.c_int32), ("antithetic", C.c_int32),
                 ("monotone", C.c_int32), ("ir_steps", C.c_int32), ("lam", C.c_double), ("sigma0", C.c_double),
-                ("beta", C.c_double), ("gamma", C.c_double), ("tau", C.c_double), ("seed", C.c_uint64)]
+                ("beta", C.c_double), ("gamma", C.c_double), ("tau", C.c_double), ("seed", C.c_uint64),
+                ("sampling", C.c_int32), ("method", C.c_int32)]
 
 
 class InstanceShape(C.Structure):
@@ -149,7 +152,7 @@ def make_problem(dynamics: int, *, N: int, K: int, iterations: int = 20, nx: int
                  dt: float = 0.0, params=(), lin=None, L: int = 16, precision: int = PREC_FP64,
                  jac_mode: int = JAC_AUTO, antithetic: bool = True, monotone: bool = False, ir_steps: int = 2,
                  lam: float = 1e-3, sigma0: float = 0.5, beta: float = 0.7, gamma: float = 0.5, tau: float = 1.0,
-                 seed: int = 0) -> Problem:
+                 seed: int = 0, sampling: int = 0, method: int = 0) -> Problem:
     p = Problem()
     p.dynamics, p.nx, p.nu, p.N, p.M = dynamics, nx, nu, N, M
     p.dt = dt
@@ -164,6 +167,7 @@ def make_problem(dynamics: int, *, N: int, K: int, iterations: int = 20, nx: int
     p.precision, p.jac_mode, p.antithetic, p.monotone, p.ir_steps = precision, jac_mode, int(antithetic), \
         int(monotone), ir_steps
     p.lam, p.sigma0, p.beta, p.gamma, p.tau, p.seed = lam, sigma0, beta, gamma, tau, seed
+    p.sampling, p.method = sampling, method
     return p
 
 

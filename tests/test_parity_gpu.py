@@ -422,3 +422,58 @@ def test_reduced_precision_lsq_breakdown_takes_the_printed_form():
             # printed form has kappa(J^T J + lambda I) = 1.1e4 for this draw:
             # the step moves by a few percent
             assert rep[0].C_new == pytest.approx(ref.C_new, rel=5e-2)
+
+
+# ------------------------------------------- Methods E and C (Sec. 5, Sec. 3)
+def test_fp64_method_e_sigma_points_pendulum_per_iteration():
+    """Method E: the n = 50 sigma-point pairs +-sqrt(n) s_i e_i instead of
+    Philox draws (K ignored), per-iteration FP64 parity with the oracle."""
+    seed = I.BASE_SEED + 5
+    x0 = I.pendulum_x0(seed, 1)[0]
+    m = O.pendulum()
+    opt = O.Options(K=2, iterations=8, lam=1e-3, seed=seed, sampling="sigma")
+    gp = G.pendulum_problem(N=50, K=2, iterations=8, lam=1e-3, sigma0=0.5, seed=seed, sampling=G.SAMPLE_SIGMA)
+    its = per_iteration_parity(m, gp, opt, x0, None, np.zeros(m.n), 0.5, 8)
+    assert all(it.jac_mode_used == 0 for it in its)
+
+
+def test_fp64_method_e_sigma_points_chain_per_iteration():
+    """Method E on a chain, M = 5, N = 30 (n = 60 pairs, 8 rows of 4 lanes ragged)."""
+    seed = I.BASE_SEED + 6
+    M, N = 5, 30
+    x0, tgt = I.chain_instances(seed, 1, M)
+    m = O.chain(M=M, N=N)
+    opt = O.Options(K=2, iterations=4, lam=1e-3, seed=seed, sampling="sigma")
+    gp = G.chain_problem(M=M, N=N, K=2, iterations=4, lam=1e-3, sigma0=0.2, seed=seed, sampling=G.SAMPLE_SIGMA)
+    per_iteration_parity(m, gp, opt, x0[0], tgt[0], np.zeros(m.n), 0.2, 4)
+
+
+def test_fp64_method_c_mppi_step_pendulum_per_iteration():
+    """Method C: the MPPI step of Eq. 5 taken whole (alpha = 1), per-iteration
+    FP64 parity with the oracle (same samples as Method D)."""
+    seed = I.BASE_SEED + 7
+    x0 = I.pendulum_x0(seed, 1)[0]
+    m = O.pendulum()
+    opt = O.Options(K=256, iterations=6, L=1, lam=1e-3, seed=seed, method="mppi")
+    gp = G.pendulum_problem(N=50, K=256, iterations=6, lam=1e-3, sigma0=0.5, seed=seed, method=G.METHOD_MPPI)
+    its = per_iteration_parity(m, gp, opt, x0, None, np.zeros(m.n), 0.5, 6)
+    assert all(it.alpha == 1.0 and it.jac_mode_used == -1 for it in its)
+
+
+def test_method_e_reduced_precision_and_group_chain():
+    """Method E in FP32 mode on a 40-mass chain (group-per-rollout kernel): the
+    sample costs and the step's cost against the FP64 oracle."""
+    seed = I.BASE_SEED + 8
+    M, N = 40, 12
+    x0, tgt = I.chain_instances(seed, 1, M)
+    m = O.chain(M=M, N=N)
+    it = O.iteration(m, O.Options(K=2, lam=1e-3, seed=seed, sampling="sigma"), x0[0], tgt[0], np.zeros(m.n), 0.2)
+    gp = G.chain_problem(M=M, N=N, K=2, iterations=1, lam=1e-3, sigma0=0.2, seed=seed, sampling=G.SAMPLE_SIGMA,
+                         precision=G.PREC_FP32)
+    s = G.Solver(gp, 1)
+    st, U, rep = s.step(x0[0], tgt[0], np.zeros(m.n), np.full(m.n, 0.2), 0)
+    Cs = s.debug("C")
+    s.close()
+    assert st == 0
+    np.testing.assert_allclose(Cs, it.C_samp, rtol=TOLRED)
+    assert rep[0].C_new == pytest.approx(it.C_new, rel=3e-3)
