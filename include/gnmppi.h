@@ -54,8 +54,14 @@ enum {
                               gravity -g y, force control on mass M-1; RK4.  Residual stage k:
                               [p_{1..M-1,k} - p*, 0.1 u_k]; terminal p_{.,N} - p*.
                               xref = p* (2(M-1) values).  params {mass,k,k3,c,g}. */
-  GNMPPI_DYN_LINEAR = 2    /* x+ = A x + B u (discrete); residual stage k [wq.*x_k, wr.*u_k],
+  GNMPPI_DYN_LINEAR = 2,   /* x+ = A x + B u (discrete); residual stage k [wq.*x_k, wr.*u_k],
                               terminal wqN.*x_N.  lin = {A (nx*nx), B (nx*nu), wq, wr, wqN}. */
+  /* The static test problems of Sec. 5: N = 1, R depends on U alone; x0 is one
+     ignored value per instance, xref unused, dt unused. */
+  GNMPPI_DYN_ROSENBROCK = 3, /* Problem I, nu = 2: [sqrt2 (1 - u1), sqrt200 (u2 - u1^2)]   */
+  GNMPPI_DYN_RASTRIGIN = 4,  /* Problem II, nu = 2: sqrt2 [u1, u2, sqrt(5 - 5cos 2pi u1),
+                                sqrt(5 - 5cos 2pi u2)] (the paper's R, scaled for 0.5||R||^2) */
+  GNMPPI_DYN_HEAVISIDE = 5   /* Problem III, nu = 1: [H(u)], H(u) = 1 for u >= 0 else 0     */
 };
 
 /* Arithmetic of the hot path. */

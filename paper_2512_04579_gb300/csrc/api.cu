@@ -149,7 +149,7 @@ static bool get_launchers(int prec, int dyn, int key, Launchers* o) {
 static gnmppi_status validate(const gnmppi_problem* p, int32_t batch, const gnmppi_instance_shape* shapes) {
   if (!p) return fail(nullptr, GNMPPI_E_ARG, "problem is NULL");
   if (batch < 1) return fail(nullptr, GNMPPI_E_ARG, "batch must be >= 1");
-  if (p->dynamics < 0 || p->dynamics > 2) return fail(nullptr, GNMPPI_E_ARG, "unknown dynamics");
+  if (p->dynamics < 0 || p->dynamics > 5) return fail(nullptr, GNMPPI_E_ARG, "unknown dynamics");
   if (p->precision < 0 || p->precision > 2) return fail(nullptr, GNMPPI_E_ARG, "unknown precision");
   if (p->jac_mode < 0 || p->jac_mode > 2) return fail(nullptr, GNMPPI_E_ARG, "unknown jac_mode");
   if (p->L < 1 || p->L > kMaxL) return fail(nullptr, GNMPPI_E_ARG, "L must be in 1..%d", kMaxL);
@@ -160,7 +160,8 @@ static gnmppi_status validate(const gnmppi_problem* p, int32_t batch, const gnmp
   if (!(p->sigma0 > 0.0) || !std::isfinite(p->sigma0)) return fail(nullptr, GNMPPI_E_ARG, "sigma0 must be > 0");
   if (p->iterations < 0) return fail(nullptr, GNMPPI_E_ARG, "iterations must be >= 0");
   if (p->ir_steps < 0 || p->ir_steps > 10) return fail(nullptr, GNMPPI_E_ARG, "ir_steps must be in 0..10");
-  if (p->dynamics != GNMPPI_DYN_LINEAR && !(p->dt > 0.0)) return fail(nullptr, GNMPPI_E_ARG, "dt must be > 0");
+  if ((p->dynamics == GNMPPI_DYN_PENDULUM || p->dynamics == GNMPPI_DYN_CHAIN) && !(p->dt > 0.0))
+    return fail(nullptr, GNMPPI_E_ARG, "dt must be > 0");
   if (p->sampling != GNMPPI_SAMPLE_RANDOM && p->sampling != GNMPPI_SAMPLE_SIGMA)
     return fail(nullptr, GNMPPI_E_ARG, "unknown sampling");
   if (p->sampling == GNMPPI_SAMPLE_SIGMA && !p->antithetic)
@@ -178,7 +179,13 @@ static gnmppi_status validate(const gnmppi_problem* p, int32_t batch, const gnmp
   for (int b = 0; b < batch; ++b) {
     const int N = (shapes && shapes[b].N > 0) ? shapes[b].N : p->N;
     const int M = (shapes && shapes[b].M > 0) ? shapes[b].M : p->M;
-    const int nu_b = p->dynamics == GNMPPI_DYN_CHAIN ? 2 : (p->dynamics == GNMPPI_DYN_PENDULUM ? 1 : p->nu);
+    const bool testfun = p->dynamics >= GNMPPI_DYN_ROSENBROCK;
+    if (testfun && ((shapes && shapes[b].N > 0) ? shapes[b].N : p->N) != 1)
+      return fail(nullptr, GNMPPI_E_ARG, "instance %d: the test problems have N = 1", b);
+    const int nu_b = p->dynamics == GNMPPI_DYN_CHAIN ? 2
+                     : p->dynamics == GNMPPI_DYN_PENDULUM ? 1
+                     : p->dynamics == GNMPPI_DYN_HEAVISIDE ? 1
+                     : testfun ? 2 : p->nu;
     const int K = p->sampling == GNMPPI_SAMPLE_SIGMA ? 2 * N * nu_b
                                                       : ((shapes && shapes[b].K > 0) ? shapes[b].K : p->K);
     if (N < 1 || N > 100000) return fail(nullptr, GNMPPI_E_ARG, "instance %d: N must be in 1..100000", b);
@@ -259,6 +266,12 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
       d.nu = 1;
       d.rps = 3;
       d.nR = 3 * d.N + 2;
+      d.nref = 1;
+    } else if (p.dynamics >= GNMPPI_DYN_ROSENBROCK) {  // static test problems: one stage, no state
+      d.nx = 1;
+      d.nu = p.dynamics == GNMPPI_DYN_HEAVISIDE ? 1 : 2;
+      d.rps = p.dynamics == GNMPPI_DYN_ROSENBROCK ? 2 : (p.dynamics == GNMPPI_DYN_RASTRIGIN ? 4 : 1);
+      d.nR = d.N * d.rps;
       d.nref = 1;
     } else {
       d.nx = p.nx;

@@ -16,7 +16,7 @@ constexpr int kMaxL = 32;            // largest line-search set
 constexpr int kMaxChainF = 16;       // free masses handled by the thread-per-rollout chain kernels
 constexpr int kMaxChainGroupF = 64;  // free masses handled by the group-per-rollout chain kernels
 
-enum Dyn { kPendulum = 0, kChain = 1, kLinear = 2 };
+enum Dyn { kPendulum = 0, kChain = 1, kLinear = 2, kRosenbrock = 3, kRastrigin = 4, kHeaviside = 5 };
 enum Prec { kFP64 = 0, kFP32 = 1, kBF16 = 2 };
 
 // Per-instance sizes and offsets into the packed workspace arrays.
@@ -411,6 +411,38 @@ struct Chain<float, F> {
 #pragma unroll
     for (int i = 0; i < 2 * F; ++i) emit(i, x[i] - pref[i]);
   }
+};
+
+// The static test problems of Sec. 5 as one-stage models (N = 1, the state is
+// one ignored value, no terminal rows), residual R(u) with Phi = 0.5 ||R||^2:
+//   3 Rosenbrock (Problem I):  [sqrt2 (1 - u1), sqrt200 (u2 - u1^2)]
+//   4 Rastrigin (Problem II):  sqrt2 [u1, u2, sqrt(5 - 5 cos 2pi u1), sqrt(5 - 5 cos 2pi u2)]
+//                              (the paper's R for Phi = ||R||^2, rescaled by sqrt2)
+//   5 Heaviside (Problem III): [H(u)], H(u) = 1 for u >= 0, else 0
+template <typename T, int KIND>
+struct TestFun {
+  static constexpr int NX = 1, NU = (KIND == kHeaviside) ? 1 : 2;
+  static constexpr int RPS = (KIND == kRosenbrock) ? 2 : ((KIND == kRastrigin) ? 4 : 1), RT = 0;
+  __device__ TestFun(const Consts&) {}
+  __device__ __forceinline__ void step(T*, const T*) const {}
+  template <class E>
+  __device__ __forceinline__ void stage(const T*, const T* u, E& emit) const {
+    const T r2 = (T)1.4142135623730951;  // sqrt(2)
+    if (KIND == kRosenbrock) {
+      emit(0, r2 * ((T)1 - u[0]));
+      emit(1, (T)14.142135623730951 * (u[1] - u[0] * u[0]));  // sqrt(200)
+    } else if (KIND == kRastrigin) {
+      const T tp = (T)6.283185307179586;  // 2 pi
+      emit(0, r2 * u[0]);
+      emit(1, r2 * u[1]);
+      emit(2, r2 * sqrt((T)5 - (T)5 * cos(tp * u[0])));
+      emit(3, r2 * sqrt((T)5 - (T)5 * cos(tp * u[1])));
+    } else {
+      emit(0, u[0] >= (T)0 ? (T)1 : (T)0);
+    }
+  }
+  template <class E>
+  __device__ __forceinline__ void terminal(const T*, E&) const {}
 };
 
 // Discrete linear model x+ = A x + B u with diagonal residual weights.

@@ -65,6 +65,15 @@ void fill(Launchers* o) {
           GNM_CHAIN_CASE(T, S, 16)                                                    \
           default: return false;                                                      \
         }                                                                             \
+      case kRosenbrock:                                                               \
+        fill<TestFun<T, kRosenbrock>, TestFun<double, kRosenbrock>, T, S>(o);         \
+        return true;                                                                  \
+      case kRastrigin:                                                                \
+        fill<TestFun<T, kRastrigin>, TestFun<double, kRastrigin>, T, S>(o);           \
+        return true;                                                                  \
+      case kHeaviside:                                                                \
+        fill<TestFun<T, kHeaviside>, TestFun<double, kHeaviside>, T, S>(o);           \
+        return true;                                                                  \
       case kLinear:                                                                   \
         switch (key) {                                                                \
           GNM_LIN_CASE(T, S, 2, 1) GNM_LIN_CASE(T, S, 2, 2) GNM_LIN_CASE(T, S, 4, 1)  \

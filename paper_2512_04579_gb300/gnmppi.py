@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgnmppi.so")
 
 OK, E_ARG, E_CUDA, E_NOT_PD, E_NONFINITE, E_TIMEOUT, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
-DYN_PENDULUM, DYN_CHAIN, DYN_LINEAR = 0, 1, 2
+DYN_PENDULUM, DYN_CHAIN, DYN_LINEAR, DYN_ROSENBROCK, DYN_RASTRIGIN, DYN_HEAVISIDE = 0, 1, 2, 3, 4, 5
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
 JAC_LSQ, JAC_SIGMA, JAC_AUTO = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
@@ -185,6 +185,13 @@ def chain_problem(M: int = 10, **kw) -> Problem:
     kw.setdefault("dt", 0.02)
     kw.setdefault("params", (0.1, 10.0, 1.0, 0.05, 9.81))
     return make_problem(DYN_CHAIN, nx=4 * (M - 1), nu=2, M=M, **kw)
+
+
+def testfun_problem(name: str, **kw) -> Problem:
+    """The static test problems of Sec. 5 (N = 1): "rosenbrock", "rastrigin", "heaviside"."""
+    dyn = {"rosenbrock": DYN_ROSENBROCK, "rastrigin": DYN_RASTRIGIN, "heaviside": DYN_HEAVISIDE}[name]
+    kw.setdefault("N", 1)
+    return make_problem(dyn, nx=1, nu=1 if dyn == DYN_HEAVISIDE else 2, **kw)
 
 
 def linear_problem(A, B, wq, wr, wqN, **kw) -> Problem:
