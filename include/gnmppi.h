@@ -48,12 +48,15 @@ typedef enum {
 enum {
   GNMPPI_DYN_PENDULUM = 0, /* x=[theta,omega]; theta''=-(g/l)sin(theta)-b*omega+u/(m l^2); RK4.
                               Residual stage k: [theta_k-pi, 0.1 omega_k, 0.1 u_k];
-                              terminal [10(theta_N-pi), 10 omega_N].  params {g,l,m,b}. */
+                              terminal [10(theta_N-pi), 10 omega_N].  params {g,l,m,b,u_f}:
+                              u_f > 0 adds dead-zone friction at the input (Setting
+                              V.ii): u_apply = 0 where |u| <= u_f; the residual keeps u. */
   GNMPPI_DYN_CHAIN = 1,    /* M point masses in a vertical plane, mass 0 fixed at the origin,
                               link tension k d + k3 d^3 (rest length 1/(M-1)), damping -c v,
                               gravity -g y, force control on mass M-1; RK4.  Residual stage k:
                               [p_{1..M-1,k} - p*, 0.1 u_k]; terminal p_{.,N} - p*.
-                              xref = p* (2(M-1) values).  params {mass,k,k3,c,g}. */
+                              xref = p* (2(M-1) values).  params {mass,k,k3,c,g,u_f}
+                              (u_f: dead-zone friction per force component, as above). */
   GNMPPI_DYN_LINEAR = 2,   /* x+ = A x + B u (discrete); residual stage k [wq.*x_k, wr.*u_k],
                               terminal wqN.*x_N.  lin = {A (nx*nx), B (nx*nu), wq, wr, wqN}. */
   /* The static test problems of Sec. 5: N = 1, R depends on U alone; x0 is one

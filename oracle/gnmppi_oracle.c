@@ -206,7 +206,12 @@ int32_t orc_rollout(const orc_model* m, const double* x0, const double* U, doubl
         xk1[i] = s;
       }
     } else {
-      orc_rk4_step(m, xk, uk, xk1);
+      /* Setting V.ii (Sec. 5): dead-zone friction at the input of the dynamics,
+       * u_apply = 0 where |u| <= u_friction (per component; u_friction = 0: off) */
+      const double uf = (m->dyn == ORC_DYN_PENDULUM) ? m->params[4] : (m->dyn == ORC_DYN_CHAIN ? m->params[5] : 0.0);
+      double ua[8];
+      for (int j = 0; j < nu && j < 8; ++j) ua[j] = (uf > 0.0 && fabs(uk[j]) <= uf) ? 0.0 : uk[j];
+      orc_rk4_step(m, xk, nu <= 8 ? ua : uk, xk1);
     }
   }
   return ORC_OK;

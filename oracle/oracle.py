@@ -143,12 +143,14 @@ class Model:
         return int(lib().orc_nR(C.byref(self.c())))
 
 
-def pendulum(N=50, dt=0.05, g=9.81, l=1.0, m=1.0, b=0.1) -> Model:
-    return Model("pendulum", 2, 1, N, dt=dt, params=(g, l, m, b))
+def pendulum(N=50, dt=0.05, g=9.81, l=1.0, m=1.0, b=0.1, u_friction=0.0) -> Model:
+    """u_friction > 0: dead-zone friction at the input (Setting V.ii of Sec. 5)."""
+    return Model("pendulum", 2, 1, N, dt=dt, params=(g, l, m, b, u_friction))
 
 
-def chain(M=10, N=100, dt=0.02, mass=0.1, k=10.0, k3=1.0, damping=0.05, gravity=9.81) -> Model:
-    return Model("chain", 4 * (M - 1), 2, N, dt=dt, M=M, params=(mass, k, k3, damping, gravity))
+def chain(M=10, N=100, dt=0.02, mass=0.1, k=10.0, k3=1.0, damping=0.05, gravity=9.81, u_friction=0.0) -> Model:
+    """u_friction > 0: dead-zone friction at the input, per component (Setting V.ii of Sec. 5)."""
+    return Model("chain", 4 * (M - 1), 2, N, dt=dt, M=M, params=(mass, k, k3, damping, gravity, u_friction))
 
 
 def linear(A, B, wq, wr, wqN, N) -> Model:

@@ -432,6 +432,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   c.ir_steps = p.ir_steps;
   c.antithetic = anti;
   c.sampling = p.sampling;
+  c.u_friction = p.dynamics == GNMPPI_DYN_PENDULUM ? p.params[4] : (p.dynamics == GNMPPI_DYN_CHAIN ? p.params[5] : 0.0);
   c.nx_lin = p.nx;
   c.nu_lin = p.nu;
   c.lin = h->d_lin;

@@ -61,7 +61,17 @@ struct Consts {
   const double* lin;  // device copy of the linear model data
   int32_t sampling;   // 0: Philox normals (Method D), 1: sigma points sqrt(n) e_m (Method E)
   int32_t pad;
+  double u_friction;  // dead-zone friction at the input of the dynamics (0: off)
 };
+
+// Setting V.ii of Sec. 5: dead-zone friction at the input of the dynamics,
+// u_apply = 0 where |u| <= u_friction (per component), u otherwise; the
+// residual still penalises the decision variable u.
+template <typename T, int NU>
+__device__ __forceinline__ void dead_zone(const T* u, T* ua, double uf) {
+#pragma unroll
+  for (int c = 0; c < NU; ++c) ua[c] = (uf > 0.0 && fabs(u[c]) <= (T)uf) ? (T)0 : u[c];
+}
 
 // ------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC 2011) and the noise stream

@@ -194,7 +194,11 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
     md.stage(x, u, em);
     cost.add(em.csum);
     eacc.add(em.esum);
-    md.step(x, u);
+    {
+      T ua[Model::NU];
+      dead_zone<T, Model::NU>(u, ua, a.cs.u_friction);
+      md.step(x, ua);
+    }
   }
   em.col = dR + I.N * stage_stride;
   em.r = sR + I.N * Model::RPS;
@@ -279,7 +283,11 @@ __global__ void __launch_bounds__(128) k_line(RollArgs a) {
     em.csum = (T)0;
     md.stage(x, u, em);
     cost.add(em.csum);
-    md.step(x, u);
+    {
+      T ua[Model::NU];
+      dead_zone<T, Model::NU>(u, ua, a.cs.u_friction);
+      md.step(x, ua);
+    }
   }
   em.base = I.N * Model::RPS;
   em.csum = (T)0;

@@ -351,7 +351,11 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
     em.csum = (T)0;
     md.rows(x, u, false, em);
     cost.add(em.csum);
-    md.step(x, u);
+    {
+      T ua[2];
+      dead_zone<T, 2>(u, ua, a.cs.u_friction);
+      md.step(x, ua);
+    }
   }
   em.base = I.N * rps;
   em.csum = (T)0;
@@ -448,7 +452,11 @@ __global__ void __launch_bounds__(256) k_line_group(RollArgs a) {
     em.csum = (T)0;
     md.rows(x, u, false, em);
     cost.add(em.csum);
-    md.step(x, u);
+    {
+      T ua[2];
+      dead_zone<T, 2>(u, ua, a.cs.u_friction);
+      md.step(x, ua);
+    }
   }
   em.base = I.N * rps;
   em.csum = (T)0;

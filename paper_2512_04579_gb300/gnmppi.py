@@ -171,19 +171,21 @@ def make_problem(dynamics: int, *, N: int, K: int, iterations: int = 20, nx: int
     return p
 
 
-def pendulum_problem(**kw) -> Problem:
-    """Pendulum swing-up: g=9.81, l=1, m=1, b=0.1, RK4 dt=0.05."""
+def pendulum_problem(u_friction: float = 0.0, **kw) -> Problem:
+    """Pendulum swing-up: g=9.81, l=1, m=1, b=0.1, RK4 dt=0.05; u_friction > 0
+    adds dead-zone friction at the input (Setting V.ii)."""
     kw.setdefault("N", 50)
     kw.setdefault("dt", 0.05)
-    kw.setdefault("params", (9.81, 1.0, 1.0, 0.1))
+    kw.setdefault("params", (9.81, 1.0, 1.0, 0.1, u_friction))
     return make_problem(DYN_PENDULUM, nx=2, nu=1, **kw)
 
 
-def chain_problem(M: int = 10, **kw) -> Problem:
-    """Hanging chain: mass 0.1, k=10, k3=1, damping 0.05, gravity 9.81, RK4 dt=0.02."""
+def chain_problem(M: int = 10, u_friction: float = 0.0, **kw) -> Problem:
+    """Hanging chain: mass 0.1, k=10, k3=1, damping 0.05, gravity 9.81, RK4 dt=0.02;
+    u_friction > 0 adds dead-zone friction per force component (Setting V.ii)."""
     kw.setdefault("N", 100)
     kw.setdefault("dt", 0.02)
-    kw.setdefault("params", (0.1, 10.0, 1.0, 0.05, 9.81))
+    kw.setdefault("params", (0.1, 10.0, 1.0, 0.05, 9.81, u_friction))
     return make_problem(DYN_CHAIN, nx=4 * (M - 1), nu=2, M=M, **kw)
 
 

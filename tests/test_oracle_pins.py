@@ -551,3 +551,25 @@ def test_mppi_step_matches_the_tilted_gaussian_mean_on_a_quadratic_cost():
     assert np.linalg.norm(it.delta - exact) <= 1e-2 * np.linalg.norm(exact)
     np.testing.assert_allclose(it.U_next, U + it.delta, rtol=0, atol=1e-15)
     assert it.C_new == pytest.approx(O.cost(m, x0, None, U + it.delta), rel=1e-14)
+
+
+# ------------------------------------- Setting V.ii: dead-zone friction ---
+def test_dead_zone_friction_zeroes_exactly_the_small_controls():
+    """u_apply = 0 where |u| <= u_f, u elsewhere (per component): the rollout
+    with friction equals the frictionless rollout of the thresholded controls,
+    and controls inside the dead zone act like no control at all."""
+    uf = 0.3
+    for fric, plain, U in (
+        (O.pendulum(N=12, u_friction=uf), O.pendulum(N=12), np.linspace(-0.6, 0.6, 12)),
+        (O.chain(M=4, N=6, u_friction=uf), O.chain(M=4, N=6), np.linspace(-0.9, 0.7, 12)),
+    ):
+        x0 = np.linspace(0.05, 0.4, fric.nx)
+        Ua = np.where(np.abs(U) <= uf, 0.0, U)
+        assert np.any(Ua == 0.0) and np.any(Ua != 0.0)
+        np.testing.assert_array_equal(O.rollout(fric, x0, U), O.rollout(plain, x0, Ua))
+        small = np.clip(U, -uf, uf)
+        np.testing.assert_array_equal(O.rollout(fric, x0, small), O.rollout(plain, x0, np.zeros_like(U)))
+        # the residual still penalises the decision variable: 0.1 u rows differ
+        assert not np.array_equal(O.residual(fric, x0, np.zeros(2 * (fric.M - 1)) if fric.M else None, small),
+                                  O.residual(plain, x0, np.zeros(2 * (fric.M - 1)) if fric.M else None,
+                                             np.zeros_like(U)))

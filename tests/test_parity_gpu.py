@@ -501,3 +501,26 @@ def test_fp64_test_problems_per_iteration(name, U0, s0, sampling, method, K, T):
                            sampling=G.SAMPLE_SIGMA if sampling == "sigma" else G.SAMPLE_RANDOM,
                            method=G.METHOD_MPPI if method == "mppi" else G.METHOD_GN)
     per_iteration_parity(m, gp, opt, np.zeros(1), None, np.array(U0, float), s0, T)
+
+
+# ------------------------------------- Setting V.ii: dead-zone friction ---
+def test_fp64_dead_zone_friction_pendulum_per_iteration():
+    """Pendulum swing-up with dead-zone friction u_f = 0.5 at the input
+    (nonsmooth in U), per-iteration FP64 parity with the oracle."""
+    seed = I.BASE_SEED + 10
+    x0 = I.pendulum_x0(seed, 1)[0]
+    m = O.pendulum(u_friction=0.5)
+    opt = O.Options(K=256, iterations=10, lam=1e-3, seed=seed)
+    gp = G.pendulum_problem(u_friction=0.5, N=50, K=256, iterations=10, lam=1e-3, sigma0=0.5, seed=seed)
+    per_iteration_parity(m, gp, opt, x0, None, np.zeros(m.n), 0.5, 10)
+
+
+def test_fp64_dead_zone_friction_chain_per_iteration():
+    """Chain M = 5, N = 30 with dead-zone friction u_f = 0.2 per force component."""
+    seed = I.BASE_SEED + 12
+    M, N, K = 5, 30, 256
+    x0, tgt = I.chain_instances(seed, 1, M)
+    m = O.chain(M=M, N=N, u_friction=0.2)
+    opt = O.Options(K=K, iterations=4, lam=1e-3, seed=seed)
+    gp = G.chain_problem(M=M, u_friction=0.2, N=N, K=K, iterations=4, lam=1e-3, sigma0=0.2, seed=seed)
+    per_iteration_parity(m, gp, opt, x0[0], tgt[0], np.zeros(m.n), 0.2, 4)
