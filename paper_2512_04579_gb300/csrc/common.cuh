@@ -409,17 +409,26 @@ struct Chain<float, F> {
       v[i] = __ffma2_rn(hh6, __fadd2_rn(av[i], acc[i]), v[i]);
     }
   }
+  // residual rows come in (x, y) pairs; pref is 8-byte aligned (shared memory
+  // at an even float offset, or an alignas(8) local array)
   template <class E>
   __device__ __forceinline__ void stage(const float* x, const float* u, E& emit) const {
+    const float2* pr = reinterpret_cast<const float2*>(pref);
 #pragma unroll
-    for (int i = 0; i < 2 * F; ++i) emit(i, x[i] - pref[i]);
-    emit(2 * F, 0.1f * u[0]);
-    emit(2 * F + 1, 0.1f * u[1]);
+    for (int i = 0; i < F; ++i) {
+      const float2 q = pr[i];
+      emit.pair(2 * i, x[2 * i] - q.x, x[2 * i + 1] - q.y);
+    }
+    emit.pair(2 * F, 0.1f * u[0], 0.1f * u[1]);
   }
   template <class E>
   __device__ __forceinline__ void terminal(const float* x, E& emit) const {
+    const float2* pr = reinterpret_cast<const float2*>(pref);
 #pragma unroll
-    for (int i = 0; i < 2 * F; ++i) emit(i, x[i] - pref[i]);
+    for (int i = 0; i < F; ++i) {
+      const float2 q = pr[i];
+      emit.pair(2 * i, x[2 * i] - q.x, x[2 * i + 1] - q.y);
+    }
   }
 };
 

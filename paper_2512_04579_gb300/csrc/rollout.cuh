@@ -91,6 +91,26 @@ struct SampleEmit {
       esum += d * r[i];
     }
   }
+  // Rows i and i + 1 (i even) at once: with antithetic pairs each lane of the
+  // pair owns one of the two rows (row i + par), so the difference, the dR
+  // store and the e update run once per lane without a divergent branch.
+  // Same arithmetic, same order per lane as two calls of operator().
+  __device__ __forceinline__ void pair(int i, T v0, T v1) {
+    if (ANTI) {
+      csum += v0 * v0;
+      csum += v1 * v1;
+      const T give = par ? v0 : v1;  // the row the partner owns
+      const T own = par ? v1 : v0;
+      const T got = __shfl_xor_sync(0xffffffffu, give, 1);
+      const T d = sign * (own - got) * (T)0.5;
+      const int row = i + par;
+      if (active) col[(int64_t)row * ldK] = to_store<S>(d);
+      esum += d * r[row];
+    } else {
+      (*this)(i, v0);
+      (*this)(i + 1, v1);
+    }
+  }
 };
 
 template <class Model, typename T, typename S, bool ANTI>
@@ -237,6 +257,10 @@ struct LineEmit {
     csum += v * v;
     if (out) out[base + i] = v;
   }
+  __device__ __forceinline__ void pair(int i, T v0, T v1) {
+    (*this)(i, v0);
+    (*this)(i + 1, v1);
+  }
 };
 
 // One thread per (instance, candidate).  mode 0: candidate j rolls out
@@ -258,7 +282,7 @@ __global__ void __launch_bounds__(128) k_line(RollArgs a) {
     for (int q = 0; q < j; ++q) alpha *= a.cs.gamma;
   }
   Model md(a.cs);
-  T ref[RefSize<Model>::value > 0 ? RefSize<Model>::value : 1];
+  alignas(8) T ref[RefSize<Model>::value > 0 ? RefSize<Model>::value : 1];  // read as float2 pairs
 #pragma unroll
   for (int i = 0; i < RefSize<Model>::value; ++i) ref[i] = (T)a.xref[I.o_xref + i];
   bind_model(md, (const T*)ref);
