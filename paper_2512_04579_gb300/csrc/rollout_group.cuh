@@ -117,9 +117,10 @@ struct ChainGroup {
     }
   }
   // Residual rows of this lane at a stage (its masses' position errors; lane
-  // 0 also the two control rows at 2F, 2F+1) or at the terminal state.  Every
-  // lane calls emit(row, value, valid) the same 2 FL + 2 times, so emitters
-  // may shuffle; slots that belong to no row of this lane come with valid false.
+  // 0 also the two control rows at 2F, 2F+1) or at the terminal state, as
+  // (x, y) row pairs.  Every lane calls emit.pair(row, v_x, v_y, valid) the
+  // same FL + 1 times, so emitters may shuffle; slots that belong to no row of
+  // this lane come with valid false.
   template <class E>
   __device__ __forceinline__ void rows(const T* x, const T* u, bool terminal, E& emit) const {
 #pragma unroll
@@ -129,12 +130,10 @@ struct ChainGroup {
       const int r0 = real ? 2 * (i - 1) : 0;
       const T px = pref_local ? pref[2 * j] : (real ? pref[r0] : (T)0);
       const T py = pref_local ? pref[2 * j + 1] : (real ? pref[r0 + 1] : (T)0);
-      emit(r0, x[2 * j] - px, real);
-      emit(r0 + 1, x[2 * j + 1] - py, real);
+      emit.pair(r0, x[2 * j] - px, x[2 * j + 1] - py, real);
     }
     const bool urow = !terminal && lg == 0;
-    emit(2 * F, (T)0.1 * u[0], urow);
-    emit(2 * F + 1, (T)0.1 * u[1], urow);
+    emit.pair(2 * F, (T)0.1 * u[0], (T)0.1 * u[1], urow);
   }
 };
 
@@ -240,12 +239,10 @@ struct ChainGroup<float, FL, G> {
       const int r0 = real ? 2 * (i - 1) : 0;
       const float px = pref_local ? pref[2 * j] : (real ? pref[r0] : 0.f);
       const float py = pref_local ? pref[2 * j + 1] : (real ? pref[r0 + 1] : 0.f);
-      emit(r0, x[2 * j] - px, real);
-      emit(r0 + 1, x[2 * j + 1] - py, real);
+      emit.pair(r0, x[2 * j] - px, x[2 * j + 1] - py, real);
     }
     const bool urow = !terminal && lg == 0;
-    emit(2 * F, 0.1f * u[0], urow);
-    emit(2 * F + 1, 0.1f * u[1], urow);
+    emit.pair(2 * F, 0.1f * u[0], 0.1f * u[1], urow);
   }
 };
 
@@ -322,6 +319,22 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
         eacc->add(d * r[row]);
       }
     }
+    // Rows r0 and r0 + 1 at once: the + group owns row r0 and the - group row
+    // r0 + 1, so both halves of the pair store a difference and update e per
+    // pair of rows instead of the + half alone per row (e is then the sum of
+    // both halves' partial sums).  Every lane shuffles.
+    __device__ __forceinline__ void pair(int r0, T v0, T v1, bool valid) {
+      const T give = plus ? v1 : v0;  // the row the other half owns
+      const T got = __shfl_xor_sync(0xffffffffu, give, G);
+      if (!valid) return;
+      csum += v0 * v0;
+      csum += v1 * v1;
+      const T own = plus ? v0 : v1;
+      const int row = base + r0 + (plus ? 0 : 1);
+      const T d = sign * (own - got) * (T)0.5;
+      if (active) dR[(int64_t)row * ldK + m] = to_store<S>(d);
+      eacc->add(d * r[row]);
+    }
   } em{dR, sR, I.ldK, m, 0, active, plus, sign, (T)0, &eacc};
   // The 2G lanes of a pair draw the normals of 2G consecutive steps at once
   // (lane l of the pair: Philox call q = k + l) and hand them round by shuffle.
@@ -369,7 +382,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   double ev = group_sum(eacc.value(), G, 0xffffffffu);
   const double Cother = __shfl_xor_sync(0xffffffffu, Cself, G);
   const double evo = __shfl_xor_sync(0xffffffffu, ev, G);  // every lane shuffles
-  ev = plus ? ev : evo;
+  ev = ev + evo;  // the two halves of the pair each hold half of the rows' terms
   const bool ok = isfinite(Cself) && isfinite(Cother) && isfinite(ev);
   if (active && lg == 0) {
     a.C[I.o_C + 2 * m + (plus ? 0 : 1)] = Cself;
@@ -435,6 +448,10 @@ __global__ void __launch_bounds__(256) k_line_group(RollArgs a) {
       if (!valid) return;
       csum += v * v;
       if (out) out[base + row_local] = v;
+    }
+    __device__ __forceinline__ void pair(int r0, T v0, T v1, bool valid) {
+      (*this)(r0, v0, valid);
+      (*this)(r0 + 1, v1, valid);
     }
   } em{out, 0, (T)0};
   Acc<T> cost;
