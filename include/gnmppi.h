@@ -188,6 +188,19 @@ gnmppi_status gnmppi_solve(gnmppi_t h, int32_t mem, const double* x0, const doub
 gnmppi_status gnmppi_solve_masked(gnmppi_t h, int32_t mem, const double* x0, const double* xref, double* U,
                                   const double* sigma, const int32_t* active, gnmppi_report* rep);
 
+/* gnmppi_solve_masked in two halves, so that the host (or another handle on
+ * another stream) works while this handle's solve runs.  gnmppi_solve_async
+ * enqueues the input copies, the solve's CUDA graph and the copy of U back on
+ * the handle's stream and returns; U must stay valid until the matching
+ * gnmppi_solve_wait.  With mem = HOST and pageable U the copy back blocks until
+ * it is done (pinned U keeps the call asynchronous).  gnmppi_solve_wait blocks
+ * until that solve has finished and fills rep like gnmppi_solve.  One solve in
+ * flight per handle.  Errors: E_ARG for a second async call before the wait,
+ * or a wait with nothing in flight; otherwise as gnmppi_solve. */
+gnmppi_status gnmppi_solve_async(gnmppi_t h, int32_t mem, const double* x0, const double* xref, double* U,
+                                 const double* sigma, const int32_t* active);
+gnmppi_status gnmppi_solve_wait(gnmppi_t h, gnmppi_report* rep);
+
 /* One Algorithm-1 iteration with index `iteration` (it selects the Philox
  * stream) at the given U (in/out: U_k -> U_{k+1}) and per-component std sigma
  * (packed like U, not modified).  rep (nullable, host, batch entries). */

@@ -76,6 +76,10 @@ struct gnmppi_s {
   // concurrency of the rollout groups and the solve CTA shape
   TuneCfg tune{};
   std::string tune_report;
+  // asynchronous solve: per-instance states land in pinned host memory
+  InstState* h_st = nullptr;
+  cudaEvent_t ev_done = nullptr;
+  bool pending = false;
   cudaStream_t aux[kMaxBranches] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kMaxBranches] = {};
   TcPlan tc{};
@@ -231,6 +235,8 @@ extern "C" void gnmppi_destroy(gnmppi_t h) {
     if (h->ev_join[i]) cudaEventDestroy(h->ev_join[i]);
   }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_done) cudaEventDestroy(h->ev_done);
+  if (h->h_st) cudaFreeHost(h->h_st);
   for (void* p : h->allocs) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -391,6 +397,8 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     CK(cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming));
   }
   CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
+  CK(cudaMallocHost((void**)&h->h_st, sizeof(InstState) * h->batch));
   for (auto& g : h->groups) {
     CK(g.fn.prepare(g.smem));
     AL(g.d_list, 4 * g.insts.size());
@@ -812,10 +820,10 @@ static gnmppi_status worst_status(const std::vector<InstState>& s) {
 // Inactive instances carry this status: every kernel skips them.
 constexpr int32_t kInactive = 1;
 
-extern "C" gnmppi_status gnmppi_solve_masked(gnmppi_t h, int32_t mem, const double* x0, const double* xref,
-                                             double* U, const double* sigma, const int32_t* active,
-                                             gnmppi_report* rep) {
+extern "C" gnmppi_status gnmppi_solve_async(gnmppi_t h, int32_t mem, const double* x0, const double* xref,
+                                            double* U, const double* sigma, const int32_t* active) {
   if (!h) return GNMPPI_E_ARG;
+  if (h->pending) return fail(h, GNMPPI_E_ARG, "a solve is already in flight on this handle");
   gnmppi_status st = load_inputs(h, mem, x0, xref, U, sigma);
   if (st != GNMPPI_OK) return st;
   if (active) {
@@ -848,10 +856,20 @@ extern "C" gnmppi_status gnmppi_solve_masked(gnmppi_t h, int32_t mem, const doub
   h->launches += h->graph_nodes;
   const cudaMemcpyKind k = mem == GNMPPI_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   CK(cudaMemcpyAsync(U, h->d_U, 8 * h->n_U, k, h->stream));
-  std::vector<InstState> s(h->batch);
-  CK(cudaMemcpyAsync(s.data(), h->d_st, sizeof(InstState) * h->batch, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(InstState) * h->batch, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaEventRecord(h->ev_done, h->stream));
+  h->pending = true;
+  return GNMPPI_OK;
+}
+
+extern "C" gnmppi_status gnmppi_solve_wait(gnmppi_t h, gnmppi_report* rep) {
+  if (!h) return GNMPPI_E_ARG;
+  if (!h->pending) return fail(h, GNMPPI_E_ARG, "no solve in flight on this handle");
+  h->pending = false;
+  gnmppi_status st;
+  CK(cudaEventSynchronize(h->ev_done));
   if ((st = check_timeout(h)) != GNMPPI_OK) return st;
+  std::vector<InstState> s(h->h_st, h->h_st + h->batch);
   if (rep) {
     std::vector<double> s_end(h->n_U);
     CK(cudaMemcpy(s_end.data(), h->d_s, 8 * h->n_U, cudaMemcpyDeviceToHost));
@@ -867,6 +885,14 @@ extern "C" gnmppi_status gnmppi_solve_masked(gnmppi_t h, int32_t mem, const doub
     }
   }
   return worst_status(s);
+}
+
+extern "C" gnmppi_status gnmppi_solve_masked(gnmppi_t h, int32_t mem, const double* x0, const double* xref,
+                                             double* U, const double* sigma, const int32_t* active,
+                                             gnmppi_report* rep) {
+  gnmppi_status st = gnmppi_solve_async(h, mem, x0, xref, U, sigma, active);
+  if (st != GNMPPI_OK) return st;
+  return gnmppi_solve_wait(h, rep);
 }
 
 extern "C" gnmppi_status gnmppi_solve(gnmppi_t h, int32_t mem, const double* x0, const double* xref, double* U,

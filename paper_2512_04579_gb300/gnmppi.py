@@ -29,7 +29,7 @@ EXPORTS = ["gnmppi_create", "gnmppi_layout", "gnmppi_solve", "gnmppi_solve_maske
            "gnmppi_destroy", "gnmppi_last_error", "gnmppi_status_string", "gnmppi_version", "gnmppi_mlp_create",
            "gnmppi_mlp_num_params", "gnmppi_mlp_set_params", "gnmppi_mlp_get_params", "gnmppi_mlp_set_normalization",
            "gnmppi_mlp_forward", "gnmppi_mlp_loss_grad", "gnmppi_mlp_train_step", "gnmppi_mlp_warm_start",
-           "gnmppi_mlp_destroy", "gnmppi_mlp_last_error", "gnmppi_autotune", "gnmppi_tune_set",
+           "gnmppi_mlp_destroy", "gnmppi_mlp_last_error", "gnmppi_autotune", "gnmppi_tune_set", "gnmppi_solve_async", "gnmppi_solve_wait",
            "gnmppi_tune_report"]
 
 
@@ -99,6 +99,10 @@ def load(path: str | None = None):
     L.gnmppi_status_string.argtypes = [C.c_int32]
     L.gnmppi_status_string.restype = C.c_char_p
     L.gnmppi_version.restype = C.c_int32
+    L.gnmppi_solve_async.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp]
+    L.gnmppi_solve_async.restype = C.c_int32
+    L.gnmppi_solve_wait.argtypes = [vp, vp]
+    L.gnmppi_solve_wait.restype = C.c_int32
     L.gnmppi_autotune.argtypes = [vp, C.c_int32, vp, vp, vp, vp, C.c_int32]
     L.gnmppi_autotune.restype = C.c_int32
     L.gnmppi_tune_set.argtypes = [vp, C.c_int32, C.c_int32]
@@ -281,6 +285,24 @@ def gnmppi_tune_report(h) -> dict:
     st = load().gnmppi_tune_report(h, buf, len(buf))
     _check(h, st, "gnmppi_tune_report")
     return json.loads(buf.value.decode())
+
+
+def gnmppi_solve_async(h, mem, x0, xref, U, sigma=None, active=None):
+    """Enqueue a solve and return (see gnmppi_solve_wait); keep U alive until then."""
+    act = None
+    if active is not None:
+        act = np.ascontiguousarray(active, dtype=np.int32)
+    st = load().gnmppi_solve_async(h, mem, _ptr(x0), _ptr(xref), _ptr(U), _ptr(sigma),
+                                   None if act is None else act.ctypes.data)
+    _check(h, st, "gnmppi_solve_async")
+    return st
+
+
+def gnmppi_solve_wait(h, batch: int | None = None):
+    rep = (Report * batch)() if batch else None
+    st = load().gnmppi_solve_wait(h, rep)
+    _check(h, st, "gnmppi_solve_wait")
+    return st, rep
 
 
 def gnmppi_solve_masked(h, mem, x0, xref, U, sigma, active, batch: int):

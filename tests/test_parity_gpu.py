@@ -524,3 +524,43 @@ def test_fp64_dead_zone_friction_chain_per_iteration():
     opt = O.Options(K=K, iterations=4, lam=1e-3, seed=seed)
     gp = G.chain_problem(M=M, u_friction=0.2, N=N, K=K, iterations=4, lam=1e-3, sigma0=0.2, seed=seed)
     per_iteration_parity(m, gp, opt, x0[0], tgt[0], np.zeros(m.n), 0.2, 4)
+
+
+def test_async_solves_on_two_streams_match_blocking_solves():
+    """gnmppi_solve_async + gnmppi_solve_wait on two handles and two streams,
+    in flight together, give bitwise the blocking gnmppi_solve results; a
+    second async call before the wait and a wait with nothing in flight are
+    rejected."""
+    import torch
+
+    seed = I.BASE_SEED + 13
+    M, N, K, B = 6, 20, 256, 8
+    x0, tgt = I.chain_instances(seed, 2 * B, M)
+    gp = G.chain_problem(M=M, N=N, K=K, iterations=5, lam=1e-3, sigma0=0.2, seed=seed, precision=G.PREC_FP32)
+    dev = torch.device("cuda")
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    hs = [G.gnmppi_create(gp, B, None, s.cuda_stream) for s in streams]
+    try:
+        xs = [torch.tensor(x0[i * B:(i + 1) * B].ravel(), dtype=torch.float64, device=dev) for i in range(2)]
+        ts = [torch.tensor(tgt[i * B:(i + 1) * B].ravel(), dtype=torch.float64, device=dev) for i in range(2)]
+        ref = []
+        for h, x, t in zip(hs, xs, ts):
+            U = torch.zeros(B * 2 * N, dtype=torch.float64, device=dev)
+            st, rep = G.gnmppi_solve(h, G.MEM_DEVICE, x, t, U, None, B)
+            ref.append((U.cpu().numpy(), [r.C_final for r in rep]))
+        Us = [torch.zeros(B * 2 * N, dtype=torch.float64, device=dev) for _ in range(2)]
+        torch.cuda.synchronize()
+        for h, x, t, U in zip(hs, xs, ts, Us):
+            G.gnmppi_solve_async(h, G.MEM_DEVICE, x, t, U, None)
+        with pytest.raises(G.GnmppiError):
+            G.gnmppi_solve_async(hs[0], G.MEM_DEVICE, xs[0], ts[0], Us[0], None)
+        for i, h in enumerate(hs):
+            st, rep = G.gnmppi_solve_wait(h, B)
+            assert st == 0
+            assert np.array_equal(Us[i].cpu().numpy(), ref[i][0])
+            assert [r.C_final for r in rep] == ref[i][1]
+        with pytest.raises(G.GnmppiError):
+            G.gnmppi_solve_wait(hs[0], B)
+    finally:
+        for h in hs:
+            G.gnmppi_destroy(h)
