@@ -670,7 +670,7 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
   MARK(1);
   SolveArgs sa = solve_args(h, shrink);
   if (ON(1)) {
-    k_softmin_wvec<S, TC><<<h->batch, 256, 0, h->stream>>>(sa);
+    k_softmin_wvec<S, TC><<<h->batch * kSoftminSplit, 256, 0, h->stream>>>(sa);
     CKL();
     h->launches++;
   }

@@ -87,10 +87,12 @@ __device__ __forceinline__ double block_min(double v, double* red) {
 // in FP32 and e, w+ - w- are staged once per chunk in shared memory in the
 // accumulation type, so the row loop runs on the FP32 pipe only (GB300's FP64
 // pipe retires conversions at the DFMA rate).
+constexpr int kSoftminSplit = 4;  // CTAs per instance (each takes every 4th group of rows of W)
+
 template <typename S, typename TA>
 __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
   constexpr int CH = 2048;  // samples staged per chunk
-  const int b = blockIdx.x;
+  const int b = blockIdx.x / kSoftminSplit, part = blockIdx.x % kSoftminSplit;
   const InstDesc I = a.inst[b];
   if (a.st[b].status != 0) return;
   __shared__ double red[32];
@@ -112,13 +114,11 @@ __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
   cmin = block_min(cmin, red);
   const int nmask = (int)block_sum((double)masked, red);
   // 2. weights exp(-(C - cmin)/tau) (Eq. 5), their sums, and w+ - w- per pair
-  double s1 = 0.0, s2 = 0.0;
   const double itau = 1.0 / a.cs.tau;
-  for (int m = threadIdx.x; m < I.Kp; m += blockDim.x) {
+  auto weights = [&](int m, double& w0, double& w1) {
     const double c0 = C[anti ? 2 * m : m];
     const double c1 = anti ? C[2 * m + 1] : c0;
     const bool ok = isfinite(c0) && isfinite(c1) && isfinite(cmin);
-    double w0 = 0.0, w1 = 0.0;
     if constexpr (sizeof(TA) == 8) {
       w0 = ok ? exp(-(c0 - cmin) * itau) : 0.0;
       w1 = (ok && anti) ? exp(-(c1 - cmin) * itau) : 0.0;
@@ -126,24 +126,40 @@ __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
       w0 = ok ? (double)expf((float)(-(c0 - cmin) * itau)) : 0.0;
       w1 = (ok && anti) ? (double)expf((float)(-(c1 - cmin) * itau)) : 0.0;
     }
+  };
+  double s1 = 0.0, s2 = 0.0;
+  const bool one_chunk = I.Kp <= CH;  // then the sums pass stages the chunk as well
+  for (int m = threadIdx.x; m < I.Kp; m += blockDim.x) {
+    double w0, w1;
+    weights(m, w0, w1);
     s1 += w0 + w1;
     s2 += w0 * w0 + w1 * w1;
-    wt[m] = w0 - w1;
+    if (part == 0) wt[m] = w0 - w1;
+    if (one_chunk) {
+      se[m] = (TA)e[m];
+      sw[m] = (TA)(w0 - w1);
+    }
   }
   s1 = block_sum(s1, red);
   s2 = block_sum(s2, red);
-  // 3. rows of W: b_j = sum_m W[j][m] e_m, mppi_j = sum_m W[j][m] wt_m / sum w
+  // 3. rows of W (this CTA's share): b_j = sum_m W[j][m] e_m,
+  //    mppi_j = sum_m W[j][m] wt_m / sum w; every CTA forms its own staged
+  //    copy of the weight differences (CTA 0's global copy may not be written yet)
   const S* W = reinterpret_cast<const S*>(a.W) + I.o_W;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int m0 = 0; m0 < I.Kp; m0 += CH) {
     const int mc = min(CH, I.Kp - m0);
-    __syncthreads();  // wt written above / previous chunk consumed
-    for (int m = threadIdx.x; m < mc; m += blockDim.x) {
-      se[m] = (TA)e[m0 + m];
-      sw[m] = (TA)wt[m0 + m];
+    if (!one_chunk) {
+      __syncthreads();  // previous chunk consumed
+      for (int m = threadIdx.x; m < mc; m += blockDim.x) {
+        double w0, w1;
+        weights(m0 + m, w0, w1);
+        se[m] = (TA)e[m0 + m];
+        sw[m] = (TA)(w0 - w1);
+      }
     }
     __syncthreads();
-    for (int j = warp; j < I.n; j += nw) {
+    for (int j = part * nw + warp; j < I.n; j += kSoftminSplit * nw) {
       const S* row = W + (int64_t)j * I.ldK + m0;
       TA ag = (TA)0, am = (TA)0;
 #pragma unroll 8
@@ -170,23 +186,15 @@ __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
       }
     }
   }
-  double gsq = 0.0;
-  for (int j = warp; j < I.n; j += nw) {
-    if (lane == 0) {
-      const double G = a.g[I.o_U + j];
-      a.mppi[I.o_U + j] = s1 > 0.0 ? a.mppi[I.o_U + j] / s1 : 0.0;
-      gsq += G * G;
-    }
-  }
-  gsq = block_sum(gsq, red);
-  if (threadIdx.x == 0) {
+  for (int j = part * nw + warp; j < I.n; j += kSoftminSplit * nw)
+    if (lane == 0) a.mppi[I.o_U + j] = s1 > 0.0 ? a.mppi[I.o_U + j] / s1 : 0.0;
+  if (part == 0 && threadIdx.x == 0) {  // |b| is taken by the step kernels, which read all of b
     InstState& s = a.st[b];
     s.c_min = cmin;
     s.sum_w = s1;
     s.sum_w2 = s2;
     s.ess = s2 > 0.0 ? s1 * s1 / s2 : 0.0;
     s.n_masked = nmask;
-    s.pr_norm = sqrt(gsq);
     if (nmask >= I.Kp) s.status = -4;  // every sample non-finite
   }
 }
@@ -380,7 +388,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_solve(SolveArgs a) {
   const TA* P = reinterpret_cast<const TA*>(a.P) + I.o_P;
   const double* s = a.s + I.o_U;
   const double Keff = (double)(I.Kp - st.n_masked);
-  for (int j = tid; j < n; j += blockDim.x) rhs[j] = -a.g[I.o_U + j];
+  double gsq = 0.0;
+  for (int j = tid; j < n; j += blockDim.x) {
+    const double gj = a.g[I.o_U + j];
+    rhs[j] = -gj;
+    gsq += gj * gj;
+  }
+  gsq = block_sum(gsq, red);
+  if (tid == 0) st.pr_norm = sqrt(gsq);  // |b|, b = P^T r
   double lam = a.cs.lambda;
   int retries = 0;
   bool ok = false;
@@ -472,15 +487,18 @@ __global__ void __launch_bounds__(256) k_mppi_step(SolveArgs a) {
   if (st.status != 0) return;
   const InstDesc I = a.inst[b];
   __shared__ double red[32];
-  double dsq = 0.0;
+  double dsq = 0.0, gsq = 0.0;
   for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
     const double d = a.mppi[I.o_U + j];
     a.delta[I.o_U + j] = d;
     a.y[I.o_U + j] = 0.0;
     dsq += d * d;
+    gsq += a.g[I.o_U + j] * a.g[I.o_U + j];
   }
   dsq = block_sum(dsq, red);
+  gsq = block_sum(gsq, red);
   if (threadIdx.x == 0) {
+    st.pr_norm = sqrt(gsq);
     st.chol_retries = 0;
     st.lambda_used = 0.0;
     st.step_norm = sqrt(dsq);

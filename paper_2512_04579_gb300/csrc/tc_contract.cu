@@ -96,10 +96,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 
 // Instruction descriptor: FP32 accumulator, A/B format (1 = BF16 for
 // kind::f16, 2 = TF32 for kind::tf32), both K-major, N >> 3 and M >> 4.
+// n_mma: the tile's MMA width, a multiple of 16 in [16, BN] (narrower for the
+// last column tile of a job, so no MMA work goes to columns that are dropped).
 template <bool BF16>
-__device__ __forceinline__ uint32_t idesc() {
+__device__ __forceinline__ uint32_t idesc(int n_mma) {
   const uint32_t fmt = BF16 ? 1u : 2u;
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n_mma >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 template <bool BF16>
@@ -217,7 +219,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
       mbar_wait(su32(bars + kb % STAGES), (kb / STAGES) & 1, abort, false);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    const uint32_t id = idesc<BF16>();
+    const int ncols = min(BN, J.Nc - tl.z * BN);  // columns of this tile that are kept
+    const uint32_t id = idesc<BF16>(min(BN, (ncols + 15) / 16 * 16));
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES, round = kb / STAGES;
       if (!mbar_wait(su32(bars + s), round & 1, abort, true)) {
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
     const int row0 = tl.y * BM + warp * 32;
     TOut* out = (J.out_sel ? D2 : D) + J.out_off;
 #pragma unroll 1
-    for (int c = 0; c < BN / 32; ++c) {
+    for (int c = 0; c < BN / 32 && tl.z * BN + c * 32 < J.Nc; ++c) {  // uniform: kept 32-column chunks
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
 #pragma unroll
