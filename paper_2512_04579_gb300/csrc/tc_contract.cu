@@ -6,14 +6,17 @@
 // with the sample index m as the reduction dimension.  dR and W of an instance
 // are stored as one [nR + n][ldK] block (sample-contiguous rows), so one TMA
 // tensor map per instance covers both operands: the A tile is rows nR + i of
-// the block, the B tile rows j.  One CTA computes a 128 x 256 output tile:
-//   warp 0 lane 0  issues TMA loads into a 4-stage shared-memory ring,
-//   warp 1 lane 0  issues tcgen05.mma (M=128, N=256, K=16 BF16 / K=8 TF32)
-//                  into a 256-column TMEM accumulator,
+// the block, the B tile rows j.  One CTA computes a (128 or 256) x 256 output
+// tile -- two 128-row sub-tiles when the instance has more than 128 unknowns,
+// so that each B tile is streamed from L2 once for both:
+//   warp 0 lane 0  issues TMA loads into a 3-stage shared-memory ring,
+//   warp 1 lane 0  issues tcgen05.mma (M=128, N <= 256, K=16 BF16 / K=8 TF32)
+//                  per sub-tile into its own 256-column TMEM accumulator,
 //   warps 0-3      read TMEM back (tcgen05.ld 32x32b) and store FP32 rows.
 //  (2) the Gram product A = P^T P of Eq. 9 in FP32-level accuracy from three
 //      TF32 passes, A ~ Ph Ph^T + Ph Pl^T + Pl Ph^T with P^T = Ph + Pl split into
-//      a TF32 head and its FP32 remainder (k_split_tf32 writes [Ph; Pl] rows),
+//      a TF32 head and its FP32 remainder (k_split_tf32 writes [Ph; Pl] rows;
+//      one 128 x 256 tile per CTA, a 2-stage ring of head + remainder blocks),
 //      and in the same launch S2 = S S^T for the scaled LSQ system: the S
 //      columns sit in the same split rows from a 32-aligned column on.
 // Both use the same kernel, driven by per-instance job descriptors.
@@ -156,10 +159,17 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
   constexpr int KSTEP = BF16 ? 16 : 8;   // elements per MMA
   constexpr int NSUB = KBLK / KSTEP;     // MMAs per k-block and operand pair (4)
   constexpr int PARTS = SPLIT3 ? 2 : 1;  // head (+ remainder) blocks per operand
-  constexpr int STAGE_BYTES = PARTS * (A_BYTES + B_BYTES);
+  constexpr int MTMAX = SPLIT3 ? 1 : 2;  // 128-row sub-tiles of A per tile (each its own accumulator)
+  constexpr int STAGE_BYTES = PARTS * (MTMAX * A_BYTES + B_BYTES);
   constexpr int STAGES = RING_BYTES / STAGE_BYTES;
+  constexpr uint32_t TCOLS = MTMAX * TMEM_COLS;
   const int4 tl = tiles[blockIdx.x];
   const TcJob J = jobs[tl.x];
+  // tl.w: sub-tiles of this tile (1, or 2 when the job has more than 128 rows),
+  // so every B tile is streamed once for up to 256 output rows
+  const int mt = SPLIT3 ? 1 : tl.w;
+  const int row_org = tl.y * mt * BM;
+  const uint32_t tx_bytes = (uint32_t)(PARTS * (mt * A_BYTES + B_BYTES));
   if (st[J.inst].status != 0) return;  // uniform over the CTA, before any allocation
   const int nkb = J.nkb;
   const CUtensorMap* map = maps + J.map;
@@ -179,7 +189,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(TCOLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -201,14 +211,15 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
         break;
       }
       const uint32_t full = su32(bars + s);
-      mbar_expect_tx(full, STAGE_BYTES);
+      mbar_expect_tx(full, tx_bytes);
       const uint32_t a_dst = su32(base + s * STAGE_BYTES);
-      const uint32_t b_dst = a_dst + PARTS * A_BYTES;
+      const uint32_t b_dst = a_dst + PARTS * MTMAX * A_BYTES;
       const int x = J.x0 + kb * KBLK;
 #pragma unroll
       for (int p = 0; p < PARTS; ++p) {
         const int off = p * J.lo_off;
-        tma_load(a_dst + p * A_BYTES, map, full, x, J.a_row0 + off + tl.y * BM);
+        for (int q = 0; q < mt; ++q)
+          tma_load(a_dst + (p * MTMAX + q) * A_BYTES, map, full, x, J.a_row0 + off + row_org + q * BM);
         tma_load(b_dst + p * B_BYTES, map, full, x, J.b_row0 + off + tl.z * BN);
         tma_load(b_dst + p * B_BYTES + BM * ROW_BYTES, map, full, x, J.b_row0 + off + tl.z * BN + BM);
       }
@@ -230,10 +241,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
       }
       tc_fence_after();
       const uint32_t a0 = su32(base + s * STAGE_BYTES);
-      const uint32_t b0 = a0 + PARTS * A_BYTES;
+      const uint32_t b0 = a0 + PARTS * MTMAX * A_BYTES;
 #pragma unroll
       for (int k = 0; k < NSUB; ++k) {
-        mma<BF16>(tmem, sdesc(a0 + k * 32), sdesc(b0 + k * 32), id, (kb > 0 || k > 0) ? 1u : 0u);
+        // sub-tile q accumulates into TMEM columns [256 q, 256 q + 256)
+        for (int q = 0; q < mt; ++q)
+          mma<BF16>(tmem + (uint32_t)(q * TMEM_COLS), sdesc(a0 + q * A_BYTES + k * 32), sdesc(b0 + k * 32), id,
+                    (kb > 0 || k > 0) ? 1u : 0u);
         if (SPLIT3) {
           mma<BF16>(tmem, sdesc(a0 + k * 32), sdesc(b0 + B_BYTES + k * 32), id, 1u);
           mma<BF16>(tmem, sdesc(a0 + A_BYTES + k * 32), sdesc(b0 + k * 32), id, 1u);
@@ -255,12 +269,14 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
   // tcgen05.ld is warp-collective: the whole warp takes the same branch
   if (__all_sync(0xffffffffu, ok && !*abort)) {
     TOut* stg = reinterpret_cast<TOut*>(base) + warp * 32 * 33;
-    const int row0 = tl.y * BM + warp * 32;
     TOut* out = (J.out_sel ? D2 : D) + J.out_off;
+#pragma unroll 1
+    for (int sub = 0; sub < mt; ++sub) {
+    const int row0 = row_org + sub * BM + warp * 32;
 #pragma unroll 1
     for (int c = 0; c < BN / 32 && tl.z * BN + c * 32 < J.Nc; ++c) {  // uniform: kept 32-column chunks
       uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sub * TMEM_COLS + c * 32), v);
 #pragma unroll
       for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = (TOut)__uint_as_float(v[q]);
       __syncwarp();
@@ -272,6 +288,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
       }
       __syncwarp();
     }
+    }
   } else if (threadIdx.x == 0) {
     atomicExch(err, 1);
   }
@@ -279,7 +296,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
   }
 }
 
@@ -395,8 +412,9 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     jc.ldc = d.ldP;
     jc.x0 = 0;
     jc.out_sel = 0;
-    for (int i = 0; i < (d.n + BM - 1) / BM; ++i)
-      for (int j = 0; j < (d.nR + d.n + BN - 1) / BN; ++j) tc.push_back(make_int4(b, i, j, 0));
+    const int mt = d.n > BM ? 2 : 1;  // up to 256 rows per tile: each B tile streamed once
+    for (int i = 0; i < (d.n + mt * BM - 1) / (mt * BM); ++i)
+      for (int j = 0; j < (d.nR + d.n + BN - 1) / BN; ++j) tc.push_back(make_int4(b, i, j, mt));
     // Gram: one FP32 map over [Ph; Pl] (2n rows, ldG columns)
     if (!encode_rows(encode, &maps[nb + b], plan->d_G + g_off[b], false, g_ld[b], g_ld[b], 2 * (int64_t)d.n)) {
       err = "cuTensorMapEncodeTiled failed (Gram, instance " + std::to_string(b) + ")";
@@ -416,7 +434,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     jg.x0 = 0;
     jg.out_sel = 0;
     for (int i = 0; i < (d.n + BM - 1) / BM; ++i)
-      for (int j = 0; j < (d.n + BN - 1) / BN; ++j) tg.push_back(make_int4(nb + b, i, j, 0));
+      for (int j = 0; j < (d.n + BN - 1) / BN; ++j) tg.push_back(make_int4(nb + b, i, j, 1));
     // S2 = S S^T over the S columns of the same split rows (LSQ mode)
     TcJob& js = jobs[2 * nb + b];
     js = jg;
@@ -425,7 +443,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     js.out_sel = 1;
     if (d.lsq)
       for (int i = 0; i < (d.n + BM - 1) / BM; ++i)
-        for (int j = 0; j < (d.n + BN - 1) / BN; ++j) tg.push_back(make_int4(2 * nb + b, i, j, 0));
+        for (int j = 0; j < (d.n + BN - 1) / BN; ++j) tg.push_back(make_int4(2 * nb + b, i, j, 1));
     for (int r = 0; r < d.n; ++r) rows.push_back(make_int2(b, r));
   }
   if (!plan_alloc(plan, &plan->d_maps, sizeof(CUtensorMap) * maps.size()) ||
