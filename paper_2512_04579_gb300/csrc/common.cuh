@@ -66,11 +66,17 @@ struct Consts {
 
 // Setting V.ii of Sec. 5: dead-zone friction at the input of the dynamics,
 // u_apply = 0 where |u| <= u_friction (per component), u otherwise; the
-// residual still penalises the decision variable u.
+// residual still penalises the decision variable u.  uf is the threshold in
+// the arithmetic type, taken once per kernel by friction_threshold (negative:
+// off), so the per-step test stays off GB300's FP64 pipe in FP32 kernels.
+template <typename T>
+__device__ __forceinline__ T friction_threshold(const Consts& cs) {
+  return cs.u_friction > 0.0 ? (T)cs.u_friction : (T)-1;
+}
 template <typename T, int NU>
-__device__ __forceinline__ void dead_zone(const T* u, T* ua, double uf) {
+__device__ __forceinline__ void dead_zone(const T* u, T* ua, T uf) {
 #pragma unroll
-  for (int c = 0; c < NU; ++c) ua[c] = (uf > 0.0 && fabs(u[c]) <= (T)uf) ? (T)0 : u[c];
+  for (int c = 0; c < NU; ++c) ua[c] = (fabs(u[c]) <= uf) ? (T)0 : u[c];
 }
 
 // ------------------------------------------------------------------------

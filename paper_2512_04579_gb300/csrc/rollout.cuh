@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
   const T sign = par ? (T)-1 : (T)1;
 
   Model md(a.cs);
+  const T uf_t = friction_threshold<T>(a.cs);
   bind_model(md, (const T*)sRef);
   alignas(16) T x[NX];
 #pragma unroll
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
     eacc.add(em.esum);
     {
       T ua[Model::NU];
-      dead_zone<T, Model::NU>(u, ua, a.cs.u_friction);
+      dead_zone<T, Model::NU>(u, ua, uf_t);
       md.step(x, ua);
     }
   }
@@ -282,6 +283,7 @@ __global__ void __launch_bounds__(128) k_line(RollArgs a) {
     for (int q = 0; q < j; ++q) alpha *= a.cs.gamma;
   }
   Model md(a.cs);
+  const T uf_t = friction_threshold<T>(a.cs);
   alignas(8) T ref[RefSize<Model>::value > 0 ? RefSize<Model>::value : 1];  // read as float2 pairs
 #pragma unroll
   for (int i = 0; i < RefSize<Model>::value; ++i) ref[i] = (T)a.xref[I.o_xref + i];
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(128) k_line(RollArgs a) {
     cost.add(em.csum);
     {
       T ua[Model::NU];
-      dead_zone<T, Model::NU>(u, ua, a.cs.u_friction);
+      dead_zone<T, Model::NU>(u, ua, uf_t);
       md.step(x, ua);
     }
   }

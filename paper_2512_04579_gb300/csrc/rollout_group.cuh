@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   // every lane of a block works on one instance with one horizon, so whole
   // warps stay converged and shuffles use the full mask
   ChainGroup<T, FL, G> md(a.cs, I.F, lg, 0xffffffffu);
+  const T uf_t = friction_threshold<T>(a.cs);
   md.pref = sRef;
   alignas(16) T x[4 * FL];
 #pragma unroll
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
     cost.add(em.csum);
     {
       T ua[2];
-      dead_zone<T, 2>(u, ua, a.cs.u_friction);
+      dead_zone<T, 2>(u, ua, uf_t);
       md.step(x, ua);
     }
   }
@@ -417,6 +418,7 @@ __global__ void __launch_bounds__(256) k_line_group(RollArgs a) {
   // every shuffle is confined to this group's lanes
   const unsigned gmask = ((G == 32) ? 0xffffffffu : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
   ChainGroup<T, FL, G> md(a.cs, I.F, lg, gmask);
+  const T uf_t = friction_threshold<T>(a.cs);
   T ref[2 * FL];
 #pragma unroll
   for (int q = 0; q < FL; ++q) {
@@ -471,7 +473,7 @@ __global__ void __launch_bounds__(256) k_line_group(RollArgs a) {
     cost.add(em.csum);
     {
       T ua[2];
-      dead_zone<T, 2>(u, ua, a.cs.u_friction);
+      dead_zone<T, 2>(u, ua, uf_t);
       md.step(x, ua);
     }
   }
