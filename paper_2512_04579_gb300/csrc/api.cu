@@ -389,7 +389,10 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     g.work += (double)d.Kp * d.N * (d.nx + 2);
     const int per = g.fn.pairs_per_block ? g.fn.pairs_per_block : (anti ? kPairsPerBlock : kSamplesPerBlock);
     for (int c = 0; c < (d.Kp + per - 1) / per; ++c) g.bmap.push_back(make_int2(b, c));
-    g.smem = std::max(g.smem, (int)(h->szT * (2 * d.n + d.nR + d.nref)));
+    // group kernels stage r and the targets interleaved: (N + 1) stages of 2 slots + 2 words
+    const int64_t words = g.fn.slots ? 2 * d.n + (int64_t)(d.N + 1) * (2 * g.fn.slots + 2) + 2 * g.fn.slots
+                                     : 2 * d.n + d.nR + d.nref;
+    g.smem = std::max(g.smem, (int)(h->szT * words));
   }
   // concurrency: streams and events for up to kMaxBranches graph branches
   for (int i = 0; i < kMaxBranches; ++i) {

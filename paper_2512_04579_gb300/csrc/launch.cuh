@@ -12,6 +12,7 @@ struct Launchers {
   void (*cost64)(const RollArgs&, int ncand_total, cudaStream_t);
   int pairs_per_block = 0;     // antithetic pairs per sample CTA (0: use the thread-per-rollout defaults)
   int antithetic_only = 0;     // group kernels support antithetic sampling only
+  int slots = 0;               // group kernels: mass slots G * FL of the interleaved shared layout
 };
 
 // key: chain -> free masses F; linear -> nx * 16 + nu; pendulum -> 0.

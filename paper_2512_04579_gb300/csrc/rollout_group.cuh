@@ -118,9 +118,12 @@ struct ChainGroup {
   }
   // Residual rows of this lane at a stage (its masses' position errors; lane
   // 0 also the two control rows at 2F, 2F+1) or at the terminal state, as
-  // (x, y) row pairs.  Every lane calls emit.pair(row, v_x, v_y, valid) the
-  // same FL + 1 times, so emitters may shuffle; slots that belong to no row of
-  // this lane come with valid false.
+  // (x, y) row pairs.  Every lane calls emit.pair(slot, row, v_x, v_y, valid)
+  // the same FL + 1 times (slot j < FL: the lane's mass j; slot FL: the
+  // controls), so emitters may shuffle; slots that belong to no row of this
+  // lane come with valid false.  The target positions are read from pref
+  // either lane-local (pref[2j], [2j+1]) or from the group-interleaved layout
+  // (pref already offset by 2 lg; mass slot j at pref[2Gj], [2Gj+1]).
   template <class E>
   __device__ __forceinline__ void rows(const T* x, const T* u, bool terminal, E& emit) const {
 #pragma unroll
@@ -128,12 +131,12 @@ struct ChainGroup {
       const int i = mass(j);
       const bool real = i <= F;
       const int r0 = real ? 2 * (i - 1) : 0;
-      const T px = pref_local ? pref[2 * j] : (real ? pref[r0] : (T)0);
-      const T py = pref_local ? pref[2 * j + 1] : (real ? pref[r0 + 1] : (T)0);
-      emit.pair(r0, x[2 * j] - px, x[2 * j + 1] - py, real);
+      const T px = pref_local ? pref[2 * j] : pref[2 * G * j];
+      const T py = pref_local ? pref[2 * j + 1] : pref[2 * G * j + 1];
+      emit.pair(j, r0, x[2 * j] - px, x[2 * j + 1] - py, real);
     }
     const bool urow = !terminal && lg == 0;
-    emit.pair(2 * F, (T)0.1 * u[0], (T)0.1 * u[1], urow);
+    emit.pair(FL, 2 * F, (T)0.1 * u[0], (T)0.1 * u[1], urow);
   }
 };
 
@@ -237,12 +240,12 @@ struct ChainGroup<float, FL, G> {
       const int i = mass(j);
       const bool real = i <= F;
       const int r0 = real ? 2 * (i - 1) : 0;
-      const float px = pref_local ? pref[2 * j] : (real ? pref[r0] : 0.f);
-      const float py = pref_local ? pref[2 * j + 1] : (real ? pref[r0 + 1] : 0.f);
-      emit.pair(r0, x[2 * j] - px, x[2 * j + 1] - py, real);
+      const float px = pref_local ? pref[2 * j] : pref[2 * G * j];
+      const float py = pref_local ? pref[2 * j + 1] : pref[2 * G * j + 1];
+      emit.pair(j, r0, x[2 * j] - px, x[2 * j + 1] - py, real);
     }
     const bool urow = !terminal && lg == 0;
-    emit.pair(2 * F, 0.1f * u[0], 0.1f * u[1], urow);
+    emit.pair(FL, 2 * F, 0.1f * u[0], 0.1f * u[1], urow);
   }
 };
 
@@ -261,18 +264,34 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   const int2 bm = a.bmap[blockIdx.x];
   const InstDesc I = a.inst[bm.x];
   if (a.st[bm.x].status != 0) return;
+  // Shared: U, s (n each), then the nominal residual and the target positions
+  // in a group-interleaved layout, so that the 2G lanes of a pair read 2G
+  // consecutive words (lane lg's mass slot j at [2G j + 2 lg], the controls
+  // after the SL mass slots of a stage):
+  //   sR[k RS + 2G j + 2 lg + c] = r[k rps + 2 (lg FL + j) + c],
+  //   sR[k RS + 2 SL + c]        = r[k rps + 2F + c],   sRef likewise, zero-padded.
+  constexpr int SL = G * FL;      // mass slots of a rollout group
+  constexpr int RS = 2 * SL + 2;  // interleaved words per stage
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sU = reinterpret_cast<T*>(smem_raw);
   T* sS = sU + I.n;
   T* sR = sS + I.n;
-  T* sRef = sR + I.nR;
+  T* sRef = sR + (int64_t)(I.N + 1) * RS;
   const T* rg = reinterpret_cast<const T*>(a.r) + I.o_R;
+  const int rps = 2 * I.F + 2;
   for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
     sU[j] = (T)a.U[I.o_U + j];
     sS[j] = (T)a.s[I.o_U + j];
   }
-  for (int j = threadIdx.x; j < I.nR; j += blockDim.x) sR[j] = rg[j];
-  for (int j = threadIdx.x; j < 2 * I.F; j += blockDim.x) sRef[j] = (T)a.xref[I.o_xref + j];
+  for (int idx = threadIdx.x; idx < I.nR; idx += blockDim.x) {
+    const int k = idx / rps, i = idx - k * rps, q = i >> 1;
+    const int w = i < 2 * I.F ? (q % FL) * 2 * G + 2 * (q / FL) + (i & 1) : 2 * SL + (i - 2 * I.F);
+    sR[k * RS + w] = rg[idx];
+  }
+  for (int idx = threadIdx.x; idx < 2 * SL; idx += blockDim.x) {
+    const int q = idx >> 1;
+    sRef[(q % FL) * 2 * G + 2 * (q / FL) + (idx & 1)] = q < I.F ? (T)a.xref[I.o_xref + idx] : (T)0;
+  }
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
@@ -285,7 +304,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   // warps stay converged and shuffles use the full mask
   ChainGroup<T, FL, G> md(a.cs, I.F, lg, 0xffffffffu);
   const T uf_t = friction_threshold<T>(a.cs);
-  md.pref = sRef;
+  md.pref = sRef + 2 * lg;
   alignas(16) T x[4 * FL];
 #pragma unroll
   for (int j = 0; j < FL; ++j) {
@@ -300,31 +319,18 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   S* Wm = reinterpret_cast<S*>(a.W) + I.o_W;
   Acc<T> cost, eacc;
   const uint32_t mm = active ? (uint32_t)m : 0u;
-  const int rps = 2 * I.F + 2;
-  // per-row difference emitter
+  // Per-row difference emitter: the + group owns row r0 and the - group row
+  // r0 + 1 of each (x, y) pair, so both halves of the rollout pair store one
+  // difference per pair of rows (e is then the sum of both halves' partial
+  // sums).  csum and esum are plain per-stage partial sums, folded into the
+  // compensated accumulators once per stage.  Every lane shuffles.
   struct Em {
     S* dR;
-    const T* r;
-    int ldK, m, base;
+    const T* r;  // interleaved nominal residual at the stage's first word
+    int ldK, m, base, own_w, ctl_w;
     bool active, plus;
-    T sign, csum;
-    Acc<T>* eacc;
-    __device__ __forceinline__ void operator()(int row_local, T v, bool valid) {
-      const T vo = __shfl_xor_sync(0xffffffffu, v, G);
-      if (!valid) return;
-      csum += v * v;
-      if (plus) {
-        const int row = base + row_local;
-        const T d = (v - vo) * (T)0.5;
-        if (active) dR[(int64_t)row * ldK + m] = to_store<S>(d);
-        eacc->add(d * r[row]);
-      }
-    }
-    // Rows r0 and r0 + 1 at once: the + group owns row r0 and the - group row
-    // r0 + 1, so both halves of the pair store a difference and update e per
-    // pair of rows instead of the + half alone per row (e is then the sum of
-    // both halves' partial sums).  Every lane shuffles.
-    __device__ __forceinline__ void pair(int r0, T v0, T v1, bool valid) {
+    T sign, csum, esum;
+    __device__ __forceinline__ void pair(int slot, int r0, T v0, T v1, bool valid) {
       const T give = plus ? v1 : v0;  // the row the other half owns
       const T got = __shfl_xor_sync(0xffffffffu, give, G);
       if (!valid) return;
@@ -334,9 +340,9 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
       const int row = base + r0 + (plus ? 0 : 1);
       const T d = sign * (own - got) * (T)0.5;
       if (active) dR[(int64_t)row * ldK + m] = to_store<S>(d);
-      eacc->add(d * r[row]);
+      esum += d * r[slot < FL ? 2 * G * slot + own_w : ctl_w];
     }
-  } em{dR, sR, I.ldK, m, 0, active, plus, sign, (T)0, &eacc};
+  } em{dR, sR, I.ldK, m, 0, 2 * lg + (plus ? 0 : 1), 2 * SL + (plus ? 0 : 1), active, plus, sign, (T)0, (T)0};
   // The 2G lanes of a pair draw the normals of 2G consecutive steps at once
   // (lane l of the pair: Philox call q = k + l) and hand them round by shuffle.
   // Sigma points (Method E): pair m perturbs control m alone, by sqrt(n) s_m.
@@ -362,9 +368,12 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
       Wm[(int64_t)(2 * k + 1) * I.ldK + m] = to_store<S>(w1);
     }
     em.base = k * rps;
+    em.r = sR + k * RS;
     em.csum = (T)0;
+    em.esum = (T)0;
     md.rows(x, u, false, em);
     cost.add(em.csum);
+    eacc.add(em.esum);
     {
       T ua[2];
       dead_zone<T, 2>(u, ua, uf_t);
@@ -372,12 +381,15 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
     }
   }
   em.base = I.N * rps;
+  em.r = sR + I.N * RS;
   em.csum = (T)0;
+  em.esum = (T)0;
   {
     const T u0[2] = {(T)0, (T)0};
     md.rows(x, u0, true, em);
   }
   cost.add(em.csum);
+  eacc.add(em.esum);
   // reduce over the group; exchange with the partner group
   const double Cself = 0.5 * group_sum(cost.value(), G, 0xffffffffu);
   double ev = group_sum(eacc.value(), G, 0xffffffffu);
@@ -451,7 +463,7 @@ __global__ void __launch_bounds__(256) k_line_group(RollArgs a) {
       csum += v * v;
       if (out) out[base + row_local] = v;
     }
-    __device__ __forceinline__ void pair(int r0, T v0, T v1, bool valid) {
+    __device__ __forceinline__ void pair(int, int r0, T v0, T v1, bool valid) {
       (*this)(r0, v0, valid);
       (*this)(r0 + 1, v1, valid);
     }

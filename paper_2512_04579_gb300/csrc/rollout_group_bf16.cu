@@ -25,6 +25,7 @@ void fill_group(Launchers* o) {
   o->cost64 = &line<double, FL, G>;
   o->pairs_per_block = 256 / (2 * G);
   o->antithetic_only = 1;
+  o->slots = G * FL;
 }
 }  // namespace
 
