@@ -84,9 +84,11 @@ def uneven_arm(args, dev, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    # per-kernel times of one more iteration on the solve's final state (before
+    # gnmppi_cost, which reloads the inputs and resets the per-instance state)
+    phases = G.gnmppi_phase_times(h, T)
     C = torch.empty(B, dtype=torch.float64, device=dev)
     G.gnmppi_cost(h, G.MEM_DEVICE, dx, dt, dU, C)
-    phases = G.gnmppi_phase_times(h, T)
     G.gnmppi_destroy(h)
     out = {"workload": "%d chain instances, M~U{4..16}, N~U{40..160}, K~U{512,1024,2048,4096}, BF16 contraction" % B,
            "ms_per_batch": ms, "instances_per_s": B / (ms / 1e3), "phases_ms_per_iteration": phases,
@@ -320,6 +322,9 @@ def run_gnmppi(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     launches = G.gnmppi_launch_count(h) - launches0
+    # per-kernel CUDA-event times of one more iteration on the solve's final
+    # state (before gnmppi_cost, which reloads the inputs and resets the state)
+    phases = G.gnmppi_phase_times(h, T)
     # FP64 re-evaluation of the final costs, outside the timed region
     Cfin = torch.empty(batch, dtype=torch.float64, device=dev)
     G.gnmppi_cost(h, G.MEM_DEVICE, d_x0, d_tgt, d_U, Cfin)
@@ -329,8 +334,6 @@ def run_gnmppi(args):
     ms_step = ms / args.steps
     value = world * solved / (ms_step / 1e3)
 
-    # per-kernel CUDA-event times of one iteration on the final state
-    phases = G.gnmppi_phase_times(h, T)
     F = M - 1
     roll_flops = batch * (K) * (N * chain_flops_per_step(F))  # K rollouts of N steps each
     t_roll = phases["samples"] / 1e3

@@ -289,7 +289,8 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     d.n = d.N * d.nu;
     d.Kp = p.sampling == GNMPPI_SAMPLE_SIGMA ? d.n : (anti ? K / 2 : K);  // sigma points: n pairs
     d.ldK = (int)round_up(d.Kp, kPadK);
-    d.ldP = (int)round_up(d.nR + d.n, 8);
+    d.sP = (int)round_up(d.nR, 32);  // S columns start 16-byte aligned (TMA operand of S S^T)
+    d.ldP = (int)round_up(d.sP + d.n, 8);
     if (p.jac_mode == GNMPPI_JAC_LSQ) d.lsq = 1;
     else if (p.jac_mode == GNMPPI_JAC_SIGMA) d.lsq = 0;
     else d.lsq = d.Kp >= d.n ? 1 : 0;
@@ -696,9 +697,8 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
   MARK(3);
   if (ON(3)) {
     if (h->use_tc) {
-      CK(tc_gram_launch(h->tc, h->d_desc, h->d_st, reinterpret_cast<const float*>(h->d_P), h->d_A, h->d_S2,
-                        h->stream));
-      h->launches += 2;
+      CK(tc_gram_launch(h->tc, h->d_st, h->d_A, h->d_S2, h->stream));
+      h->launches++;
     } else {
       ga.tiles = h->d_tiles[1];
       k_gemm_nt<kGram, TA, TC, double><<<h->ntiles[1], 256, 0, h->stream>>>(ga);
@@ -1023,7 +1023,16 @@ extern "C" gnmppi_status gnmppi_debug_read(gnmppi_t h, int32_t what, int32_t ins
       break;
     }
     case 3: st = rows((const unsigned char*)(h->d_e + d.o_C / 2), 8, 1, d.Kp, d.Kp); break;
-    case 4: st = rows(P, h->szA, d.n, d.ldP, d.nR + d.n); break;
+    case 4: {  // rows [P^T | S] without the alignment gap between the two parts
+      need = (int64_t)d.n * (d.nR + d.n);
+      if (count < need) return fail(h, GNMPPI_E_ARG, "buffer too small: need %lld doubles", (long long)need);
+      for (int64_t r = 0; r < d.n && st == GNMPPI_OK; ++r) {
+        double* o = host_out + r * (d.nR + d.n);
+        st = read_typed(h, P + (size_t)r * d.ldP * h->szA, h->szA, 0, d.nR, o);
+        if (st == GNMPPI_OK) st = read_typed(h, P + ((size_t)r * d.ldP + d.sP) * h->szA, h->szA, 0, d.n, o + d.nR);
+      }
+      break;
+    }
     case 5: st = rows((const unsigned char*)(h->d_A + d.o_nn), 8, d.n, d.n, d.n); break;
     case 6: st = rows((const unsigned char*)(h->d_g + d.o_U), 8, 1, d.n, d.n); break;
     case 7: st = rows((const unsigned char*)(h->d_delta + d.o_U), 8, 1, d.n, d.n); break;

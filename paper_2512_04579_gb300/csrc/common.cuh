@@ -24,10 +24,10 @@ struct InstDesc {
   int32_t N, M, F, nx, nu, n, nR, rps;  // rps: residual rows per stage
   int32_t Kp;                           // antithetic pairs, or one-sided samples
   int32_t ldK;                          // padded row length of dR / W (multiple of kPadK)
-  int32_t ldP;                          // row length of [P^T | S] (nR + n, padded)
+  int32_t ldP;                          // row length of [P^T | S] (sP + n, padded; columns nR..sP unused)
   int32_t lsq;                          // 1: J = P S^-1, 0: J = P Sigma^-1 / K'
   int32_t nref;                         // entries of xref
-  int32_t pad;
+  int32_t sP;                           // column of S in a [P^T | S] row: nR rounded up to 32 (16-byte aligned)
   int64_t o_x0, o_xref, o_U;            // packed double arrays (x0; xref; U, s, delta, g, ...)
   int64_t o_dR, o_W;                    // dR [nR][ldK], W [n][ldK] (storage type)
   int64_t o_C;                          // sample costs [Kp][2] (double), e and weights [Kp]

@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256) k_gemm_nt(GemmArgs g) {
     Cbase = reinterpret_cast<TOut*>(g.A) + I.o_nn; ldc = I.n;
   } else {
     Mr = I.n; Nc = I.n; Kd = I.n;
-    Abase = reinterpret_cast<const TIn*>(g.P) + I.o_P + I.nR; lda = I.ldP;
+    Abase = reinterpret_cast<const TIn*>(g.P) + I.o_P + I.sP; lda = I.ldP;
     B1 = Abase; nb1 = I.n; B2 = Abase; ldb = I.ldP;
     Cbase = reinterpret_cast<TOut*>(g.S2) + I.o_nn; ldc = I.n;
   }
@@ -295,7 +295,9 @@ __global__ void __launch_bounds__(256) k_gemm_nt(GemmArgs g) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = j0 + tx * 4 + q;
-      if (j < Nc) Cbase[(int64_t)i * ldc + j] = (TOut)acc[p][q];
+      // contraction: the S columns go to sP on (P^T and S are stored apart)
+      const int jw = (KIND == kContract && j >= I.nR) ? j + (I.sP - I.nR) : j;
+      if (j < Nc) Cbase[(int64_t)i * ldc + jw] = (TOut)acc[p][q];
     }
   }
 }
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_solve(SolveArgs a) {
   double dsq = 0.0;
   for (int i = tid; i < n; i += blockDim.x) {
     double acc;
-    if (lsq) acc = srow_dot(P + (int64_t)i * I.ldP + I.nR, x, yh, yl, n);
+    if (lsq) acc = srow_dot(P + (int64_t)i * I.ldP + I.sP, x, yh, yl, n);
     else acc = Keff * s[i] * s[i] * x[i];
     a.delta[I.o_U + i] = acc;
     a.y[I.o_U + i] = x[i];

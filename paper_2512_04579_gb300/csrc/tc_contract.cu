@@ -12,14 +12,19 @@
 //   warp 0 lane 0  issues TMA loads into a 3-stage shared-memory ring,
 //   warp 1 lane 0  issues tcgen05.mma (M=128, N <= 256, K=16 BF16 / K=8 TF32)
 //                  per sub-tile into its own 256-column TMEM accumulator,
-//   warps 0-3      read TMEM back (tcgen05.ld 32x32b) and store FP32 rows.
+//   warps 0-3      read TMEM back (tcgen05.ld 32x32b) and store FP32 rows
+//                  (the S columns from column sP on, 16-byte aligned).
 //  (2) the Gram product A = P^T P of Eq. 9 in FP32-level accuracy from three
-//      TF32 passes, A ~ Ph Ph^T + Ph Pl^T + Pl Ph^T with P^T = Ph + Pl split into
-//      a TF32 head and its FP32 remainder (k_split_tf32 writes [Ph; Pl] rows;
-//      one 128 x 256 tile per CTA, a 2-stage ring of head + remainder blocks),
-//      and in the same launch S2 = S S^T for the scaled LSQ system: the S
-//      columns sit in the same split rows from a 32-aligned column on.
-// Both use the same kernel, driven by per-instance job descriptors.
+//      TF32 passes, A ~ Ph Ph^T + Ph Pl^T + Pl Ph^T with every FP32 operand
+//      x split into a TF32 head h = rna(x) and its remainder x - h (exact in
+//      FP32), and in the same launch S2 = S S^T for the scaled LSQ system.
+//      TMA streams the FP32 rows of [P^T | S] straight from the contraction's
+//      output; warps 2-3 split each landed stage in shared memory (head in
+//      place, remainder beside it) before the MMAs read it.  A diagonal tile
+//      takes its A sub-tiles from its own B rows (the operand is the same
+//      matrix), each sub-tile's MMAs stop at the diagonal, and the strictly
+//      lower 32 x 32 blocks are also stored transposed, so every entry of the
+//      symmetric output is written once.
 // Every mbarrier wait is bounded by the global timer; a wait that runs out
 // sets the plan's error word and the CTA winds down without a trap.
 #include <cudaTypedefs.h>
@@ -34,6 +39,7 @@ namespace {
 
 constexpr int BM = 128, BN = 256;
 constexpr int ROW_BYTES = 128;  // one k-block of a row: 64 BF16 or 32 FP32 values
+constexpr int KBLK_F32 = 32;
 constexpr int A_BYTES = BM * ROW_BYTES;
 constexpr int B_BYTES = BN * ROW_BYTES;
 constexpr int RING_BYTES = 4 * (A_BYTES + B_BYTES);  // 192 KB of operand ring
@@ -147,29 +153,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// D[i][j] = sum_k A[i][k] B[j][k] for one 128 x 256 tile of one job.  SPLIT3:
-// A and B each have a head block and a remainder block lo_off rows below, and
-// the tile accumulates head*head + head*rem + rem*head.
-template <bool BF16, bool SPLIT3, typename TOut>
-__global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
-                                                    const InstState* __restrict__ st, const int4* __restrict__ tiles,
-                                                    TOut* __restrict__ D, TOut* __restrict__ D2,
-                                                    int* __restrict__ err) {
-  constexpr int KBLK = BF16 ? 64 : 32;   // elements per k-block
-  constexpr int KSTEP = BF16 ? 16 : 8;   // elements per MMA
-  constexpr int NSUB = KBLK / KSTEP;     // MMAs per k-block and operand pair (4)
-  constexpr int PARTS = SPLIT3 ? 2 : 1;  // head (+ remainder) blocks per operand
-  constexpr int MTMAX = SPLIT3 ? 1 : 2;  // 128-row sub-tiles of A per tile (each its own accumulator)
-  constexpr int STAGE_BYTES = PARTS * (MTMAX * A_BYTES + B_BYTES);
+// D[i][j] = sum_k A[i][k] B[j][k] for one (128 or 256) x 256 tile of one
+// contraction job; output columns >= ccut are stored cgap further right.
+template <bool BF16>
+__global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __restrict__ maps,
+                                                        const TcJob* __restrict__ jobs, const InstState* __restrict__ st,
+                                                        const int4* __restrict__ tiles, float* __restrict__ D,
+                                                        int* __restrict__ err) {
+  constexpr int KBLK = BF16 ? 64 : 32;  // elements per k-block
+  constexpr int KSTEP = BF16 ? 16 : 8;  // elements per MMA
+  constexpr int NSUB = KBLK / KSTEP;    // MMAs per k-block and sub-tile (4)
+  constexpr int MTMAX = 2;              // 128-row sub-tiles of A per tile (each its own accumulator)
+  constexpr int STAGE_BYTES = MTMAX * A_BYTES + B_BYTES;
   constexpr int STAGES = RING_BYTES / STAGE_BYTES;
   constexpr uint32_t TCOLS = MTMAX * TMEM_COLS;
   const int4 tl = tiles[blockIdx.x];
   const TcJob J = jobs[tl.x];
   // tl.w: sub-tiles of this tile (1, or 2 when the job has more than 128 rows),
   // so every B tile is streamed once for up to 256 output rows
-  const int mt = SPLIT3 ? 1 : tl.w;
+  const int mt = tl.w;
   const int row_org = tl.y * mt * BM;
-  const uint32_t tx_bytes = (uint32_t)(PARTS * (mt * A_BYTES + B_BYTES));
+  const uint32_t tx_bytes = (uint32_t)(mt * A_BYTES + B_BYTES);
   if (st[J.inst].status != 0) return;  // uniform over the CTA, before any allocation
   const int nkb = J.nkb;
   const CUtensorMap* map = maps + J.map;
@@ -213,16 +217,11 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
       const uint32_t full = su32(bars + s);
       mbar_expect_tx(full, tx_bytes);
       const uint32_t a_dst = su32(base + s * STAGE_BYTES);
-      const uint32_t b_dst = a_dst + PARTS * MTMAX * A_BYTES;
+      const uint32_t b_dst = a_dst + MTMAX * A_BYTES;
       const int x = J.x0 + kb * KBLK;
-#pragma unroll
-      for (int p = 0; p < PARTS; ++p) {
-        const int off = p * J.lo_off;
-        for (int q = 0; q < mt; ++q)
-          tma_load(a_dst + (p * MTMAX + q) * A_BYTES, map, full, x, J.a_row0 + off + row_org + q * BM);
-        tma_load(b_dst + p * B_BYTES, map, full, x, J.b_row0 + off + tl.z * BN);
-        tma_load(b_dst + p * B_BYTES + BM * ROW_BYTES, map, full, x, J.b_row0 + off + tl.z * BN + BM);
-      }
+      for (int q = 0; q < mt; ++q) tma_load(a_dst + q * A_BYTES, map, full, x, J.a_row0 + row_org + q * BM);
+      tma_load(b_dst, map, full, x, J.b_row0 + tl.z * BN);
+      tma_load(b_dst + BM * ROW_BYTES, map, full, x, J.b_row0 + tl.z * BN + BM);
       ++issued;
     }
     // every copy this thread issued has landed before the CTA may exit
@@ -241,17 +240,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
       }
       tc_fence_after();
       const uint32_t a0 = su32(base + s * STAGE_BYTES);
-      const uint32_t b0 = a0 + PARTS * MTMAX * A_BYTES;
+      const uint32_t b0 = a0 + MTMAX * A_BYTES;
 #pragma unroll
       for (int k = 0; k < NSUB; ++k) {
         // sub-tile q accumulates into TMEM columns [256 q, 256 q + 256)
         for (int q = 0; q < mt; ++q)
           mma<BF16>(tmem + (uint32_t)(q * TMEM_COLS), sdesc(a0 + q * A_BYTES + k * 32), sdesc(b0 + k * 32), id,
                     (kb > 0 || k > 0) ? 1u : 0u);
-        if (SPLIT3) {
-          mma<BF16>(tmem, sdesc(a0 + k * 32), sdesc(b0 + B_BYTES + k * 32), id, 1u);
-          mma<BF16>(tmem, sdesc(a0 + A_BYTES + k * 32), sdesc(b0 + k * 32), id, 1u);
-        }
       }
       mma_commit(su32(bars + STAGES + s));  // frees the stage once these MMAs have read it
     }
@@ -268,26 +263,27 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
   tc_fence_after();
   // tcgen05.ld is warp-collective: the whole warp takes the same branch
   if (__all_sync(0xffffffffu, ok && !*abort)) {
-    TOut* stg = reinterpret_cast<TOut*>(base) + warp * 32 * 33;
-    TOut* out = (J.out_sel ? D2 : D) + J.out_off;
+    float* stg = reinterpret_cast<float*>(base) + warp * 32 * 33;
+    float* out = D + J.out_off;
 #pragma unroll 1
     for (int sub = 0; sub < mt; ++sub) {
-    const int row0 = row_org + sub * BM + warp * 32;
+      const int row0 = row_org + sub * BM + warp * 32;
 #pragma unroll 1
-    for (int c = 0; c < BN / 32 && tl.z * BN + c * 32 < J.Nc; ++c) {  // uniform: kept 32-column chunks
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sub * TMEM_COLS + c * 32), v);
+      for (int c = 0; c < BN / 32 && tl.z * BN + c * 32 < J.Nc; ++c) {  // uniform: kept 32-column chunks
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sub * TMEM_COLS + c * 32), v);
 #pragma unroll
-      for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = (TOut)__uint_as_float(v[q]);
-      __syncwarp();
-      const int col = tl.z * BN + c * 32 + lane;
-      if (col < J.Nc) {
+        for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = __uint_as_float(v[q]);
+        __syncwarp();
+        const int col = tl.z * BN + c * 32 + lane;
+        if (col < J.Nc) {
+          const int colw = col < J.ccut ? col : col + J.cgap;
 #pragma unroll 4
-        for (int rr = 0; rr < 32; ++rr)
-          if (row0 + rr < J.M) out[(int64_t)(row0 + rr) * J.ldc + col] = stg[rr * 33 + lane];
+          for (int rr = 0; rr < 32; ++rr)
+            if (row0 + rr < J.M) out[(int64_t)(row0 + rr) * J.ldc + colw] = stg[rr * 33 + lane];
+        }
+        __syncwarp();
       }
-      __syncwarp();
-    }
     }
   } else if (threadIdx.x == 0) {
     atomicExch(err, 1);
@@ -300,30 +296,209 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const CUtensorMap* __restric
   }
 }
 
-// [Ph; Pl] rows of the Gram operand: Ph = [P^T | S] rounded to TF32
-// (cvt.rna), Pl = [P^T | S] - Ph (exact in FP32).  The P^T columns go to
-// [0, nR), the S columns (LSQ mode) to [nRp, nRp + n) with nRp = nR rounded
-// up to a k-block; the gap stays zero.  One CTA per instance row.
-__global__ void __launch_bounds__(256) k_split_tf32(const InstDesc* __restrict__ inst, const InstState* __restrict__ st,
-                                                    const int2* __restrict__ rows, const float* __restrict__ P,
-                                                    float* __restrict__ G, const int64_t* __restrict__ g_off,
-                                                    const int* __restrict__ g_ld) {
-  const int2 rb = rows[blockIdx.x];  // (instance, row)
-  if (st[rb.x].status != 0) return;
-  const InstDesc I = inst[rb.x];
-  const float* src = P + I.o_P + (int64_t)rb.y * I.ldP;
-  float* hi = G + g_off[rb.x] + (int64_t)rb.y * g_ld[rb.x];
-  float* lo = hi + (int64_t)I.n * g_ld[rb.x];
-  const int nRp = (I.nR + 31) / 32 * 32;
-  const int ncol = I.nR + (I.lsq ? I.n : 0);
-  for (int k = threadIdx.x; k < ncol; k += blockDim.x) {
-    const float x = src[k];
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    const float hf = __uint_as_float(h);
-    const int c = k < I.nR ? k : nRp + (k - I.nR);
-    hi[c] = hf;
-    lo[c] = x - hf;
+__device__ __forceinline__ float tf32_head(float x) {
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  return __uint_as_float(h);
+}
+
+// Splits `n4` float4 of a landed operand block in place: head (TF32) at p,
+// remainder at p + delta bytes.  Same positions in both blocks, so the
+// 128-byte swizzle of the TMA layout carries over.
+__device__ __forceinline__ void split_block(unsigned char* p, int delta, int n4, int t, int nt) {
+#pragma unroll 4
+  for (int i = t; i < n4; i += nt) {
+    float4* hp = reinterpret_cast<float4*>(p) + i;
+    const float4 x = *hp;
+    float4 h, l;
+    h.x = tf32_head(x.x);
+    h.y = tf32_head(x.y);
+    h.z = tf32_head(x.z);
+    h.w = tf32_head(x.w);
+    l.x = x.x - h.x;
+    l.y = x.y - h.y;
+    l.z = x.z - h.z;
+    l.w = x.w - h.w;
+    *hp = h;
+    *reinterpret_cast<float4*>(p + delta + (size_t)i * 16) = l;
+  }
+}
+
+// Gram tile of one job: output rows tl.y.., columns tl.z.. (the B rows),
+// tl.w = sub-tiles (1 or 2) | 4 if the tile sits on the diagonal.  Per stage
+// (one 32-column k-block): B head and remainder (256 rows), and for an
+// off-diagonal tile A head and remainder (128 rows).
+__global__ void __launch_bounds__(128, 1) k_gram_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
+                                                    const InstState* __restrict__ st, const int4* __restrict__ tiles,
+                                                    double* __restrict__ A, double* __restrict__ S2,
+                                                    int* __restrict__ err) {
+  constexpr int KBLK = 32, NSUB = 4;  // FP32 elements per k-block, TF32 MMAs (K = 8) per k-block
+  constexpr int SPLITTERS = 64;       // warps 2-3
+  constexpr int MAXST = 3;
+  const int4 tl = tiles[blockIdx.x];
+  const TcJob J = jobs[tl.x];
+  const int mt = tl.w & 3;
+  const bool diag = (tl.w & 4) != 0;
+  const int row_org = tl.y, col_org = tl.z;
+  const int kept = min(BN, J.Nc - col_org);  // output columns of this tile = B rows
+  const int nbox = kept > BM ? 2 : 1;        // 128-row TMA boxes of B
+  const int stage_bytes = diag ? 2 * B_BYTES : 2 * (B_BYTES + A_BYTES);
+  const int stages = RING_BYTES / stage_bytes;  // 3 (diagonal) or 2
+  const uint32_t tx_bytes = (uint32_t)(nbox * BM * ROW_BYTES + (diag ? 0 : A_BYTES));
+  const uint32_t tcols = mt == 2 ? 2 * TMEM_COLS : TMEM_COLS;
+  if (st[J.inst].status != 0) return;  // uniform over the CTA, before any allocation
+  const int nkb = J.nkb;
+  const CUtensorMap* map = maps + J.map;
+
+  extern __shared__ unsigned char smem_dyn[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + RING_BYTES);
+  // bars[0..3): full (TMA landed), [3..6): split (heads and remainders
+  // written), [6..9): empty (MMAs done with the stage), [9]: done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * MAXST + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MAXST; ++s) {
+      mbar_init(su32(bars + s), 1);
+      mbar_init(su32(bars + MAXST + s), SPLITTERS);
+      mbar_init(su32(bars + 2 * MAXST + s), 1);
+    }
+    mbar_init(su32(bars + 3 * MAXST), 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t done = su32(bars + 3 * MAXST);
+  // stage layout: B head [0, 32K), B remainder [32K, 64K), A head, A remainder (off-diagonal)
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % stages, round = kb / stages;
+      if (kb >= stages && !mbar_wait(su32(bars + 2 * MAXST + s), (round - 1) & 1, abort, true)) {
+        *abort = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      const uint32_t full = su32(bars + s);
+      mbar_expect_tx(full, tx_bytes);
+      const uint32_t b_dst = su32(base + s * stage_bytes);
+      const int x = J.x0 + kb * KBLK;
+      for (int q = 0; q < nbox; ++q) tma_load(b_dst + q * A_BYTES, map, full, x, col_org + q * BM);
+      if (!diag) tma_load(b_dst + 2 * B_BYTES, map, full, x, row_org);
+      ++issued;
+    }
+    for (int kb = (issued > stages ? issued - stages : 0); kb < issued; ++kb)
+      mbar_wait(su32(bars + kb % stages), (kb / stages) & 1, abort, false);
+  } else if (warp >= 2) {
+    // ---------------- splitters: head in place, remainder beside it
+    const int t = threadIdx.x - 64;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % stages, round = kb / stages;
+      if (!mbar_wait(su32(bars + s), round & 1, abort, true)) {
+        *abort = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      unsigned char* sb = base + s * stage_bytes;
+      split_block(sb, B_BYTES, nbox * A_BYTES / 16, t, SPLITTERS);
+      if (!diag) split_block(sb + 2 * B_BYTES, A_BYTES, A_BYTES / 16, t, SPLITTERS);
+      // the generic-proxy writes become visible to the tensor core's reads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bars + MAXST + s)) : "memory");
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer: three TF32 passes per sub-tile
+    uint32_t id[2];
+    for (int q = 0; q < 2; ++q) {
+      const int need = diag ? min(kept, BM * (q + 1)) : kept;  // columns up to the diagonal
+      id[q] = idesc<false>(min(BN, (need + 15) / 16 * 16));
+    }
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % stages, round = kb / stages;
+      if (!mbar_wait(su32(bars + MAXST + s), round & 1, abort, true)) {
+        *abort = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t bh = su32(base + s * stage_bytes), bl = bh + B_BYTES;
+#pragma unroll
+      for (int k = 0; k < NSUB; ++k) {
+        for (int q = 0; q < mt; ++q) {
+          // diagonal: A sub-tile q is B rows [128 q, 128 q + 128)
+          const uint32_t ah = diag ? bh + q * A_BYTES : bh + 2 * B_BYTES;
+          const uint32_t al = diag ? bl + q * A_BYTES : bh + 2 * B_BYTES + A_BYTES;
+          const uint32_t d = tmem + (uint32_t)(q * TMEM_COLS);
+          mma<false>(d, sdesc(ah + k * 32), sdesc(bh + k * 32), id[q], (kb > 0 || k > 0) ? 1u : 0u);
+          mma<false>(d, sdesc(ah + k * 32), sdesc(bl + k * 32), id[q], 1u);
+          mma<false>(d, sdesc(al + k * 32), sdesc(bh + k * 32), id[q], 1u);
+        }
+      }
+      mma_commit(su32(bars + 2 * MAXST + s));
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: rows of D, and the transposes of the blocks
+  // strictly below the diagonal (whose mirror images no tile computes)
+  const bool ok = mbar_wait(done, 0, abort, false);
+  tc_fence_after();
+  if (__all_sync(0xffffffffu, ok && !*abort)) {
+    double* stg = reinterpret_cast<double*>(base) + warp * 32 * 33;
+    double* out = (J.out_sel ? S2 : A) + J.out_off;
+#pragma unroll 1
+    for (int sub = 0; sub < mt; ++sub) {
+      const int row0 = row_org + sub * BM + warp * 32;
+      const int cend = diag ? min(kept, BM * (sub + 1)) : kept;
+#pragma unroll 1
+      for (int c = 0; c * 32 < cend; ++c) {  // uniform over the warp
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sub * TMEM_COLS + c * 32), v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = (double)__uint_as_float(v[q]);
+        __syncwarp();
+        const int col = col_org + c * 32 + lane;
+        if (col < J.Nc) {
+#pragma unroll 4
+          for (int rr = 0; rr < 32; ++rr)
+            if (row0 + rr < J.M) out[(int64_t)(row0 + rr) * J.ldc + col] = stg[rr * 33 + lane];
+        }
+        if (!diag || c < 4 * sub) {  // strictly lower block: store its transpose too
+          const int rowt = row0 + lane;
+          if (rowt < J.M) {
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+              const int colt = col_org + c * 32 + rr;
+              if (colt < J.Nc) out[(int64_t)colt * J.ldc + rowt] = stg[lane * 33 + rr];
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
   }
 }
 
@@ -361,6 +536,17 @@ static bool plan_alloc(TcPlan* plan, P** p, size_t bytes) {
   return true;
 }
 
+// Gram tiles of an n x n symmetric output: per 256-column block J the
+// diagonal tile (rows = columns, one or two 128-row sub-tiles), then the
+// 128-row off-diagonal tiles below it.
+static void gram_tiles(int job, int n, std::vector<int4>& out) {
+  for (int J = 0; J * BN < n; ++J) {
+    const int r0 = J * BN;
+    out.push_back(make_int4(job, r0, r0, (n - r0 > BM ? 2 : 1) | 4));
+    for (int i = r0 + BN; i < n; i += BM) out.push_back(make_int4(job, i, r0, 1));
+  }
+}
+
 gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void* P, int bf16, cudaStream_t stream,
                              TcPlan* plan, std::string& err) {
   plan->bf16 = bf16;
@@ -369,28 +555,17 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
   const size_t esz = bf16 ? 2 : 4;
   const int kblk = bf16 ? 64 : 32;
   const int nb = (int)desc.size();
-  // Gram operand blocks [Ph; Pl], rows of ldG = nR rounded to 32 floats plus,
-  // in LSQ mode, n rounded to 32 floats for the S columns
-  std::vector<int64_t> g_off(nb);
-  std::vector<int> g_ld(nb);
-  int64_t g_total = 0;
-  for (int b = 0; b < nb; ++b) {
-    g_ld[b] = (int)((desc[b].nR + 31) / 32 * 32) + (desc[b].lsq ? (int)((desc[b].n + 31) / 32 * 32) : 0);
-    g_off[b] = g_total;
-    g_total += 2 * (int64_t)desc[b].n * g_ld[b];
-  }
-  if (!plan_alloc(plan, &plan->d_G, 4 * (size_t)std::max<int64_t>(g_total, 4))) {
-    err = "cudaMalloc failed for the Gram operands";
-    return GNMPPI_E_NOMEM;
-  }
-  std::vector<CUtensorMap> maps(2 * (size_t)nb);
+  std::vector<CUtensorMap> maps(3 * (size_t)nb);
   std::vector<TcJob> jobs(3 * (size_t)nb);
   std::vector<int4> tc, tg;
-  std::vector<int2> rows;
   for (int b = 0; b < nb; ++b) {
     const InstDesc& d = desc[b];
     if (d.ldK % kblk != 0) {
       err = "sample padding is not a multiple of the k-block";
+      return GNMPPI_E_ARG;
+    }
+    if (d.sP % 32 != 0 || d.ldP % 4 != 0 || d.o_P % 4 != 0) {
+      err = "[P^T | S] rows are not 16-byte aligned";
       return GNMPPI_E_ARG;
     }
     // contraction: one map over the instance's [dR; W] block
@@ -400,65 +575,58 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
       return GNMPPI_E_CUDA;
     }
     TcJob& jc = jobs[b];
+    jc = TcJob{};
     jc.inst = b;
     jc.map = b;
     jc.a_row0 = d.nR;
     jc.b_row0 = 0;
-    jc.lo_off = 0;
     jc.M = d.n;
     jc.Nc = d.nR + d.n;
     jc.nkb = d.ldK / kblk;
+    jc.x0 = 0;
     jc.out_off = d.o_P;
     jc.ldc = d.ldP;
-    jc.x0 = 0;
-    jc.out_sel = 0;
+    jc.ccut = d.nR;          // S columns of the output ...
+    jc.cgap = d.sP - d.nR;   // ... start at sP
     const int mt = d.n > BM ? 2 : 1;  // up to 256 rows per tile: each B tile streamed once
     for (int i = 0; i < (d.n + mt * BM - 1) / (mt * BM); ++i)
       for (int j = 0; j < (d.nR + d.n + BN - 1) / BN; ++j) tc.push_back(make_int4(b, i, j, mt));
-    // Gram: one FP32 map over [Ph; Pl] (2n rows, ldG columns)
-    if (!encode_rows(encode, &maps[nb + b], plan->d_G + g_off[b], false, g_ld[b], g_ld[b], 2 * (int64_t)d.n)) {
+    // Gram: FP32 maps over the P^T columns (nR) and the S columns (n) of [P^T | S]
+    float* Pb = reinterpret_cast<float*>(P) + d.o_P;
+    if (!encode_rows(encode, &maps[nb + b], Pb, false, d.nR, d.ldP, d.n) ||
+        !encode_rows(encode, &maps[2 * nb + b], Pb + d.sP, false, d.n, d.ldP, d.n)) {
       err = "cuTensorMapEncodeTiled failed (Gram, instance " + std::to_string(b) + ")";
       return GNMPPI_E_CUDA;
     }
     TcJob& jg = jobs[nb + b];
+    jg = TcJob{};
     jg.inst = b;
     jg.map = nb + b;
-    jg.a_row0 = 0;
-    jg.b_row0 = 0;
-    jg.lo_off = d.n;
     jg.M = d.n;
     jg.Nc = d.n;
-    jg.nkb = (d.nR + 31) / 32;
+    jg.nkb = (d.nR + KBLK_F32 - 1) / KBLK_F32;
     jg.out_off = d.o_nn;
     jg.ldc = d.n;
-    jg.x0 = 0;
-    jg.out_sel = 0;
-    for (int i = 0; i < (d.n + BM - 1) / BM; ++i)
-      for (int j = 0; j < (d.n + BN - 1) / BN; ++j) tg.push_back(make_int4(nb + b, i, j, 1));
-    // S2 = S S^T over the S columns of the same split rows (LSQ mode)
+    jg.ccut = d.n;
+    gram_tiles(nb + b, d.n, tg);
+    // S2 = S S^T over the S columns (LSQ mode)
     TcJob& js = jobs[2 * nb + b];
     js = jg;
-    js.x0 = (d.nR + 31) / 32 * 32;
-    js.nkb = (d.n + 31) / 32;
+    js.map = 2 * nb + b;
+    js.nkb = (d.n + KBLK_F32 - 1) / KBLK_F32;
     js.out_sel = 1;
-    if (d.lsq)
-      for (int i = 0; i < (d.n + BM - 1) / BM; ++i)
-        for (int j = 0; j < (d.n + BN - 1) / BN; ++j) tg.push_back(make_int4(2 * nb + b, i, j, 1));
-    for (int r = 0; r < d.n; ++r) rows.push_back(make_int2(b, r));
+    if (d.lsq) gram_tiles(2 * nb + b, d.n, tg);
   }
   if (!plan_alloc(plan, &plan->d_maps, sizeof(CUtensorMap) * maps.size()) ||
       !plan_alloc(plan, &plan->d_jobs, sizeof(TcJob) * jobs.size()) ||
       !plan_alloc(plan, &plan->d_tiles_c, sizeof(int4) * std::max<size_t>(1, tc.size())) ||
       !plan_alloc(plan, &plan->d_tiles_g, sizeof(int4) * std::max<size_t>(1, tg.size())) ||
-      !plan_alloc(plan, &plan->d_rows, sizeof(int2) * std::max<size_t>(1, rows.size())) ||
-      !plan_alloc(plan, &plan->d_goff, sizeof(int64_t) * (size_t)nb) ||
-      !plan_alloc(plan, &plan->d_gld, sizeof(int) * (size_t)nb) || !plan_alloc(plan, &plan->d_err, sizeof(int))) {
+      !plan_alloc(plan, &plan->d_err, sizeof(int))) {
     err = "cudaMalloc failed for the tensor-core plan";
     return GNMPPI_E_NOMEM;
   }
   plan->ntiles_c = (int)tc.size();
   plan->ntiles_g = (int)tg.size();
-  plan->nrows = (int)rows.size();
   bool ok = cudaMemcpyAsync(plan->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
                             stream) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(plan->d_jobs, jobs.data(), sizeof(TcJob) * jobs.size(), cudaMemcpyHostToDevice, stream) ==
@@ -467,51 +635,44 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
                  cudaSuccess;
   ok = ok && cudaMemcpyAsync(plan->d_tiles_g, tg.data(), sizeof(int4) * tg.size(), cudaMemcpyHostToDevice, stream) ==
                  cudaSuccess;
-  ok = ok && cudaMemcpyAsync(plan->d_rows, rows.data(), sizeof(int2) * rows.size(), cudaMemcpyHostToDevice, stream) ==
-                 cudaSuccess;
-  ok = ok && cudaMemcpyAsync(plan->d_goff, g_off.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, stream) ==
-                 cudaSuccess;
-  ok = ok && cudaMemcpyAsync(plan->d_gld, g_ld.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, stream) == cudaSuccess;
-  ok = ok && cudaMemsetAsync(plan->d_G, 0, 4 * (size_t)std::max<int64_t>(g_total, 4), stream) == cudaSuccess;
   ok = ok && cudaMemsetAsync(plan->d_err, 0, sizeof(int), stream) == cudaSuccess;
   if (!ok) {
     err = "copying the tensor-core plan failed";
     return GNMPPI_E_CUDA;
   }
+  // the host vectors are temporaries
+  if (cudaStreamSynchronize(stream) != cudaSuccess) {
+    err = "copying the tensor-core plan failed";
+    return GNMPPI_E_CUDA;
+  }
   plan->smem = RING_BYTES + 1024 + 256;
-  cudaError_t e = bf16 ? cudaFuncSetAttribute(k_gemm_tc<true, false, float>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem)
-                       : cudaFuncSetAttribute(k_gemm_tc<false, false, float>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gemm_tc<false, true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
+  cudaError_t e = bf16 ? cudaFuncSetAttribute(k_contract_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              plan->smem)
+                       : cudaFuncSetAttribute(k_contract_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              plan->smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
   if (e != cudaSuccess) {
     err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
     return GNMPPI_E_CUDA;
   }
-  (void)P;
   return GNMPPI_OK;
 }
 
 cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float* P, cudaStream_t stream) {
   if (plan.ntiles_c == 0) return cudaSuccess;
   if (plan.bf16)
-    k_gemm_tc<true, false, float><<<plan.ntiles_c, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
-                                                                             plan.d_tiles_c, P, P, plan.d_err);
+    k_contract_tc<true><<<plan.ntiles_c, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st, plan.d_tiles_c, P,
+                                                                   plan.d_err);
   else
-    k_gemm_tc<false, false, float><<<plan.ntiles_c, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
-                                                                              plan.d_tiles_c, P, P, plan.d_err);
+    k_contract_tc<false><<<plan.ntiles_c, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st, plan.d_tiles_c, P,
+                                                                    plan.d_err);
   return cudaGetLastError();
 }
 
-cudaError_t tc_gram_launch(const TcPlan& plan, const InstDesc* d_desc, const InstState* d_st, const float* P, double* A,
-                           double* S2, cudaStream_t stream) {
+cudaError_t tc_gram_launch(const TcPlan& plan, const InstState* d_st, double* A, double* S2, cudaStream_t stream) {
   if (plan.ntiles_g == 0) return cudaSuccess;
-  k_split_tf32<<<plan.nrows, 256, 0, stream>>>(d_desc, d_st, plan.d_rows, P, plan.d_G, plan.d_goff, plan.d_gld);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_gemm_tc<false, true, double><<<plan.ntiles_g, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
-                                                                            plan.d_tiles_g, A, S2, plan.d_err);
+  k_gram_tc<<<plan.ntiles_g, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st, plan.d_tiles_g, A, S2,
+                                                       plan.d_err);
   return cudaGetLastError();
 }
 
