@@ -296,10 +296,12 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
   }
 }
 
+// TF32 head of x: rounded to 10 mantissa bits, to nearest with ties away
+// from zero, on the bit pattern (adding half a TF32 unit to the magnitude
+// bits carries into the kept bits, the exponent included), then the 13 low
+// bits cleared.  Integer pipe work; the remainder x - head is exact in FP32.
 __device__ __forceinline__ float tf32_head(float x) {
-  uint32_t h;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-  return __uint_as_float(h);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // Splits `n4` float4 of a landed operand block in place: head (TF32) at p,
@@ -327,13 +329,15 @@ __device__ __forceinline__ void split_block(unsigned char* p, int delta, int n4,
 // Gram tile of one job: output rows tl.y.., columns tl.z.. (the B rows),
 // tl.w = sub-tiles (1 or 2) | 4 if the tile sits on the diagonal.  Per stage
 // (one 32-column k-block): B head and remainder (256 rows), and for an
-// off-diagonal tile A head and remainder (128 rows).
-__global__ void __launch_bounds__(128, 1) k_gram_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
+// off-diagonal tile A head and remainder (128 rows).  192 threads: warp 0
+// lane 0 TMA, warp 1 lane 0 MMA, warps 2-5 split; warps 0-3 read TMEM back.
+constexpr int kGramThreads = 192;
+__global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
                                                     const InstState* __restrict__ st, const int4* __restrict__ tiles,
                                                     double* __restrict__ A, double* __restrict__ S2,
                                                     int* __restrict__ err) {
   constexpr int KBLK = 32, NSUB = 4;  // FP32 elements per k-block, TF32 MMAs (K = 8) per k-block
-  constexpr int SPLITTERS = 64;       // warps 2-3
+  constexpr int SPLITTERS = kGramThreads - 64;  // warps 2-5
   constexpr int MAXST = 3;
   const int4 tl = tiles[blockIdx.x];
   const TcJob J = jobs[tl.x];
@@ -455,10 +459,13 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const CUtensorMap* __restric
   __syncwarp();
 
   // ---------------- epilogue: rows of D, and the transposes of the blocks
-  // strictly below the diagonal (whose mirror images no tile computes)
+  // strictly below the diagonal (whose mirror images no tile computes);
+  // warps 0-3, one per 32 TMEM lanes
   const bool ok = mbar_wait(done, 0, abort, false);
   tc_fence_after();
-  if (__all_sync(0xffffffffu, ok && !*abort)) {
+  if (warp >= 4) {
+    // no TMEM lanes of their own
+  } else if (__all_sync(0xffffffffu, ok && !*abort)) {
     double* stg = reinterpret_cast<double*>(base) + warp * 32 * 33;
     double* out = (J.out_sel ? S2 : A) + J.out_off;
 #pragma unroll 1
@@ -557,7 +564,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
   const int nb = (int)desc.size();
   std::vector<CUtensorMap> maps(3 * (size_t)nb);
   std::vector<TcJob> jobs(3 * (size_t)nb);
-  std::vector<int4> tc, tg;
+  std::vector<int4> tc, tg, ts;
   for (int b = 0; b < nb; ++b) {
     const InstDesc& d = desc[b];
     if (d.ldK % kblk != 0) {
@@ -615,8 +622,22 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     js.map = 2 * nb + b;
     js.nkb = (d.n + KBLK_F32 - 1) / KBLK_F32;
     js.out_sel = 1;
-    if (d.lsq) gram_tiles(2 * nb + b, d.n, tg);
+    if (d.lsq) gram_tiles(2 * nb + b, d.n, ts);
   }
+  // longest first, so that the short tiles (the S2 products, small
+  // instances) fill the SMs that the last long ones leave idle.  Gram tiles
+  // by k-blocks x sub-tiles x kept columns; contraction tiles by their
+  // instance's k-blocks x sub-tiles only, so that the column tiles of an
+  // instance, which share its W rows in L2, stay adjacent.
+  tg.insert(tg.end(), ts.begin(), ts.end());
+  auto gram_work = [&](const int4& t) {
+    const TcJob& j = jobs[t.x];
+    return (int64_t)j.nkb * (t.w & 3) * std::min(BN, j.Nc - t.z);
+  };
+  auto contract_work = [&](const int4& t) { return (int64_t)jobs[t.x].nkb * t.w; };
+  std::stable_sort(tc.begin(), tc.end(),
+                   [&](const int4& a, const int4& b) { return contract_work(a) > contract_work(b); });
+  std::stable_sort(tg.begin(), tg.end(), [&](const int4& a, const int4& b) { return gram_work(a) > gram_work(b); });
   if (!plan_alloc(plan, &plan->d_maps, sizeof(CUtensorMap) * maps.size()) ||
       !plan_alloc(plan, &plan->d_jobs, sizeof(TcJob) * jobs.size()) ||
       !plan_alloc(plan, &plan->d_tiles_c, sizeof(int4) * std::max<size_t>(1, tc.size())) ||
@@ -671,7 +692,7 @@ cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float*
 
 cudaError_t tc_gram_launch(const TcPlan& plan, const InstState* d_st, double* A, double* S2, cudaStream_t stream) {
   if (plan.ntiles_g == 0) return cudaSuccess;
-  k_gram_tc<<<plan.ntiles_g, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st, plan.d_tiles_g, A, S2,
+  k_gram_tc<<<plan.ntiles_g, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st, plan.d_tiles_g, A, S2,
                                                        plan.d_err);
   return cudaGetLastError();
 }
