@@ -216,7 +216,8 @@ gnmppi_status gnmppi_cost(gnmppi_t h, int32_t mem, const double* x0, const doubl
  * gnmppi_solve iteration to host memory as doubles, for verification.
  * what: 0 dR [nR][K'], 1 W [n][K'], 2 sample costs [K'][2] (one-sided: [K]), 3 e = dR r [K'],
  * 4 [P^T | S] [n][nR+n], 5 A = P^T P [n][n], 6 g = P^T r [n], 7 delta [n],
- * 8 line-search costs [L(+1)], 9 nominal residual r [nR], 10 MPPI direction [n].
+ * 8 line-search costs [L(+1)], 9 nominal residual r [nR], 10 MPPI direction [n],
+ * 11 S2 = S S^T [n][n] (formed for instances in LSQ mode only).
  * count: capacity of host_out in doubles; the number written is returned in
  * *written.  Errors: E_ARG for unknown `what` or too small a buffer. */
 gnmppi_status gnmppi_debug_read(gnmppi_t h, int32_t what, int32_t inst, double* host_out, int64_t count,

@@ -1039,6 +1039,7 @@ extern "C" gnmppi_status gnmppi_debug_read(gnmppi_t h, int32_t what, int32_t ins
     case 8: st = rows((const unsigned char*)(h->d_Cl + (int64_t)inst * (kMaxL + 1)), 8, 1, h->p.L, h->p.L); break;
     case 9: st = rows((const unsigned char*)h->d_r + h->szT * d.o_R, h->szT, 1, d.nR, d.nR); break;
     case 10: st = rows((const unsigned char*)(h->d_mppi + d.o_U), 8, 1, d.n, d.n); break;
+    case 11: st = rows((const unsigned char*)(h->d_S2 + d.o_nn), 8, d.n, d.n, d.n); break;
     default: return fail(h, GNMPPI_E_ARG, "unknown buffer %d", what);
   }
   if (written) *written = (st == GNMPPI_OK) ? need : 0;

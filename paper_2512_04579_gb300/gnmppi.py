@@ -364,7 +364,7 @@ def gnmppi_launch_count(h) -> int:
     return int(load().gnmppi_launch_count(h))
 
 
-DEBUG = {"dR": 0, "W": 1, "C": 2, "e": 3, "PS": 4, "A": 5, "g": 6, "delta": 7, "Cline": 8, "r": 9, "mppi": 10}
+DEBUG = {"dR": 0, "W": 1, "C": 2, "e": 3, "PS": 4, "A": 5, "g": 6, "delta": 7, "Cline": 8, "r": 9, "mppi": 10, "S2": 11}
 
 
 @dataclass

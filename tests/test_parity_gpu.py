@@ -330,6 +330,54 @@ def test_tensor_core_contraction_matches_oracle(prec, tol):
     assert np.allclose(A, A.T, rtol=1e-5, atol=1e-5 * np.abs(A).max())
 
 
+@pytest.mark.parametrize("prec", [G.PREC_FP32, G.PREC_BF16])
+@pytest.mark.parametrize("M,N,K", [(6, 75, 1400), (4, 150, 640), (3, 260, 1056)])
+def test_tensor_core_gram_matches_its_definition(prec, M, N, K):
+    """A = P^T P and S2 = S S^T of Eq. 9 from the tcgen05 Gram kernel (TF32
+    head/remainder split in shared memory, three passes, FP32 accumulation)
+    against the same products formed in FP64 from the [P^T | S] the GPU holds,
+    at n = 150, 300 and 520: one and two 128-row sub-tiles on the diagonal,
+    off-diagonal tiles, lower blocks stored transposed, ragged edges.  Every
+    entry must be written (a stale or missing block fails the entrywise
+    bound) and A symmetric."""
+    seed = 31
+    n = 2 * N
+    x0, tgt = I.chain_instances(seed, 1, M)
+    gp = G.chain_problem(M=M, N=N, K=K, iterations=1, lam=1e-3, sigma0=0.2, seed=seed, precision=prec)
+    s = G.Solver(gp, 1)
+    s.step(x0[0], tgt[0], np.zeros(n), np.full(n, 0.2), 0)
+    PS = s.debug("PS")
+    nR = PS.size // n - n
+    PS = PS.reshape(n, nR + n)
+    A = s.debug("A").reshape(n, n)
+    S2 = s.debug("S2").reshape(n, n)
+    s.close()
+    assert K // 2 >= n  # LSQ mode: S2 is formed
+    Pt, S = PS[:, :nR], PS[:, nR:]
+    for got, ref in ((A, Pt @ Pt.T), (S2, S @ S.T)):
+        # Each entry is a dot product of two rows: its rounding error is
+        # bounded by a multiple of |row_i| |row_j| = sqrt(ref_ii ref_jj)
+        # (Cauchy-Schwarz).  The split itself leaves ~2^-22 per product; the
+        # tensor core's FP32 accumulation over nR = 1206-1566 terms measures
+        # ~2e-5 of that scale here, so 1e-4 bounds it while a stale or missing
+        # block (an O(1) error) fails.
+        d = np.sqrt(np.diag(ref))
+        assert rel(got, ref) < 5e-5
+        assert np.all(np.abs(got - ref) <= 1e-4 * np.outer(d, d))
+    assert np.all(np.abs(A - A.T) <= 1e-4 * np.outer(np.sqrt(np.diag(A)), np.sqrt(np.diag(A))))
+    # The remainder passes take effect: the head-only product hi hi^T (hi =
+    # [P^T] rounded to TF32, the one pass a dropped remainder would leave) has
+    # a different, larger error, and the GPU's error is uncorrelated with it.
+    u = Pt.astype(np.float32).view(np.uint32).astype(np.uint64)
+    hi = ((u + 0x1000) & 0xFFFFE000).astype(np.uint32).view(np.float32).astype(np.float64)
+    Aref = Pt @ Pt.T
+    d = np.sqrt(np.diag(Aref))
+    e_gpu = (A - Aref) / np.outer(d, d)
+    e_head = (hi @ hi.T - Aref) / np.outer(d, d)
+    assert np.sqrt(np.mean(e_gpu ** 2)) < 0.5 * np.sqrt(np.mean(e_head ** 2))
+    assert abs(np.sum(e_gpu * e_head)) < 0.3 * np.sqrt(np.sum(e_gpu ** 2) * np.sum(e_head ** 2))
+
+
 @pytest.mark.parametrize("M,N,K", [(20, 15, 200), (40, 10, 96), (65, 6, 64)])
 def test_fp64_group_rollout_chains_per_iteration(M, N, K):
     """Chains of 19, 39 and 64 free masses: a group of 4 or 8 lanes per rollout
