@@ -59,7 +59,7 @@ struct gnmppi_s {
   Consts cs{};
   // workspace
   double *d_x0 = nullptr, *d_xref = nullptr, *d_U = nullptr, *d_s = nullptr, *d_g = nullptr, *d_mppi = nullptr;
-  double *d_delta = nullptr, *d_y = nullptr, *d_wt = nullptr, *d_C = nullptr, *d_e = nullptr, *d_A = nullptr;
+  double *d_delta = nullptr, *d_y = nullptr, *d_C = nullptr, *d_e = nullptr, *d_A = nullptr;
   double *d_S2 = nullptr, *d_H = nullptr, *d_Cl = nullptr, *d_Cout = nullptr, *d_lin = nullptr, *d_Lg = nullptr;
   int64_t* d_oL = nullptr;
   void *d_dR = nullptr, *d_W = nullptr, *d_P = nullptr, *d_r = nullptr, *d_RL = nullptr;
@@ -341,7 +341,6 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   AL(h->d_mppi, 8 * h->n_U);
   AL(h->d_delta, 8 * h->n_U);
   AL(h->d_y, 8 * h->n_U);
-  AL(h->d_wt, 8 * (h->n_C / 2));
   AL(h->d_e, 8 * (h->n_C / 2));
   AL(h->d_C, 8 * h->n_C);
   AL(h->d_A, 8 * h->n_nn);
@@ -575,7 +574,6 @@ static SolveArgs solve_args(gnmppi_t h, int shrink) {
   a.mppi = h->d_mppi;
   a.delta = h->d_delta;
   a.y = h->d_y;
-  a.wt = h->d_wt;
   a.C = h->d_C;
   a.e = h->d_e;
   a.W = h->d_W;

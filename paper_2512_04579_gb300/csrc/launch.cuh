@@ -1,7 +1,7 @@
 // launch.cuh -- host-side launch table of the model-templated rollout kernels.
 // Internal; one table per storage precision (rollout_{f64,f32,bf16}.cu).
 #pragma once
-#include "rollout.cuh"
+#include "rollout_group.cuh"
 
 namespace gnm {
 
@@ -50,6 +50,25 @@ void fill(Launchers* o) {
   o->cost64 = &launch_line<M64, double>;
 }
 
+// Line search and FP64 cost of a chain with a group of G lanes per candidate
+// rollout: one rollout per thread leaves a few warps per SM running a long
+// serial chain of RK4 steps; split over G lanes, each lane's chain is ~G times
+// shorter (same rows and costs, see k_line_group).
+template <typename T, int FL, int G>
+void launch_line_group(const RollArgs& a, int ncand_total, cudaStream_t s) {
+  const long lanes = (long)ncand_total * G;
+  if (lanes > 0) k_line_group<T, FL, G><<<(unsigned)((lanes + 255) / 256), 256, 0, s>>>(a);
+}
+template <typename T, typename S, int F>
+void fill_chain(Launchers* o) {
+  fill<Chain<T, F>, Chain<double, F>, T, S>(o);
+  if constexpr (F >= 5) {
+    constexpr int G = 4, FL = (F + G - 1) / G;
+    o->line = &launch_line_group<T, FL, G>;
+    o->cost64 = &launch_line_group<double, FL, G>;
+  }
+}
+
 #define GNM_DEFINE_LAUNCHERS(NAME, T, S)                                              \
   bool NAME(int dyn, int key, Launchers* o) {                                         \
     switch (dyn) {                                                                    \
@@ -87,7 +106,7 @@ void fill(Launchers* o) {
   }
 #define GNM_CHAIN_CASE(T, S, F) \
   case F:                       \
-    fill<Chain<T, F>, Chain<double, F>, T, S>(o); \
+    fill_chain<T, S, F>(o);     \
     return true;
 #define GNM_LIN_CASE(T, S, X, U) \
   case X * 16 + U:               \

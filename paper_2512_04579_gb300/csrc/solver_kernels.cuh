@@ -12,7 +12,7 @@
 //     the damped GGN step (J^T J + lambda I) delta = -J^T r for J = P S_used^-1;
 //   * k_update: argmin of the line search (Eq. 11), U += alpha* delta (Eq. 10),
 //     r <- R(U_{k+1}) and the covariance shrink Sigma <- beta Sigma.
-// Internal; instantiated once in solver.cu.
+// Internal; instantiated in api.cu.
 #pragma once
 #include "common.cuh"
 #include "chol.cuh"
@@ -29,7 +29,6 @@ struct SolveArgs {
   double* mppi;    // weighted mean perturbation [n]
   double* delta;   // [n]
   double* y;       // [n] scratch
-  double* wt;      // [Kp] softmin weight differences
   const double* C; // [Kp][2]
   const double* e; // [Kp]
   const void* W;   // [n][ldK] storage type
@@ -89,6 +88,17 @@ __device__ __forceinline__ double block_min(double v, double* red) {
 // pipe retires conversions at the DFMA rate).
 constexpr int kSoftminSplit = 4;  // CTAs per instance (each takes every 4th group of rows of W)
 
+// Four consecutive W entries as FP32 (16-byte FP32 or 8-byte BF16 load).
+__device__ __forceinline__ float4 load4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u), __uint_as_float(u.y << 16),
+                     __uint_as_float(u.y & 0xFFFF0000u));
+}
+__device__ __forceinline__ float4 load4(const double* p) {
+  return make_float4((float)p[0], (float)p[1], (float)p[2], (float)p[3]);
+}
+
 template <typename S, typename TA>
 __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
   constexpr int CH = 2048;  // samples staged per chunk
@@ -96,55 +106,84 @@ __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
   const InstDesc I = a.inst[b];
   if (a.st[b].status != 0) return;
   __shared__ double red[32];
-  __shared__ TA se[CH], sw[CH];
+  __shared__ __align__(16) TA se[CH];
+  __shared__ __align__(16) TA sw[CH];
   const bool anti = a.cs.antithetic != 0;
   const double* C = a.C + I.o_C;
   const double* e = a.e + I.o_C / 2;
-  double* wt = a.wt + I.o_C / 2;
-  // 1. minimum over the finite sample costs; pairs with a non-finite cost are dropped
+  // 1. minimum over the finite sample costs; pairs with a non-finite cost are
+  //    dropped.  Outside FP64 mode this runs on the integer pipe: finiteness
+  //    is a test of the exponent bits, and the costs are sums of squares
+  //    (>= 0), so the order of their bit patterns as signed integers is their
+  //    numeric order.
+  auto finite_bits = [](double c) {
+    return (__double_as_longlong(c) & 0x7FF0000000000000LL) != 0x7FF0000000000000LL;
+  };
   double cmin = INFINITY;
   int masked = 0;
-  for (int m = threadIdx.x; m < I.Kp; m += blockDim.x) {
-    const double c0 = C[anti ? 2 * m : m];
-    const double c1 = anti ? C[2 * m + 1] : c0;
-    const bool ok = isfinite(c0) && isfinite(c1);
-    if (ok) cmin = fmin(cmin, fmin(c0, c1));
-    masked += ok ? 0 : 1;
+  if constexpr (sizeof(TA) == 8) {
+    for (int m = threadIdx.x; m < I.Kp; m += blockDim.x) {
+      const double c0 = C[anti ? 2 * m : m];
+      const double c1 = anti ? C[2 * m + 1] : c0;
+      const bool ok = isfinite(c0) && isfinite(c1);
+      if (ok) cmin = fmin(cmin, fmin(c0, c1));
+      masked += ok ? 0 : 1;
+    }
+  } else {
+    long long mb = 0x7FF0000000000000LL;  // +inf
+    for (int m = threadIdx.x; m < I.Kp; m += blockDim.x) {
+      const double c0 = C[anti ? 2 * m : m];
+      const double c1 = anti ? C[2 * m + 1] : c0;
+      const bool ok = finite_bits(c0) && finite_bits(c1);
+      if (ok) mb = min(mb, min(__double_as_longlong(c0), __double_as_longlong(c1)));
+      masked += ok ? 0 : 1;
+    }
+    cmin = __longlong_as_double(mb);
   }
   cmin = block_min(cmin, red);
   const int nmask = (int)block_sum((double)masked, red);
-  // 2. weights exp(-(C - cmin)/tau) (Eq. 5), their sums, and w+ - w- per pair
+  // 2. weights exp(-(C - cmin)/tau) (Eq. 5), their sums, and w+ - w- per pair;
+  //    outside FP64 mode from the exact FP64 difference rounded once to FP32,
+  //    with per-thread FP32 sums (a few terms each) reduced in FP64
   const double itau = 1.0 / a.cs.tau;
-  auto weights = [&](int m, double& w0, double& w1) {
+  const float itau_f = (float)itau;
+  const bool cmin_ok = isfinite(cmin);
+  auto weights = [&](int m, TA& w0, TA& w1) {
     const double c0 = C[anti ? 2 * m : m];
     const double c1 = anti ? C[2 * m + 1] : c0;
-    const bool ok = isfinite(c0) && isfinite(c1) && isfinite(cmin);
     if constexpr (sizeof(TA) == 8) {
+      const bool ok = isfinite(c0) && isfinite(c1) && cmin_ok;
       w0 = ok ? exp(-(c0 - cmin) * itau) : 0.0;
       w1 = (ok && anti) ? exp(-(c1 - cmin) * itau) : 0.0;
     } else {
-      w0 = ok ? (double)expf((float)(-(c0 - cmin) * itau)) : 0.0;
-      w1 = (ok && anti) ? (double)expf((float)(-(c1 - cmin) * itau)) : 0.0;
+      const bool ok = finite_bits(c0) && finite_bits(c1) && cmin_ok;
+      w0 = ok ? expf(-(float)(c0 - cmin) * itau_f) : 0.f;
+      w1 = (ok && anti) ? expf(-(float)(c1 - cmin) * itau_f) : 0.f;
     }
   };
-  double s1 = 0.0, s2 = 0.0;
+  TA s1t = (TA)0, s2t = (TA)0;
   const bool one_chunk = I.Kp <= CH;  // then the sums pass stages the chunk as well
   for (int m = threadIdx.x; m < I.Kp; m += blockDim.x) {
-    double w0, w1;
+    TA w0, w1;
     weights(m, w0, w1);
-    s1 += w0 + w1;
-    s2 += w0 * w0 + w1 * w1;
-    if (part == 0) wt[m] = w0 - w1;
+    s1t += w0 + w1;
+    s2t += w0 * w0 + w1 * w1;
     if (one_chunk) {
       se[m] = (TA)e[m];
-      sw[m] = (TA)(w0 - w1);
+      sw[m] = w0 - w1;
     }
   }
-  s1 = block_sum(s1, red);
-  s2 = block_sum(s2, red);
+  const double s1 = block_sum((double)s1t, red);
+  const double s2 = block_sum((double)s2t, red);
+  // zero the staged tail up to a multiple of 4 (the vector row loop reads it
+  // against W's zero padding columns)
+  if (one_chunk && threadIdx.x < 4 && I.Kp + (int)threadIdx.x < ((I.Kp + 3) & ~3)) {
+    se[I.Kp + threadIdx.x] = (TA)0;
+    sw[I.Kp + threadIdx.x] = (TA)0;
+  }
   // 3. rows of W (this CTA's share): b_j = sum_m W[j][m] e_m,
-  //    mppi_j = sum_m W[j][m] wt_m / sum w; every CTA forms its own staged
-  //    copy of the weight differences (CTA 0's global copy may not be written yet)
+  //    mppi_j = sum_m W[j][m] (w+ - w-)_m / sum w; every CTA stages its own
+  //    copy of e and the weight differences
   const S* W = reinterpret_cast<const S*>(a.W) + I.o_W;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int m0 = 0; m0 < I.Kp; m0 += CH) {
@@ -152,23 +191,41 @@ __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
     if (!one_chunk) {
       __syncthreads();  // previous chunk consumed
       for (int m = threadIdx.x; m < mc; m += blockDim.x) {
-        double w0, w1;
+        TA w0, w1;
         weights(m0 + m, w0, w1);
         se[m] = (TA)e[m0 + m];
-        sw[m] = (TA)(w0 - w1);
+        sw[m] = w0 - w1;
+      }
+      if (threadIdx.x < 4 && mc + (int)threadIdx.x < ((mc + 3) & ~3)) {
+        se[mc + threadIdx.x] = (TA)0;
+        sw[mc + threadIdx.x] = (TA)0;
       }
     }
     __syncthreads();
     for (int j = part * nw + warp; j < I.n; j += kSoftminSplit * nw) {
       const S* row = W + (int64_t)j * I.ldK + m0;
       TA ag = (TA)0, am = (TA)0;
+      if constexpr (sizeof(TA) == 8) {
 #pragma unroll 8
-      for (int m = lane; m < mc; m += 32) {
-        TA w;
-        if constexpr (sizeof(TA) == 8) w = to_d(row[m]);
-        else w = to_f(row[m]);
-        ag += w * se[m];
-        am += w * sw[m];
+        for (int m = lane; m < mc; m += 32) {
+          const TA w = to_d(row[m]);
+          ag += w * se[m];
+          am += w * sw[m];
+        }
+      } else {
+        // four samples per lane and load (16 B of FP32 or 8 B of BF16 W), so
+        // a row of 1024 samples is one batch of 8 independent loads per lane;
+        // rows start 16-byte aligned (ldK and m0 are multiples of 64)
+        const int m4 = (mc + 3) >> 2;
+        const float4* se4 = reinterpret_cast<const float4*>(se);
+        const float4* sw4 = reinterpret_cast<const float4*>(sw);
+#pragma unroll 8
+        for (int q = lane; q < m4; q += 32) {
+          const float4 w = load4(row + 4 * q);
+          const float4 ev = se4[q], wv = sw4[q];
+          ag += w.x * ev.x + w.y * ev.y + w.z * ev.z + w.w * ev.w;
+          am += w.x * wv.x + w.y * wv.y + w.z * wv.z + w.w * wv.w;
+        }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
