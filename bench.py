@@ -203,6 +203,22 @@ def dist_env():
         os.environ.get("LOCAL_RANK", "0"))
 
 
+def reduce_over_ranks(ms, solved, world, device):
+    """Replicas: every rank solves its own copy of the batch.  The job's time
+    is the slowest rank's (max over ranks) and its work the instances solved
+    on all ranks (sum); returns both, unchanged for one rank."""
+    if world <= 1:
+        return ms, solved
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([float(solved)], dtype=torch.float64, device=device)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(s.item()))
+
+
 class Clocks:
     """nvidia-smi sampler for SM clocks and throttle reasons during the timed region."""
 
@@ -317,10 +333,6 @@ def run_gnmppi(args):
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     launches = G.gnmppi_launch_count(h) - launches0
     # per-kernel CUDA-event times of one more iteration on the solve's final
     # state (before gnmppi_cost, which reloads the inputs and resets the state)
@@ -330,9 +342,11 @@ def run_gnmppi(args):
     G.gnmppi_cost(h, G.MEM_DEVICE, d_x0, d_tgt, d_U, Cfin)
     Cfin = Cfin.cpu().numpy()
     gap = (Cfin - Cstar) / Cstar
-    solved = int(np.sum(gap <= GAP))
+    solved_rank = int(np.sum(gap <= GAP))
+    ms, solved_all = reduce_over_ranks(ms, solved_rank, world, dev)
+    solved = solved_all // world  # per replica, for the solved fraction
     ms_step = ms / args.steps
-    value = world * solved / (ms_step / 1e3)
+    value = solved_all / (ms_step / 1e3)
 
     F = M - 1
     roll_flops = batch * (K) * (N * chain_flops_per_step(F))  # K rollouts of N steps each
@@ -365,8 +379,8 @@ def run_gnmppi(args):
     Ce = np.zeros(batch)
     G.gnmppi_cost(he, G.MEM_HOST, hx0.numpy(), htg.numpy(), hU.numpy(), Ce)
     G.gnmppi_destroy(he)
-    e2e_solved = int(np.sum((Ce - Cstar) / Cstar <= GAP))
-    e2e = {"value": world * e2e_solved / e2e_s, "unit": "solves/s",
+    e2e_s, e2e_solved = reduce_over_ranks(e2e_s, int(np.sum((Ce - Cstar) / Cstar <= GAP)), world, dev)
+    e2e = {"value": e2e_solved / e2e_s, "unit": "solves/s",
            "h2d_bytes_per_step": int(8 * (x0.size + tgt.size + batch * N * 2)),
            "d2h_bytes_per_step": int(8 * batch * N * 2)}
 
