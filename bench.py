@@ -457,11 +457,14 @@ def cpu_baseline(args):
     cores = os.cpu_count() or 1
     iters = max(1, args.cpu_iters)
     t_it = oracle_iteration_seconds(cores, iters)
+    t_1 = oracle_iteration_seconds(1, 1)  # the same on one thread, one iteration
     _, C_gn, Cs = load_cstar()
     frac = float(np.mean((C_gn - Cs) / Cs <= GAP))
     return {"value": frac / (t_it * T), "unit": "solves/s", "cores": cores, "kind": "oracle",
             "sample": f"1 instance, {iters} of {T} iterations, {cores} OpenMP threads over samples; "
-                      f"scaled by T and by the oracle's own solved fraction {frac:.3f}"}
+                      f"scaled by T and by the oracle's own solved fraction {frac:.3f}",
+            "one_thread": {"value": frac / (t_1 * T), "unit": "solves/s", "cores": 1,
+                           "sample": f"1 instance, 1 of {T} iterations, one thread"}}
 
 
 def run_reference(args):
