@@ -373,10 +373,10 @@ struct Chain<float, F> {
       const float q = fmaf(d.x, d.x, d.y * d.y);
       const float rinv = rsqrtf(q);
       const float dd = fmaf(q, rinv, -l0);
-      const float fr = fmaf(k3m * dd, dd, km) * dd * rinv;  // (k d + k3 d^3) / (m |d|)
-      const float2 f = __fmul2_rn(make_float2(fr, fr), d);
-      acc[i] = __ffma2_rn(f, mneg1, acc[i]);
-      if (i > 0) acc[i - 1] = __fadd2_rn(acc[i - 1], f);
+      const float t = fmaf(k3m * dd, dd, km) * dd;
+      const float fr = t * rinv;  // (k d + k3 d^3) / (m |d|): the link pulls mass i back, mass i-1 on
+      acc[i] = __ffma2_rn(make_float2(-fr, -fr), d, acc[i]);
+      if (i > 0) acc[i - 1] = __ffma2_rn(make_float2(fr, fr), d, acc[i - 1]);
     }
   }
   __device__ __forceinline__ void step(float* xs, const float* u) const {

@@ -173,26 +173,31 @@ struct ChainGroup<float, FL, G> {
     prev.x = __shfl_up_sync(mask, p[FL - 1].x, 1, G);
     prev.y = __shfl_up_sync(mask, p[FL - 1].y, 1, G);
     if (lg == 0) prev = make_float2(0.f, 0.f);
-    float2 f[FL];
+    // link j of this lane ends at its mass j: d_j and fr_j with the force
+    // fr_j d_j pulling mass j back and the mass before it on
+    float2 d[FL];
+    float fr[FL];
 #pragma unroll
     for (int j = 0; j < FL; ++j) {
-      const float2 d = __ffma2_rn((j == 0) ? prev : p[j - 1], mneg1, p[j]);
+      d[j] = __ffma2_rn((j == 0) ? prev : p[j - 1], mneg1, p[j]);
       const bool real = mass(j) <= F;
-      const float q = real ? fmaf(d.x, d.x, d.y * d.y) : 1.f;
+      const float q = real ? fmaf(d[j].x, d[j].x, d[j].y * d[j].y) : 1.f;
       const float rinv = rsqrtf(q);
       const float dd = fmaf(q, rinv, -l0);
-      const float fr = real ? fmaf(k3m * dd, dd, km) * dd * rinv : 0.f;
-      f[j] = __fmul2_rn(make_float2(fr, fr), d);
+      fr[j] = real ? fmaf(k3m * dd, dd, km) * dd * rinv : 0.f;
     }
-    float2 fn;
-    fn.x = __shfl_down_sync(mask, f[0].x, 1, G);
-    fn.y = __shfl_down_sync(mask, f[0].y, 1, G);
-    if (lg == G - 1) fn = make_float2(0.f, 0.f);
+    // the next lane's first link (the one after this lane's last mass)
+    float2 dn;
+    dn.x = __shfl_down_sync(mask, d[0].x, 1, G);
+    dn.y = __shfl_down_sync(mask, d[0].y, 1, G);
+    float frn = __shfl_down_sync(mask, fr[0], 1, G);
+    if (lg == G - 1) frn = 0.f;
 #pragma unroll
     for (int j = 0; j < FL; ++j) {
       float2 a = __ffma2_rn(v[j], cneg, grav);
-      a = __ffma2_rn(f[j], mneg1, a);
-      a = __fadd2_rn(a, (j + 1 < FL) ? f[j + 1] : fn);
+      a = __ffma2_rn(make_float2(-fr[j], -fr[j]), d[j], a);
+      const float fo = (j + 1 < FL) ? fr[j + 1] : frn;
+      a = __ffma2_rn(make_float2(fo, fo), (j + 1 < FL) ? d[j + 1] : dn, a);
       if (mass(j) == F) a = __fadd2_rn(a, um);
       acc[j] = (mass(j) <= F) ? a : make_float2(0.f, 0.f);
     }
