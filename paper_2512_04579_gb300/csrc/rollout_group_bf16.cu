@@ -12,17 +12,12 @@ template <typename T, typename S, int FL, int G>
 void samp(const RollArgs& a, int nb, int smem, cudaStream_t s) {
   k_samples_group<T, S, FL, G><<<nb, 256, smem, s>>>(a);
 }
-template <typename T, int FL, int G>
-void line(const RollArgs& a, int ncand_total, cudaStream_t s) {
-  const long lanes = (long)ncand_total * G;
-  if (lanes > 0) k_line_group<T, FL, G><<<(unsigned)((lanes + 255) / 256), 256, 0, s>>>(a);
-}
 template <typename T, typename S, int FL, int G>
 void fill_group(Launchers* o) {
   o->prepare = &prep<T, S, FL, G>;
   o->samples = &samp<T, S, FL, G>;
-  o->line = &line<T, FL, G>;
-  o->cost64 = &line<double, FL, G>;
+  o->line = &launch_line_group<T, FL, G>;
+  o->cost64 = &launch_line_group<double, FL, G>;
   o->pairs_per_block = 256 / (2 * G);
   o->antithetic_only = 1;
   o->slots = G * FL;
