@@ -39,7 +39,7 @@ WORKLOAD = "chain M=10 N=100 nu=2 K=2048 T=30 sigma0=0.2 lambda=1e-3"
 
 # DRAM read + write of one k_samples launch of the default workload (256 instances), from one
 # full-size ncu capture of this command (one-pass metrics); null for other batch sizes.
-K_SAMPLES_TRAFFIC_B256 = 2.2794e9
+K_SAMPLES_TRAFFIC_B256 = 2.2790e9
 
 
 def load_cstar(path=CSTAR):
