@@ -244,19 +244,21 @@ const char* gnmppi_phase_name(int32_t i);
  * launch configurations and keeps the fastest:
  *   - branches: how many concurrent CUDA-graph branches carry the per-size
  *     rollout groups (sample rollouts and line search), 1, 2, 4 or 8;
- *   - solve_nt: threads per Cholesky CTA, 256 (two per SM) or 128 (four).
+ *   - solve_nt: threads per Cholesky CTA, 512 (one per SM), 256 (two) or 128
+ *     (four); without tuning 512 when the batch fits one instance per SM, else 256.
  * reps: timed repetitions per candidate (<= 0: 3), after one warm-up.  The
  * choice is cached for the process under a signature of the device, the
  * model, the precision and the multiset of instance shapes; when the
  * environment variable GNMPPI_TUNE_FILE names a file, cached choices are read
  * from it and new ones appended ("signature branches solve_nt" lines).  A
- * cached choice is applied without timing.  Results do not depend on the
- * configuration (the arithmetic of every kernel is unchanged).  The next
+ * cached choice is applied without timing.  The iterates do not depend on the
+ * configuration (the arithmetic of every kernel is unchanged); only the
+ * reported norms |b| and |delta|, block-wide sums, may round differently.  The next
  * gnmppi_solve recaptures its CUDA graph.  Errors: as gnmppi_solve. */
 gnmppi_status gnmppi_autotune(gnmppi_t h, int32_t mem, const double* x0, const double* xref, const double* U,
                               const double* sigma, int32_t reps);
 
-/* Set the launch configuration by hand (branches 1..8, solve_nt 128 or 256).
+/* Set the launch configuration by hand (branches 1..8, solve_nt 128, 256 or 512).
  * Errors: E_ARG for values out of range. */
 gnmppi_status gnmppi_tune_set(gnmppi_t h, int32_t branches, int32_t solve_nt);
 

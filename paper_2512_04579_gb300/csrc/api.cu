@@ -41,7 +41,7 @@ constexpr int kMaxBranches = 8;
 // Launch configuration picked by the autotuner (or the defaults).
 struct TuneCfg {
   int branches = 1;   // concurrent graph branches for the per-size rollout groups
-  int solve_nt = 256; // threads per k_solve CTA (256: two CTAs per SM, 128: four)
+  int solve_nt = 256; // threads per k_solve CTA (512: one CTA per SM, 256: two, 128: four)
 };
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -454,8 +454,8 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     for (void* q : h->tc.allocs) h->allocs.push_back(q);
     if (st != GNMPPI_OK) return st;
   }
-  // the Cholesky kernel: vectors only in shared memory, two (256 threads) or
-  // four (128 threads) CTAs per SM, the rest of the carveout left to L1 (which
+  // the Cholesky kernel: vectors only in shared memory, one (512 threads), two
+  // (256) or four (128) CTAs per SM, the rest of the carveout left to L1 (which
   // caches the factor's panels)
   {
     int dev = 0, optin = 0, smsm = 0;
@@ -465,20 +465,32 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     if (h->solve_smem + 1024 > optin) return fail(h, GNMPPI_E_ARG, "N*nu too large for the solver");
     const int pct2 = std::min(100, (int)(100.0 * 2 * (h->solve_smem + 2048) / std::max(1, smsm)) + 5);
     const int pct4 = std::min(100, (int)(100.0 * 4 * (h->solve_smem + 2048) / std::max(1, smsm)) + 5);
+    const int pct1 = std::min(100, (int)(100.0 * (h->solve_smem + 2048) / std::max(1, smsm)) + 5);
     if (prec == kFP64) {
+      CK(cudaFuncSetAttribute(k_solve<double, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
+      CK(cudaFuncSetAttribute(k_solve<double, 512>, cudaFuncAttributePreferredSharedMemoryCarveout, pct1));
       CK(cudaFuncSetAttribute(k_solve<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
       CK(cudaFuncSetAttribute(k_solve<double, 256>, cudaFuncAttributePreferredSharedMemoryCarveout, pct2));
       CK(cudaFuncSetAttribute(k_solve<double, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
       CK(cudaFuncSetAttribute(k_solve<double, 128>, cudaFuncAttributePreferredSharedMemoryCarveout, pct4));
     } else {
+      CK(cudaFuncSetAttribute(k_solve<float, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
+      CK(cudaFuncSetAttribute(k_solve<float, 512>, cudaFuncAttributePreferredSharedMemoryCarveout, pct1));
       CK(cudaFuncSetAttribute(k_solve<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
       CK(cudaFuncSetAttribute(k_solve<float, 256>, cudaFuncAttributePreferredSharedMemoryCarveout, pct2));
       CK(cudaFuncSetAttribute(k_solve<float, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->solve_smem));
       CK(cudaFuncSetAttribute(k_solve<float, 128>, cudaFuncAttributePreferredSharedMemoryCarveout, pct4));
     }
   }
-  // default launch configuration (the autotuner may replace it)
-  h->tune.solve_nt = 256;
+  // default launch configuration (the autotuner may replace it): a batch no
+  // larger than the SM count gets one SM per instance, and then 16 warps per
+  // Cholesky shorten its serial steps; larger batches pair instances per SM
+  {
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    h->tune.solve_nt = h->batch <= nsm ? 512 : 256;
+  }
   set_branches(h, std::min<int>(4, (int)h->groups.size()));
   CK(cudaStreamSynchronize(h->stream));
   return GNMPPI_OK;
@@ -715,6 +727,7 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
   if (ON(5)) {
     if (!gn) k_mppi_step<<<h->batch, 256, 0, h->stream>>>(sa);
     else if (h->tune.solve_nt == 128) k_solve<TA, 128><<<h->batch, 128, h->solve_smem, h->stream>>>(sa);
+    else if (h->tune.solve_nt == 512) k_solve<TA, 512><<<h->batch, 512, h->solve_smem, h->stream>>>(sa);
     else k_solve<TA, 256><<<h->batch, 256, h->solve_smem, h->stream>>>(sa);
     CKL();
     h->launches++;
@@ -1142,7 +1155,8 @@ static gnmppi_status time_phases(gnmppi_t h, unsigned mask, int reps, double* be
 extern "C" gnmppi_status gnmppi_tune_set(gnmppi_t h, int32_t branches, int32_t solve_nt) {
   if (!h) return GNMPPI_E_ARG;
   if (branches < 1 || branches > kMaxBranches) return fail(h, GNMPPI_E_ARG, "branches must be in 1..%d", kMaxBranches);
-  if (solve_nt != 128 && solve_nt != 256) return fail(h, GNMPPI_E_ARG, "solve_nt must be 128 or 256");
+  if (solve_nt != 128 && solve_nt != 256 && solve_nt != 512)
+    return fail(h, GNMPPI_E_ARG, "solve_nt must be 128, 256 or 512");
   set_branches(h, branches);
   h->tune.solve_nt = solve_nt;
   drop_graph(h);
@@ -1207,7 +1221,7 @@ extern "C" gnmppi_status gnmppi_autotune(gnmppi_t h, int32_t mem, const double* 
   int best_nt = 256;
   {
     double best = 1e300;
-    for (int nt : {256, 128}) {
+    for (int nt : {256, 128, 512}) {
       h->tune.solve_nt = nt;
       double ms = 0.0;
       st = time_phases(h, 1u << 5, reps, &ms);

@@ -153,6 +153,9 @@ class LearnedSolver:
         self.mlp, self.batch, self.tol = mlp, batch, tol
         self.h_warm = G.gnmppi_create(chain_problem(K, T, precision), batch, None, stream)
         self.h_plain = G.gnmppi_create(chain_problem(K_plain, T_plain, precision), batch, None, stream)
+        # the fallback runs the few instances the warm start left unconverged
+        # (the others are masked off): one SM and 16 warps per Cholesky
+        G.gnmppi_tune_set(self.h_plain, 1, 512)
         torch = _torch()
         self.U0 = torch.zeros(batch * NMU, dtype=torch.float64, device="cuda")
         self.sig = torch.zeros(batch * NMU, dtype=torch.float64, device="cuda")

@@ -44,7 +44,7 @@ def test_launch_configuration_does_not_change_the_solve():
     try:
         assert G.gnmppi_tune_report(h)["source"] == "default"
         ref_U, ref_C = None, None
-        for cfg in [(1, 256), (4, 128), (8, 256), (2, 128)]:
+        for cfg in [(1, 256), (4, 128), (8, 256), (2, 128), (2, 512)]:
             G.gnmppi_tune_set(h, *cfg)
             rep = G.gnmppi_tune_report(h)
             assert rep["source"] == "set" and (rep["branches"], rep["solve_nt"]) == cfg
@@ -56,7 +56,7 @@ def test_launch_configuration_does_not_change_the_solve():
                 assert C == ref_C
         rep = G.gnmppi_autotune(h, G.MEM_HOST, x0, xr, np.zeros(nU))
         assert rep["source"] == "timed"
-        assert rep["branches"] in (1, 2, 4, 8) and rep["solve_nt"] in (128, 256)
+        assert rep["branches"] in (1, 2, 4, 8) and rep["solve_nt"] in (128, 256, 512)
         timed = [c for c in rep["candidates"] if "branches" in c]
         assert [c["branches"] for c in timed][:2] == [1, 2] and all(c["ms"] > 0 for c in rep["candidates"])
         U, C = solve(h, x0, xr, nU, batch)
@@ -78,7 +78,7 @@ def test_launch_configuration_does_not_change_the_solve():
 def test_tune_set_rejects_values_out_of_range():
     h, *_ = uneven_handle(I.BASE_SEED + 78, 4, iterations=1)
     try:
-        for cfg in [(0, 256), (9, 256), (2, 64), (2, 512)]:
+        for cfg in [(0, 256), (9, 256), (2, 64), (2, 1024)]:
             with pytest.raises(G.GnmppiError):
                 G.gnmppi_tune_set(h, *cfg)
     finally:
