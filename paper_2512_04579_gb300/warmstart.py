@@ -146,13 +146,17 @@ def load(path=WEIGHTS, bf16=True, max_batch=4096, stream=None):
 
 class LearnedSolver:
     """Warm-started GN-MPPI with plain GN-MPPI as the fallback, for a batch of
-    instances of one size (device-resident inputs)."""
+    instances of one size (device-resident inputs).  An instance whose last
+    warm-started iteration still lowered its cost by more than `tol`
+    (relative), or whose cost is not finite, continues from the warm-started
+    controls with the plain settings for the rest of the plain iteration
+    budget (T_plain - T iterations)."""
 
     def __init__(self, mlp, batch, K=512, T=5, K_plain=2048, T_plain=30, tol=1e-6, precision=G.PREC_FP32,
                  stream=None):
         self.mlp, self.batch, self.tol = mlp, batch, tol
         self.h_warm = G.gnmppi_create(chain_problem(K, T, precision), batch, None, stream)
-        self.h_plain = G.gnmppi_create(chain_problem(K_plain, T_plain, precision), batch, None, stream)
+        self.h_plain = G.gnmppi_create(chain_problem(K_plain, max(1, T_plain - T), precision), batch, None, stream)
         # the fallback runs the few instances the warm start left unconverged
         # (the others are masked off): one SM and 16 warps per Cholesky
         G.gnmppi_tune_set(self.h_plain, 1, 512)
