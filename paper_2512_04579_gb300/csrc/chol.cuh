@@ -1,5 +1,5 @@
 // chol.cuh -- FP64 Cholesky factorisation and triangular solves of one n x n
-// symmetric positive definite system per CTA of 256 threads (8 warps), for
+// symmetric positive definite system per CTA of 128, 256 or 512 threads, for
 // the damped Gauss-Newton step of GN-MPPI (arXiv 2512.04579, Sec. 4, the
 // normal equations of Eq. 9 with damping).
 //
@@ -7,8 +7,8 @@
 // per 64 cycles whatever its active lanes, and the SM retires one FP64 warp
 // instruction per 19 cycles once four or more warps feed it.  So the work is
 // kept on full warps, serial chains are short, and the latency-bound
-// diagonal-block step runs on one warp while the other seven carry the
-// trailing update (look-ahead by one panel).
+// diagonal-block step runs on one warp while the others carry the trailing
+// update (look-ahead by one panel).
 //
 // Storage: the lower factor is packed by rows in global memory (element
 // (i, j), j <= i, at i (i + 1) / 2 + j) and stays L2/L1 resident; the inverse
@@ -81,7 +81,7 @@ __device__ __noinline__ bool diag_factor(double* L, double* invd, double* Yp, in
 
 // Panel rows below the diagonal block at p0: L21 = A21 L11^-T, i.e.
 // v_c = sum_{q <= c} a_q Y[c][q] with Y = L11^-1.  Called by every thread of
-// the CTA (4 or 8 warps).  Short panels split each row's 16 outputs over R = 2
+// the CTA (4, 8 or 16 warps).  Short panels split each row's 16 outputs over R = 2
 // or 4 warps (a warp-uniform residue class of c) so that their FP64 work
 // still reaches all four sub-partitions of the SM.
 __device__ __forceinline__ void panel_rows(double* L, const double* Yp, int n, int p0, int nb) {
@@ -199,7 +199,7 @@ __device__ __forceinline__ void trailing_update(double* L, int n, int p0, int nb
 // block (and inverts it) while the other warps reduce the rest of the
 // trailing matrix.  invd[i] = 1 / L[i][i]; Y holds the inverted diagonal
 // blocks (CNB2 doubles per panel).  Returns false, uniformly over the CTA, on
-// a pivot that is not positive and finite.  128 or 256 threads.
+// a pivot that is not positive and finite.  128, 256 or 512 threads.
 __device__ bool chol_factor(double* L, double* invd, double* Y, int n, int* fail) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int np = (n + CNB - 1) / CNB;

@@ -3,8 +3,8 @@
 // G * FL).  Lane l of a group owns masses l*FL + 1 .. l*FL + FL (1-based;
 // masses beyond F are inert placeholders with zero state).  Per right-hand
 // side evaluation a lane needs the position of the mass just before its first
-// one (one shuffle up) and the force of the link just after its last one (one
-// shuffle down); shuffles are width-G so groups never mix.  The two rollouts
+// one (shuffle up) and the link just after its last one (its vector and force
+// scale, shuffle down); shuffles are width-G so groups never mix.  The two rollouts
 // of an antithetic pair are two adjacent groups (partner lane = lane ^ G).
 // Same outputs as k_samples / k_line (rollout.cuh): dR, W, sample costs and
 // e = dR . r; line-search residuals and costs.
