@@ -51,6 +51,7 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 struct gnmppi_s {
   gnmppi_problem p{};
   int batch = 0;
+  int nmax = 0;  // largest horizon N of the instances
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<InstDesc> desc;
@@ -308,6 +309,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     d.o_R = orr; orr += d.nR;
     d.o_RL = orl; orl += (int64_t)p.L * d.nR;
     h->desc[b] = d;
+    h->nmax = std::max(h->nmax, d.N);
   }
   // k_solve keeps rhs, x, res, 1/diag and the float split of y (5 n doubles)
   // in shared memory; the packed factor plus the inverted diagonal blocks,
@@ -572,6 +574,7 @@ static RollArgs roll_args(gnmppi_t h, uint32_t it) {
   a.Cl = h->d_Cl;
   a.Cout = h->d_Cout;
   a.it = it;
+  a.nmax = h->nmax;
   return a;
 }
 

@@ -59,7 +59,14 @@ void fill(Launchers* o) {
 template <typename T, int FL, int G>
 void launch_line_group(const RollArgs& a, int ncand_total, cudaStream_t s) {
   const long lanes = (long)ncand_total * G;
-  if (lanes > 0) k_line_group<T, FL, G><<<(unsigned)((lanes + 255) / 256), 256, 0, s>>>(a);
+  if (lanes <= 0) return;
+  // FP32 candidates stage their controls U + alpha delta (formed in FP64,
+  // lane-parallel over the steps) in shared memory when they fit the default
+  // 48 KB; longer horizons form them per step
+  RollArgs b = a;
+  const size_t smem = (size_t)(256 / G) * (size_t)a.nmax * sizeof(float2);
+  b.pre = (sizeof(T) == 4 && a.mode != 2 && smem <= 48 * 1024) ? 1 : 0;
+  k_line_group<T, FL, G><<<(unsigned)((lanes + 255) / 256), 256, b.pre ? smem : 0, s>>>(b);
 }
 template <typename T, typename S, int F>
 void fill_chain(Launchers* o) {

@@ -39,6 +39,9 @@ struct RollArgs {
   int ncand;          // candidates per instance (line search)
   uint32_t it;        // iteration index of the noise stream
   int mode;           // k_line: 0 line search, 1 nominal, 2 FP64 cost only
+  int nmax;           // largest horizon N of the handle's instances
+  int pre;            // k_line_group: controls staged in dynamic shared memory
+                      // (candidates of the CTA x nmax float2), else formed per step
 };
 
 // Models that read a per-instance reference (the chain's target positions)

@@ -477,12 +477,32 @@ __global__ void __launch_bounds__(256) k_line_group(RollArgs a) {
   const double* U = a.U + I.o_U;
   const double* D = a.delta + I.o_U;
   const int rps = 2 * I.F + 2;
+  // Staged controls (FP32 candidates): the group's lanes form U + alpha delta
+  // for steps lg, lg + G, ... in FP64 once, so the FP64 work of a warp
+  // instruction covers G steps instead of one (GB300's FP64 pipe issues one
+  // instruction per warp per 64 cycles whatever the active lanes).
+  extern __shared__ __align__(16) unsigned char line_smem[];
+  float2* su = reinterpret_cast<float2*>(line_smem) + (int64_t)(threadIdx.x / G) * a.nmax;
+  if (a.pre) {
+    for (int k = lg; k < I.N; k += G) {
+      const double v0 = (a.mode == 0) ? U[2 * k] + alpha * D[2 * k] : U[2 * k];
+      const double v1 = (a.mode == 0) ? U[2 * k + 1] + alpha * D[2 * k + 1] : U[2 * k + 1];
+      su[k] = make_float2((float)v0, (float)v1);
+    }
+    __syncwarp(gmask);
+  }
   for (int k = 0; k < I.N; ++k) {
     T u[2];
+    if (a.pre) {
+      const float2 v = su[k];
+      u[0] = (T)v.x;
+      u[1] = (T)v.y;
+    } else {
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int q = 2 * k + c;
-      u[c] = (a.mode == 0) ? (T)(U[q] + alpha * D[q]) : (T)U[q];
+      for (int c = 0; c < 2; ++c) {
+        const int q = 2 * k + c;
+        u[c] = (a.mode == 0) ? (T)(U[q] + alpha * D[q]) : (T)U[q];
+      }
     }
     em.base = k * rps;
     em.csum = (T)0;

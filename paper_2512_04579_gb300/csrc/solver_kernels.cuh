@@ -178,6 +178,10 @@ __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
   }
   const double s1 = block_sum((double)s1t, red);
   const double s2 = block_sum((double)s2t, red);
+  // the MPPI direction is normalised by one reciprocal (a FP64 division is a
+  // multi-instruction sequence on GB300's slow FP64 pipe; one per row cost
+  // more than the rest of the kernel's FP64 work)
+  const double inv_s1 = s1 > 0.0 ? 1.0 / s1 : 0.0;
   // zero the staged tail up to a multiple of 4 (the vector row loop reads it
   // against W's zero padding columns)
   if (one_chunk && threadIdx.x < 4 && I.Kp + (int)threadIdx.x < ((I.Kp + 3) & ~3)) {
@@ -236,7 +240,10 @@ __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
         am += __shfl_xor_sync(0xffffffffu, am, o);
       }
       if (lane == 0) {
-        if (m0 == 0) {
+        if (one_chunk) {
+          a.g[I.o_U + j] = (double)ag;
+          a.mppi[I.o_U + j] = (double)am * inv_s1;
+        } else if (m0 == 0) {
           a.g[I.o_U + j] = (double)ag;
           a.mppi[I.o_U + j] = (double)am;
         } else {
@@ -246,8 +253,9 @@ __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
       }
     }
   }
-  for (int j = part * nw + warp; j < I.n; j += kSoftminSplit * nw)
-    if (lane == 0) a.mppi[I.o_U + j] = s1 > 0.0 ? a.mppi[I.o_U + j] / s1 : 0.0;
+  if (!one_chunk)
+    for (int j = part * nw + warp; j < I.n; j += kSoftminSplit * nw)
+      if (lane == 0) a.mppi[I.o_U + j] *= inv_s1;
   if (part == 0 && threadIdx.x == 0) {  // |b| is taken by the step kernels, which read all of b
     InstState& s = a.st[b];
     s.c_min = cmin;
