@@ -167,9 +167,6 @@ __device__ __forceinline__ double to_store<double>(double x) { return x; }
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(float x) { return (double)x; }
 __device__ __forceinline__ double to_d(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
-__device__ __forceinline__ float to_f(float x) { return x; }
-__device__ __forceinline__ float to_f(double x) { return (float)x; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 // ------------------------------------------------------------------------
 // Models.  Each provides NX, NU, RPS (rows per stage), RT (terminal rows),
