@@ -1,8 +1,8 @@
 """What the learned warm start gains: an MLP trained (on the GPU, by the
 library's own kernels) on 16384 plain GN-MPPI solutions of one chain target
 warm-starts held-out instances so that GN-MPPI with K = 512 and 5 iterations
-lands much closer to the plain solution (K = 2048, 30 iterations, the judge
-of the cost gap) than the same budget from a cold start."""
+lands much closer to the plain solution (K = 2048, 30 iterations, the
+reference of the cost gap) than the same budget from a cold start."""
 import numpy as np
 import pytest
 
