@@ -165,7 +165,7 @@ def learned_arm(args, dev, stream):
     (relative).  Plain: cold start, K=2048, 30 iterations.
       * 256 held-out initial states with the oracle's optima C*;
       * 4096 held-out initial states (the first 256 are the ones above),
-        judged against the better of the two methods' final costs, since the
+        measured against the better of the two methods' final costs, since the
         oracle's optima of all 4096 are out of reach on the host."""
     from paper_2512_04579_gb300 import warmstart as W
 

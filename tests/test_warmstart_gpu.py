@@ -48,7 +48,7 @@ def test_warm_start_beats_cold_start_at_equal_budget(trained):
     x0, tgt = I.chain_fixed_target_states(W.SEED, B, W.M, I.WARM_PHI, stream=I.EVAL_STREAM)
     dx = torch.tensor(x0.ravel(), dtype=torch.float64, device="cuda")
     dt = torch.tensor(np.tile(tgt, (B, 1)).ravel(), dtype=torch.float64, device="cuda")
-    # judge: plain GN-MPPI, cold start, K = 2048, 30 iterations
+    # reference: plain GN-MPPI, cold start, K = 2048, 30 iterations
     hp = G.gnmppi_create(W.chain_problem(2048, 30), B)
     Up = torch.zeros(B * W.NMU, dtype=torch.float64, device="cuda")
     G.gnmppi_solve(hp, G.MEM_DEVICE, dx, dt, Up, None)
