@@ -562,7 +562,8 @@ int32_t orc_iteration(const orc_model* m, const orc_options* o, const double* x0
     /* J = P S^-1, i.e. S J^T = P^T: one Cholesky solve per row of P */
     double* Sf = (double*)malloc(sizeof(double) * (size_t)n * n);
     memcpy(Sf, S, sizeof(double) * (size_t)n * n);
-    if (orc_cholesky(n, Sf) == ORC_OK) {
+    const int s_broken = o->break_kind == ORC_BREAK_S && (int32_t)it == o->break_it;
+    if (!s_broken && orc_cholesky(n, Sf) == ORC_OK) {
       for (int i = 0; i < nR; ++i) {
         double* Ji = J + (size_t)i * n;
         memcpy(Ji, P + (size_t)i * n, sizeof(double) * (size_t)n);
@@ -602,6 +603,8 @@ int32_t orc_iteration(const orc_model* m, const orc_options* o, const double* x0
     double* rhs = (double*)malloc(sizeof(double) * (size_t)n);
     for (int j = 0; j < n; ++j) rhs[j] = -g[j];
     retries = damped_solve(n, G, o->lambda, rhs, o->ir_steps, delta, &lambda_used);
+    if (pass == 0 && jm == ORC_JAC_LSQ && o->break_kind == ORC_BREAK_SYSTEM && (int32_t)it == o->break_it)
+      retries = ORC_E_NOT_PD; /* test hook: the LSQ system has no factor */
     free(rhs);
   }
   if (status == ORC_OK && retries < 0) status = ORC_E_NOT_PD;

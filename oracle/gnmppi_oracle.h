@@ -73,7 +73,14 @@ typedef struct {
   uint64_t seed;
   int32_t sampling;   /* ORC_SAMPLE_*; sigma points need antithetic, K = 2n */
   int32_t method;     /* ORC_METHOD_*                                       */
+  /* Test hook (off when break_kind is 0): at iteration break_it the LSQ
+   * form is made to break down as if S had no Cholesky factor (kind 1) or
+   * the damped LSQ system had none at any damping (kind 2), so that the
+   * tests can pin the fallback to the printed form on any input. */
+  int32_t break_it, break_kind;
 } orc_options;
+
+enum { ORC_BREAK_NONE = 0, ORC_BREAK_S = 1, ORC_BREAK_SYSTEM = 2 };
 
 /* One Algorithm-1 iteration's outputs.  Array pointers are optional. */
 typedef struct {

@@ -52,7 +52,8 @@ class OrcOptions(C.Structure):
     _fields_ = [("K", C.c_int32), ("iterations", C.c_int32), ("L", C.c_int32), ("jac_mode", C.c_int32),
                 ("antithetic", C.c_int32), ("monotone", C.c_int32), ("threads", C.c_int32),
                 ("ir_steps", C.c_int32), ("lam", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
-                ("tau", C.c_double), ("seed", C.c_uint64), ("sampling", C.c_int32), ("method", C.c_int32)]
+                ("tau", C.c_double), ("seed", C.c_uint64), ("sampling", C.c_int32), ("method", C.c_int32),
+                ("break_it", C.c_int32), ("break_kind", C.c_int32)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -194,6 +195,10 @@ class Options:
     seed: int = 0
     sampling: str = "random"  # "random" (Method D) or "sigma" (sigma points, Method E)
     method: str = "gn"  # "gn" (Algorithm 1) or "mppi" (the MPPI step of Eq. 5, Method C)
+    # test hook: at iteration break_it make the LSQ form break down ("s": S has
+    # no Cholesky factor; "system": the damped LSQ system has none)
+    break_it: int = -1
+    break_kind: str = "none"
 
     def c(self) -> OrcOptions:
         o = OrcOptions()
@@ -204,6 +209,8 @@ class Options:
         o.lam, o.beta, o.gamma, o.tau, o.seed = self.lam, self.beta, self.gamma, self.tau, self.seed
         o.sampling = {"random": 0, "sigma": 1}[self.sampling]
         o.method = {"gn": 0, "mppi": 1}[self.method]
+        o.break_it = self.break_it
+        o.break_kind = {"none": 0, "s": 1, "system": 2}[self.break_kind]
         return o
 
     def pairs(self, n: int) -> int:

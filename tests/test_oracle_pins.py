@@ -573,3 +573,59 @@ def test_dead_zone_friction_zeroes_exactly_the_small_controls():
         assert not np.array_equal(O.residual(fric, x0, np.zeros(2 * (fric.M - 1)) if fric.M else None, small),
                                   O.residual(plain, x0, np.zeros(2 * (fric.M - 1)) if fric.M else None,
                                              np.zeros_like(U)))
+
+
+# ------------------------------------------- LSQ breakdown (Eq. 9, B > 0) ---
+# Eq. 9 assumes a positive definite B_GGN.  The oracle's reading: when the
+# LSQ form J = P S^-1 breaks down (S without a Cholesky factor, or the damped
+# LSQ system without one at every damping), the iteration takes the printed
+# Monte Carlo form J = P Sigma^-1 / K', and so does the rest of the solve.
+# The breakdown is forced through the oracle's test hook, so both branches and
+# the sticky rule are pinned on any input: against a direct call in the
+# printed form (a different code path through the same arithmetic), and
+# against the LSQ iteration it replaces (which must differ).
+def _breakdown_problem():
+    seed = 41
+    M, N, K = 4, 10, 64  # n = 20, K' = 32 >= n: AUTO takes the LSQ form
+    x0, tgt = I.chain_instances(seed, 1, M)
+    return O.chain(M=M, N=N), x0[0], tgt[0], K, seed
+
+
+@pytest.mark.parametrize("kind", ["s", "system"])
+def test_lsq_breakdown_takes_the_printed_form(kind):
+    m, x0, tgt, K, seed = _breakdown_problem()
+    U = np.random.default_rng(3).normal(0.0, 0.2, size=m.n)
+    lsq = O.iteration(m, O.Options(K=K, seed=seed), x0, tgt, U, 0.2, it=1)
+    sig = O.iteration(m, O.Options(K=K, seed=seed, jac_mode="sigma"), x0, tgt, U, 0.2, it=1)
+    brk = O.iteration(m, O.Options(K=K, seed=seed, break_it=1, break_kind=kind), x0, tgt, U, 0.2, it=1)
+    other_it = O.iteration(m, O.Options(K=K, seed=seed, break_it=1, break_kind=kind), x0, tgt, U, 0.2, it=2)
+    lsq2 = O.iteration(m, O.Options(K=K, seed=seed), x0, tgt, U, 0.2, it=2)
+    assert lsq.status == sig.status == brk.status == 0
+    assert lsq.jac_mode_used == 0 and sig.jac_mode_used == 1 and brk.jac_mode_used == 1
+    assert np.array_equal(brk.delta, sig.delta) and np.array_equal(brk.U_next, sig.U_next)
+    assert brk.C_new == sig.C_new and brk.j_star == sig.j_star
+    assert np.linalg.norm(brk.delta - lsq.delta) > 1e-3 * np.linalg.norm(lsq.delta)
+    # the hook acts at its own iteration only
+    assert other_it.jac_mode_used == 0 and np.array_equal(other_it.delta, lsq2.delta)
+
+
+def test_lsq_breakdown_is_sticky_for_the_rest_of_the_solve():
+    m, x0, tgt, K, seed = _breakdown_problem()
+    T, b = 6, 2
+    opt = O.Options(K=K, iterations=T, seed=seed, break_it=b, break_kind="system")
+    st, U, Uh, Ch, its = O.solve(m, opt, x0, tgt, np.zeros(m.n), 0.2)
+    assert st == 0
+    assert [it.jac_mode_used for it in its] == [0] * b + [1] * (T - b)
+    # the same path step by step: LSQ before the breakdown, the printed form from it on
+    s = np.full(m.n, 0.2)
+    Uk = np.zeros(m.n)
+    for k in range(T):
+        jm = "auto" if k < b else "sigma"
+        ref = O.iteration(m, O.Options(K=K, seed=seed, jac_mode=jm), x0, tgt, Uk, s, it=k)
+        assert np.array_equal(Uh[k + 1], ref.U_next), k
+        Uk = ref.U_next
+        s = s * math.sqrt(0.7)
+    # without the sticky rule iteration b + 1 would return to LSQ
+    free = O.iteration(m, O.Options(K=K, seed=seed), x0, tgt, Uh[b + 1], s * 0 + 0.2 * math.sqrt(0.7) ** (b + 1),
+                       it=b + 1)
+    assert free.jac_mode_used == 0
