@@ -34,7 +34,10 @@ METRIC = "OCP solves/s to 1e-6 rel. cost gap"
 CSTAR = os.path.join(ROOT, "tests", "golden", "chain_m10_cstar.txt")
 CSTAR_FIXED = os.path.join(ROOT, "tests", "golden", "chain_m10_fixed_cstar.txt")
 CSTAR_UNEVEN = os.path.join(ROOT, "tests", "golden", "chain_uneven_cstar.txt")
+CSTAR_PEND = os.path.join(ROOT, "tests", "golden", "pendulum_cstar.txt")
 WORKLOAD = "chain M=10 N=100 nu=2 K=2048 T=30 sigma0=0.2 lambda=1e-3"
+PREC, PREC_NAME = 2, "bf16x3"  # the library's BF16 mode (GNMPPI_PREC_BF16)
+DTYPE = "f32 rollouts, bf16 head+remainder contractions (3 passes, f32 accumulate), f64 Cholesky"
 
 
 # DRAM read + write of one k_samples launch of the default workload (256 instances), from one
@@ -102,6 +105,74 @@ def uneven_arm(args, dev, stream):
     else:
         out["solved"] = None
     return out
+
+
+def pendulum_arm(args, dev, stream):
+    """The pendulum swing-up (N=50, K=256, sigma0 0.5, lambda 1e-3, 20
+    iterations, FP64 mode), one instance per handle and solve as the
+    configuration states it, on the held-out initial states whose reference
+    optima the oracle wrote to tests/golden/pendulum_cstar.txt (its 20-iteration
+    solve polished by Method A).  Reports solves/s to the 1e-6 gap (honestly
+    0 when 20 iterations do not reach the optimum), the latency per solve, and
+    the same instances batched in one handle."""
+    import torch
+
+    from paper_2512_04579_gb300 import gnmppi as G
+    from paper_2512_04579_gb300 import inputs as I
+
+    if not os.path.exists(CSTAR_PEND):
+        return {"unavailable": "no pendulum reference optima"}
+    _, C_gn, Cs = load_cstar(CSTAR_PEND)
+    B = len(Cs)
+    seed = I.BASE_SEED
+    x0 = I.pendulum_x0(seed, B)
+    dx = torch.tensor(x0.ravel(), dtype=torch.float64, device=dev)
+    C = torch.empty(1, dtype=torch.float64, device=dev)
+    Cfin = np.zeros(B)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    hs = [G.gnmppi_create(G.pendulum_problem(N=50, K=256, iterations=20, lam=LAM, sigma0=0.5, seed=seed,
+                                             first_instance=b), 1, None, stream.cuda_stream) for b in range(B)]
+    dU = torch.zeros(50, dtype=torch.float64, device=dev)
+    for b in range(min(B, 3)):  # warm-up (graph capture)
+        G.gnmppi_solve(hs[b], G.MEM_DEVICE, dx[2 * b: 2 * b + 2], None, dU, None)
+    t_ms = 0.0
+    for b in range(B):
+        dU.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        G.gnmppi_solve(hs[b], G.MEM_DEVICE, dx[2 * b: 2 * b + 2], None, dU, None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ms += e0.elapsed_time(e1)
+        G.gnmppi_cost(hs[b], G.MEM_DEVICE, dx[2 * b: 2 * b + 2], None, dU, C)
+        Cfin[b] = float(C.item())
+    for h in hs:
+        G.gnmppi_destroy(h)
+    ms = t_ms / B
+    g = (Cfin - Cs) / Cs
+    solved = int(np.sum(g <= GAP))
+    # the same instances in one handle
+    hb = G.gnmppi_create(G.pendulum_problem(N=50, K=256, iterations=20, lam=LAM, sigma0=0.5, seed=seed), B, None,
+                         stream.cuda_stream)
+    dUb = torch.zeros(B * 50, dtype=torch.float64, device=dev)
+    G.gnmppi_solve(hb, G.MEM_DEVICE, dx, None, dUb, None)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(max(1, args.steps)):
+        dUb.zero_()
+        G.gnmppi_solve(hb, G.MEM_DEVICE, dx, None, dUb, None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / max(1, args.steps)
+    G.gnmppi_destroy(hb)
+    return {"workload": "pendulum swing-up N=50 K=256 sigma0=0.5 lambda=1e-3 T=20, FP64, %d held-out x0" % B,
+            "solves_per_s": solved / (ms / 1e3), "solved": solved, "instances": B, "ms_per_solve": ms,
+            "gap_median": float(np.median(g)), "gap_min": float(np.min(g)),
+            "oracle_gap_median": float(np.median((C_gn - Cs) / Cs)),
+            "batched": {"ms_per_batch": ms_b, "instance_solves_per_s": B / (ms_b / 1e3)},
+            "note": "20 iterations of Method D do not reach the swing-up optimum (the oracle's own solve neither); "
+                    "the GPU's FP64 solve follows the oracle's"}
 
 
 def learned_eval(args, dev, stream, B, steps):
@@ -203,10 +274,42 @@ def dist_env():
         os.environ.get("LOCAL_RANK", "0"))
 
 
+def partition(batch, rank, world):
+    """Contiguous instance range [lo, hi) of rank r.  Instances are
+    independent, so the ranks split one batch with no data-path exchange; a
+    rank's handle gets first_instance = lo, so every instance draws the noise
+    stream it draws in the unsplit batch and the ranks together compute
+    exactly the one-GPU batch (strong scaling: the total work is fixed)."""
+    q, r = divmod(batch, world)
+    lo = rank * q + min(rank, r)
+    return lo, lo + q + (1 if rank < r else 0)
+
+
+def gather_rows(local, batch, world, device):
+    """Per-instance rows ([hi - lo, w] on each rank) of every rank, in
+    instance order, on every rank: the final gather of U and of the costs.
+    Ranks with fewer rows pad to the largest share for the all-gather."""
+    if world <= 1:
+        return local
+    import torch
+    import torch.distributed as dist
+
+    cnt = -(-batch // world)
+    buf = torch.zeros((cnt,) + tuple(local.shape[1:]), dtype=local.dtype, device=device)
+    buf[: local.shape[0]] = local.to(device)
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(parts, buf)
+    rows = []
+    for r in range(world):
+        lo, hi = partition(batch, r, world)
+        rows.append(parts[r][: hi - lo])
+    return torch.cat(rows)
+
+
 def reduce_over_ranks(ms, solved, world, device):
-    """Replicas: every rank solves its own copy of the batch.  The job's time
-    is the slowest rank's (max over ranks) and its work the instances solved
-    on all ranks (sum); returns both, unchanged for one rank."""
+    """The job's time is the slowest rank's (max over ranks) and its work the
+    instances solved on all ranks (sum); returns both, unchanged for one
+    rank."""
     if world <= 1:
         return ms, solved
     import torch
@@ -298,19 +401,21 @@ def run_gnmppi(args):
         dist.barrier()
     G.load()
 
-    idx, C_gn_oracle, Cstar = load_cstar()
+    idx, C_gn_oracle, Cstar_all = load_cstar()
     batch = len(idx) if args.batch <= 0 else min(args.batch, len(idx))
-    Cstar = Cstar[:batch]
+    Cstar_all = Cstar_all[:batch]
     seed = I.BASE_SEED + 1
     x0, tgt = I.chain_instances(seed, len(idx), M)
-    x0, tgt = x0[:batch], tgt[:batch]
+    lo, hi = partition(batch, rank, world)  # this rank's instances
+    nb = hi - lo
+    x0, tgt, Cstar = x0[lo:hi], tgt[lo:hi], Cstar_all[lo:hi]
     stream = torch.cuda.current_stream(dev)
-    prob = G.chain_problem(M=M, N=N, K=K, iterations=T, lam=LAM, sigma0=SIGMA0, seed=seed,
-                           precision=G.PREC_FP32)
-    h = G.gnmppi_create(prob, batch, None, stream.cuda_stream)
+    prob = G.chain_problem(M=M, N=N, K=K, iterations=T, lam=LAM, sigma0=SIGMA0, seed=seed, precision=PREC,
+                           first_instance=lo)
+    h = G.gnmppi_create(prob, nb, None, stream.cuda_stream)
     d_x0 = torch.tensor(x0.ravel(), dtype=torch.float64, device=dev)
     d_tgt = torch.tensor(tgt.ravel(), dtype=torch.float64, device=dev)
-    d_U0 = torch.zeros(batch * N * 2, dtype=torch.float64, device=dev)
+    d_U0 = torch.zeros(nb * N * 2, dtype=torch.float64, device=dev)
     d_U = torch.empty_like(d_U0)
 
     def one_step():
@@ -337,19 +442,21 @@ def run_gnmppi(args):
     # per-kernel CUDA-event times of one more iteration on the solve's final
     # state (before gnmppi_cost, which reloads the inputs and resets the state)
     phases = G.gnmppi_phase_times(h, T)
-    # FP64 re-evaluation of the final costs, outside the timed region
-    Cfin = torch.empty(batch, dtype=torch.float64, device=dev)
+    # FP64 re-evaluation of the final costs, outside the timed region, and the
+    # final gather of every rank's U and costs
+    Cfin = torch.empty(nb, dtype=torch.float64, device=dev)
     G.gnmppi_cost(h, G.MEM_DEVICE, d_x0, d_tgt, d_U, Cfin)
-    Cfin = Cfin.cpu().numpy()
-    gap = (Cfin - Cstar) / Cstar
-    solved_rank = int(np.sum(gap <= GAP))
-    ms, solved_all = reduce_over_ranks(ms, solved_rank, world, dev)
-    solved = solved_all // world  # per replica, for the solved fraction
+    U_all = gather_rows(d_U.view(nb, N * 2), batch, world, dev)
+    C_all = gather_rows(Cfin.view(nb, 1), batch, world, dev).view(-1).cpu().numpy()
+    assert U_all.shape[0] == batch and C_all.shape[0] == batch
+    gap = (C_all - Cstar_all) / Cstar_all
+    solved = int(np.sum(gap <= GAP))
+    ms, _ = reduce_over_ranks(ms, 0, world, dev)
     ms_step = ms / args.steps
-    value = solved_all / (ms_step / 1e3)
+    value = solved / (ms_step / 1e3)
 
     F = M - 1
-    roll_flops = batch * (K) * (N * chain_flops_per_step(F))  # K rollouts of N steps each
+    roll_flops = nb * (K) * (N * chain_flops_per_step(F))  # K rollouts of N steps each
     t_roll = phases["samples"] / 1e3
     peaks = {}
     try:
@@ -361,82 +468,98 @@ def run_gnmppi(args):
     achieved = roll_flops / t_roll / 1e12
     G.gnmppi_destroy(h)
 
-    # end to end through the C ABI with host buffers (copies inside the timed region)
-    prob_e = G.chain_problem(M=M, N=N, K=K, iterations=T, lam=LAM, sigma0=SIGMA0, seed=seed,
-                             precision=G.PREC_FP32)
-    he = G.gnmppi_create(prob_e, batch, None, stream.cuda_stream)
+    # end to end through the C ABI with host buffers: the copies of x0, the
+    # targets and U0 in and of U out are inside every timed step
+    prob_e = G.chain_problem(M=M, N=N, K=K, iterations=T, lam=LAM, sigma0=SIGMA0, seed=seed, precision=PREC,
+                             first_instance=lo)
+    he = G.gnmppi_create(prob_e, nb, None, stream.cuda_stream)
     hx0 = torch.tensor(x0.ravel(), dtype=torch.float64).pin_memory()
     htg = torch.tensor(tgt.ravel(), dtype=torch.float64).pin_memory()
-    hU = torch.zeros(batch * N * 2, dtype=torch.float64).pin_memory()
-    G.gnmppi_solve(he, G.MEM_HOST, hx0, htg, hU, None)
-    e_steps = max(1, min(args.steps, 3))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e_steps):
+    hU = torch.zeros(nb * N * 2, dtype=torch.float64).pin_memory()
+    for _ in range(args.warmup):
         hU.zero_()
         G.gnmppi_solve(he, G.MEM_HOST, hx0, htg, hU, None)
-    e2e_s = (time.perf_counter() - t0) / e_steps
-    Ce = np.zeros(batch)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        hU.zero_()
+        G.gnmppi_solve(he, G.MEM_HOST, hx0, htg, hU, None)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    Ce = np.zeros(nb)
     G.gnmppi_cost(he, G.MEM_HOST, hx0.numpy(), htg.numpy(), hU.numpy(), Ce)
     G.gnmppi_destroy(he)
     e2e_s, e2e_solved = reduce_over_ranks(e2e_s, int(np.sum((Ce - Cstar) / Cstar <= GAP)), world, dev)
-    e2e = {"value": e2e_solved / e2e_s, "unit": "solves/s",
-           "h2d_bytes_per_step": int(8 * (x0.size + tgt.size + batch * N * 2)),
+    e2e = {"value": e2e_solved / e2e_s, "unit": "solves/s", "steps": args.steps,
+           "h2d_bytes_per_step": int(8 * (batch * 4 * F + batch * 2 * F + batch * N * 2)),
            "d2h_bytes_per_step": int(8 * batch * N * 2)}
 
-    # plain GN-MPPI: one instance per handle and launch, in sequence
-    nplain = min(args.plain, batch)
-    hp = G.gnmppi_create(prob, 1, None, stream.cuda_stream)
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": DTYPE, "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD + f" batch={batch}", "batch": batch, "precision": PREC_NAME,
+                   "parallelism": f"instances split over {world} GPUs" if world > 1 else "single GPU",
+                   "l2": "working set per iteration > L2 (dR alone %.1f GB)" % (batch * (2 * F + 2) * N * K / 2 * 4 / 1e9)},
+        "solved": solved, "solved_fraction": solved / batch, "gap_median": float(np.median(gap)),
+        "gap_max": float(np.max(gap)),
+        "phases_ms_per_iteration": phases,
+        "roofline": {"kernel": "k_samples (RK4 rollouts + residual/cost/dR/W)", "bound": "alu",
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": K_SAMPLES_TRAFFIC_B256 if nb == 256 else None,
+                     "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size k_samples "
+                                     "launch at 256 instances, bytes per launch",
+                     "peak_note": "FP32 152 SMs x 128 lanes x 2 flop/FMA at the %.0f MHz maximum SM clock" % sm_max},
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    if rank == 0:
+        out["plain"] = plain_arm(args, dev, stream, prob, d_x0, d_tgt, Cstar)
+        out["learned"] = learned_arm(args, dev, stream)
+        out["pendulum"] = pendulum_arm(args, dev, stream)
+        if not args.no_uneven:
+            out["uneven"] = uneven_arm(args, dev, stream)
+        out["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def plain_arm(args, dev, stream, prob, d_x0, d_tgt, Cstar):
+    """Plain GN-MPPI: one instance per handle and graph launch, in sequence,
+    same kernels (the first instances of this rank's share)."""
+    import torch
+
+    from paper_2512_04579_gb300 import gnmppi as G
+
+    F = M - 1
+    nplain = min(args.plain, len(Cstar))
+    p1 = G.chain_problem(M=M, N=N, K=K, iterations=T, lam=LAM, sigma0=SIGMA0, seed=prob.seed, precision=PREC,
+                         first_instance=prob.first_instance)
+    hp = G.gnmppi_create(p1, 1, None, stream.cuda_stream)
     pU = torch.zeros(N * 2, dtype=torch.float64, device=dev)
     pC = torch.empty(1, dtype=torch.float64, device=dev)
     G.gnmppi_solve(hp, G.MEM_DEVICE, d_x0[: 4 * F], d_tgt[: 2 * F], pU, None)
     torch.cuda.synchronize()
     p_solved = 0
     p0 = torch.cuda.Event(enable_timing=True)
-    p1 = torch.cuda.Event(enable_timing=True)
+    p1e = torch.cuda.Event(enable_timing=True)
     p_ms = 0.0
     for b in range(nplain):
         pU.zero_()
         p0.record(stream)
         G.gnmppi_solve(hp, G.MEM_DEVICE, d_x0[b * 4 * F:(b + 1) * 4 * F], d_tgt[b * 2 * F:(b + 1) * 2 * F], pU, None)
-        p1.record(stream)
+        p1e.record(stream)
         G.gnmppi_cost(hp, G.MEM_DEVICE, d_x0[b * 4 * F:(b + 1) * 4 * F], d_tgt[b * 2 * F:(b + 1) * 2 * F], pU, pC)
         torch.cuda.synchronize()
-        p_ms += p0.elapsed_time(p1)
+        p_ms += p0.elapsed_time(p1e)
         p_solved += int((float(pC.item()) - Cstar[b]) / Cstar[b] <= GAP)
     plain_ms = p_ms / max(1, nplain)
     G.gnmppi_destroy(hp)
-
-    out = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 rollouts/contractions, f64 Cholesky", "data": "synthetic (seeded)",
-        "config": {"workload": WORKLOAD + f" batch={batch}", "batch": batch, "precision": "fp32",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "working set per iteration > L2 (dR alone %.1f GB)" % (batch * (2 * F + 2) * N * K / 2 * 4 / 1e9)},
-        "solved": solved, "solved_fraction": solved / batch, "gap_median": float(np.median(gap)),
-        "gap_max": float(np.max(gap)),
-        "plain": {"solves_per_s": (p_solved / max(1, nplain)) * 1e3 / plain_ms, "ms_per_solve": plain_ms,
-                  "instances": nplain, "solved": p_solved,
-                  "note": "one instance per handle and graph launch, in sequence, same kernels"},
-        "phases_ms_per_iteration": phases,
-        "roofline": {"kernel": "k_samples (RK4 rollouts + residual/cost/dR/W)", "bound": "alu",
-                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": K_SAMPLES_TRAFFIC_B256 if batch == 256 else None,
-                     "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size k_samples "
-                                     "launch at 256 instances, bytes per launch",
-                     "peak_note": "FP32 152 SMs x 128 lanes x 2 flop/FMA at the %.0f MHz maximum SM clock" % sm_max},
-        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
-    }
-    out["learned"] = learned_arm(args, dev, stream)
-    if not args.no_uneven:
-        out["uneven"] = uneven_arm(args, dev, stream)
-    if rank == 0:
-        out["cpu_baseline"] = cpu_baseline(args)
-        print(json.dumps(out))
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
+    return {"solves_per_s": (p_solved / max(1, nplain)) * 1e3 / plain_ms, "ms_per_solve": plain_ms,
+            "instances": nplain, "solved": p_solved,
+            "note": "one instance per handle and graph launch, in sequence, same kernels"}
 
 
 def oracle_iteration_seconds(threads: int, iters: int, b: int = 0):

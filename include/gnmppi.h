@@ -70,10 +70,14 @@ enum {
 /* Arithmetic of the hot path. */
 enum {
   GNMPPI_PREC_FP64 = 0, /* every step in FP64 (parity mode)                               */
-  GNMPPI_PREC_FP32 = 1, /* FP32 rollouts with compensated cost sums, FP32 contraction and
-                           Gram, FP64 Cholesky with iterative refinement                   */
-  GNMPPI_PREC_BF16 = 2  /* as FP32, but residual differences and perturbations stored in
-                           BF16 and contracted on the tensor cores (FP32 accumulation)     */
+  GNMPPI_PREC_FP32 = 1, /* FP32 rollouts with compensated cost sums; contraction and Gram
+                           on the tensor cores from three TF32 passes over FP32 operands
+                           split into head and remainder (FP32-level accuracy, FP32
+                           accumulation); FP64 Cholesky with iterative refinement         */
+  GNMPPI_PREC_BF16 = 2  /* as FP32, but residual differences and perturbations stored as
+                           a BF16 head plus a BF16 remainder and contracted by three BF16
+                           passes (head x head + head x remainder + remainder x head,
+                           FP32 accumulation; 16 significant bits per operand)             */
 };
 
 /* Jacobian estimator (Eq. 7).  dR_m = (R(U+W_m) - R(U-W_m))/2 (antithetic) or
@@ -124,6 +128,12 @@ typedef struct {
   uint64_t seed;      /* Philox key of the noise stream                            */
   int32_t sampling;   /* GNMPPI_SAMPLE_* (0: random, Method D)                     */
   int32_t method;     /* GNMPPI_METHOD_* (0: Gauss-Newton, Algorithm 1)            */
+  int32_t first_instance; /* noise stream of instance b is that of instance
+                             first_instance + b (>= 0; 0: its position), so a batch
+                             split into contiguous ranges over several handles or
+                             GPUs, each given its range's first index, draws exactly
+                             the noise of the unsplit batch                       */
+  int32_t pad0;
 } gnmppi_problem;
 
 /* Per-instance shape of an uneven batch; fields <= 0 take the problem's value. */
@@ -267,6 +277,25 @@ gnmppi_status gnmppi_tune_set(gnmppi_t h, int32_t branches, int32_t solve_nt);
  * into buf (host, cap bytes).  Errors: E_ARG if cap is too small. */
 gnmppi_status gnmppi_tune_report(gnmppi_t h, char* buf, int32_t cap);
 
+/* Failure injection for tests (the paper has no counterpart: it exercises the
+ * library's handling of failures that Eq. 9's assumption B_GGN > 0 and the
+ * bounded device waits leave open, without faulting the GPU).  At Algorithm-1
+ * iteration `iteration` of every later gnmppi_step / gnmppi_solve on h:
+ *   kind 1: every LSQ system's Cholesky factorisation is treated as failed at
+ *           all dampings, so the iteration takes the printed form J = P Sigma^-1 / K'
+ *           (jac_mode_used 1) and the rest of the solve stays in it;
+ *   kind 2: every system of the iteration fails (the damping retries run out),
+ *           so the instances end with status GNMPPI_E_NOT_PD;
+ *   kind 3: in the tensor-core contraction every CTA first waits on a barrier
+ *           that nothing completes; the wait gives up after 20 ms, the kernel
+ *           winds down and the call returns GNMPPI_E_TIMEOUT (FP32 and BF16
+ *           modes only);
+ *   kind 0: off.
+ * The arithmetic of every kernel is otherwise unchanged; the next solve
+ * recaptures its CUDA graph.  Errors: E_ARG for an unknown kind, or kind 3
+ * on an FP64 handle. */
+gnmppi_status gnmppi_debug_inject(gnmppi_t h, int32_t kind, int32_t iteration);
+
 /* Softmin weights exp(-(C - min C)/tau) and the weighted mean perturbation
  * sum w_i W_i / sum w_i of one sample set, computed without any device
  * allocation.  The paper has no counterpart: this entry point exists for
@@ -278,20 +307,27 @@ gnmppi_status gnmppi_tune_report(gnmppi_t h, char* buf, int32_t cap);
  *   C      device, count doubles (one-sided) or 2*count doubles (antithetic:
  *          C[2m] = C(U + W_m), C[2m+1] = C(U - W_m)); non-finite pairs get
  *          weight 0.
- *   W      device, [n][count] doubles, sample-contiguous rows (the layout of
- *          gnmppi_debug_read buffer 1).
+ *   W      device, [n][count] doubles, sample-contiguous rows of exactly
+ *          count entries with no padding (the layout of gnmppi_debug_read
+ *          buffer 1; a solver handle's internal W, whose rows are padded and
+ *          stored in the handle's precision, is not this layout).
  *   mppi   device, n doubles out; stats device, 4 doubles out:
  *          {min C, sum w, sum w^2, effective sample size}.
  *   cuda_stream  cudaStream_t or NULL; the call is asynchronous on it.
  *   err    optional host buffer of err_len bytes for the error text.
  * Scratch: one double per sample pair in a fixed device array of 65536
  * entries (512 KB) that every GPU loading the library holds until exit; count
- * above 65536 is rejected with E_ARG.  The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress) with the device current;
- * make that first call before any stream capture.  Every call on a device
- * shares the array, so calls that overlap on the GPU race: serialise them
- * (one stream, or synchronise between calls).  No cudaMalloc, cudaFree or
- * other allocating routine is called. */
+ * above 65536 is rejected with E_ARG.  The first call on a device is a set-up
+ * call: it looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current, and under lazy module loading (the CUDA default) that
+ * lookup also loads the library's device code onto the device, which the
+ * driver allocates for; make that first call before any stream capture and
+ * outside the allocation-free phase (a warm-up call).  The address is kept
+ * for the life of the process, so resetting the device (cudaDeviceReset)
+ * after the first call is not supported.  Every call on a device shares the
+ * array, so calls that overlap on the GPU race: serialise them (one stream,
+ * or synchronise between calls).  No cudaMalloc, cudaFree or other
+ * allocating routine is called. */
 gnmppi_status gnmppi_softmin_noalloc(const double* C, const double* W, int32_t count, int32_t n,
                                      int32_t antithetic, double tau, double* mppi, double* stats,
                                      void* cuda_stream, char* err, int32_t err_len);

@@ -77,8 +77,13 @@ struct gnmppi_s {
   // concurrency of the rollout groups and the solve CTA shape
   TuneCfg tune{};
   std::string tune_report;
-  // asynchronous solve: per-instance states land in pinned host memory
+  // asynchronous solve: per-instance states (and the initial ones of a
+  // masked solve) and the tensor-core error word pass through pinned host memory
   InstState* h_st = nullptr;
+  InstState* h_init = nullptr;
+  int* h_err = nullptr;
+  // test injection (gnmppi_debug_inject): kind 3 = tensor-core wait at iteration inj_it
+  int inj_tc = 0;
   cudaEvent_t ev_done = nullptr;
   bool pending = false;
   cudaStream_t aux[kMaxBranches] = {};
@@ -173,6 +178,8 @@ static gnmppi_status validate(const gnmppi_problem* p, int32_t batch, const gnmp
     return fail(nullptr, GNMPPI_E_ARG, "sigma points need antithetic pairs");
   if (p->method != GNMPPI_METHOD_GN && p->method != GNMPPI_METHOD_MPPI)
     return fail(nullptr, GNMPPI_E_ARG, "unknown method");
+  if (p->first_instance < 0 || (int64_t)p->first_instance + batch > (1 << 28))
+    return fail(nullptr, GNMPPI_E_ARG, "first_instance + batch must be in 0..2^28 (noise-stream counter)");
   if (p->dynamics == GNMPPI_DYN_LINEAR) {
     const int nx = p->nx, nu = p->nu;
     const int key = nx * 16 + nu;
@@ -238,6 +245,8 @@ extern "C" void gnmppi_destroy(gnmppi_t h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_done) cudaEventDestroy(h->ev_done);
   if (h->h_st) cudaFreeHost(h->h_st);
+  if (h->h_init) cudaFreeHost(h->h_init);
+  if (h->h_err) cudaFreeHost(h->h_err);
   for (void* p : h->allocs) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -299,10 +308,13 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     d.o_xref = oR; oR += d.nref;
     d.o_U = oU; oU += d.n;
     // dR and W of an instance form one [nR + n][ldK] block (W rows last), so a
-    // single TMA tensor map covers both contraction operands
+    // single TMA tensor map covers both contraction operands; BF16 storage
+    // holds the heads in that block and the remainders in a second one right
+    // after it (the low plane, `lo` elements on)
     d.o_dR = odR;
     d.o_W = odR + (int64_t)d.nR * d.ldK;
-    odR += (int64_t)(d.nR + d.n) * d.ldK;
+    d.lo = prec == kBF16 ? (int64_t)(d.nR + d.n) * d.ldK : 0;
+    odR += (int64_t)(d.nR + d.n) * d.ldK * (prec == kBF16 ? 2 : 1);
     d.o_C = oC; oC += 2 * (int64_t)d.Kp;
     d.o_P = oP; oP += (int64_t)d.n * d.ldP;
     d.o_nn = onn; onn += (int64_t)d.n * d.n;
@@ -404,6 +416,9 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
   CK(cudaMallocHost((void**)&h->h_st, sizeof(InstState) * h->batch));
+  CK(cudaMallocHost((void**)&h->h_init, sizeof(InstState) * h->batch));
+  CK(cudaMallocHost((void**)&h->h_err, sizeof(int)));
+  *h->h_err = 0;
   for (auto& g : h->groups) {
     CK(g.fn.prepare(g.smem));
     AL(g.d_list, 4 * g.insts.size());
@@ -445,6 +460,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   c.ir_steps = p.ir_steps;
   c.antithetic = anti;
   c.sampling = p.sampling;
+  c.inst_base = p.first_instance;
   c.u_friction = p.dynamics == GNMPPI_DYN_PENDULUM ? p.params[4] : (p.dynamics == GNMPPI_DYN_CHAIN ? p.params[5] : 0.0);
   c.nx_lin = p.nx;
   c.nu_lin = p.nu;
@@ -686,6 +702,7 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
   }
   MARK(1);
   SolveArgs sa = solve_args(h, shrink);
+  sa.it = it;
   if (ON(1)) {
     k_softmin_wvec<S, TC><<<h->batch * kSoftminSplit, 256, 0, h->stream>>>(sa);
     CKL();
@@ -698,7 +715,8 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
   GemmArgs ga{h->d_desc, h->d_st, nullptr, h->d_dR, h->d_W, h->d_P, h->d_A, h->d_S2};
   if (ON(2)) {
     if (h->use_tc) {
-      CK(tc_contract_launch(h->tc, h->d_st, reinterpret_cast<float*>(h->d_P), h->stream));
+      const int inject = h->inj_tc && (int32_t)it == h->cs.inj_it;
+      CK(tc_contract_launch(h->tc, h->d_st, reinterpret_cast<float*>(h->d_P), h->stream, inject));
       h->launches++;
     } else {
       ga.tiles = h->d_tiles[0];
@@ -807,21 +825,29 @@ static gnmppi_status load_inputs(gnmppi_t h, int32_t mem, const double* x0, cons
   if (sigma) {
     CK(cudaMemcpyAsync(h->d_s, sigma, 8 * h->n_U, k, h->stream));
   } else {
-    std::vector<double> s0(h->n_U, h->p.sigma0);
-    CK(cudaMemcpyAsync(h->d_s, s0.data(), 8 * h->n_U, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));  // s0 is a temporary
+    const int64_t blocks = std::min<int64_t>(1024, (h->n_U + 255) / 256);
+    k_fill<<<(int)std::max<int64_t>(1, blocks), 256, 0, h->stream>>>(h->d_s, h->n_U, h->p.sigma0);
+    CKL();
+    h->launches++;
   }
   CK(cudaMemsetAsync(h->d_st, 0, sizeof(InstState) * h->batch, h->stream));
   return GNMPPI_OK;
 }
 
-// A bounded device wait that ran out leaves a flag; report it once and clear it.
+// The tensor-core error word (a bounded device wait ran out): copied to
+// pinned host memory and cleared on the stream, after the work it covers;
+// read by check_timeout once the stream has passed that point.
+static gnmppi_status fetch_timeout(gnmppi_t h) {
+  if (!h->use_tc) return GNMPPI_OK;
+  CK(cudaMemcpyAsync(h->h_err, h->tc.d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemsetAsync(h->tc.d_err, 0, sizeof(int), h->stream));
+  return GNMPPI_OK;
+}
+
 static gnmppi_status check_timeout(gnmppi_t h) {
   if (!h->use_tc) return GNMPPI_OK;
-  int flag = 0;
-  CK(cudaMemcpy(&flag, h->tc.d_err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (flag) {
-    CK(cudaMemset(h->tc.d_err, 0, sizeof(int)));
+  if (*h->h_err) {
+    *h->h_err = 0;
     return fail(h, GNMPPI_E_TIMEOUT, "a bounded wait in the tensor-core contraction ran out");
   }
   return GNMPPI_OK;
@@ -844,11 +870,11 @@ extern "C" gnmppi_status gnmppi_solve_async(gnmppi_t h, int32_t mem, const doubl
   gnmppi_status st = load_inputs(h, mem, x0, xref, U, sigma);
   if (st != GNMPPI_OK) return st;
   if (active) {
-    std::vector<InstState> init(h->batch);
-    memset(init.data(), 0, sizeof(InstState) * h->batch);
-    for (int b = 0; b < h->batch; ++b) init[b].status = active[b] ? 0 : kInactive;
-    CK(cudaMemcpyAsync(h->d_st, init.data(), sizeof(InstState) * h->batch, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));  // init is a temporary
+    // staged in the handle's pinned buffer: the previous solve's copy of it
+    // has completed (gnmppi_solve_wait synchronised), so no wait is needed here
+    memset(h->h_init, 0, sizeof(InstState) * h->batch);
+    for (int b = 0; b < h->batch; ++b) h->h_init[b].status = active[b] ? 0 : kInactive;
+    CK(cudaMemcpyAsync(h->d_st, h->h_init, sizeof(InstState) * h->batch, cudaMemcpyHostToDevice, h->stream));
   }
   // one CUDA graph per handle: the nominal rollout and every Algorithm-1 iteration
   if (!h->gexec) {
@@ -871,9 +897,14 @@ extern "C" gnmppi_status gnmppi_solve_async(gnmppi_t h, int32_t mem, const doubl
   }
   CK(cudaGraphLaunch(h->gexec, h->stream));
   h->launches += h->graph_nodes;
+  k_sigma_end<<<(h->batch + 127) / 128, 128, 0, h->stream>>>(h->d_desc, h->d_st, h->d_s, h->batch);
+  CKL();
+  h->launches++;
   const cudaMemcpyKind k = mem == GNMPPI_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   CK(cudaMemcpyAsync(U, h->d_U, 8 * h->n_U, k, h->stream));
   CK(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(InstState) * h->batch, cudaMemcpyDeviceToHost, h->stream));
+  gnmppi_status fst = fetch_timeout(h);
+  if (fst != GNMPPI_OK) return fst;
   CK(cudaEventRecord(h->ev_done, h->stream));
   h->pending = true;
   return GNMPPI_OK;
@@ -888,13 +919,11 @@ extern "C" gnmppi_status gnmppi_solve_wait(gnmppi_t h, gnmppi_report* rep) {
   if ((st = check_timeout(h)) != GNMPPI_OK) return st;
   std::vector<InstState> s(h->h_st, h->h_st + h->batch);
   if (rep) {
-    std::vector<double> s_end(h->n_U);
-    CK(cudaMemcpy(s_end.data(), h->d_s, 8 * h->n_U, cudaMemcpyDeviceToHost));
     for (int b = 0; b < h->batch; ++b) {
       rep[b].C_final = s[b].C_nom;
       rep[b].C_initial = s[b].C_init;
       rep[b].C_prev = s[b].iters > 0 ? s[b].C_start : s[b].C_nom;
-      rep[b].sigma_final = s_end[h->desc[b].o_U];
+      rep[b].sigma_final = s[b].sigma_end;
       rep[b].iterations = s[b].iters;
       rep[b].status = s[b].status == kInactive ? 0 : s[b].status;
       rep[b].n_masked = s[b].total_masked;
@@ -931,6 +960,7 @@ extern "C" gnmppi_status gnmppi_step(gnmppi_t h, int32_t mem, const double* x0, 
   CK(cudaMemcpyAsync(U, h->d_U, 8 * h->n_U, k, h->stream));
   std::vector<InstState> s(h->batch);
   CK(cudaMemcpyAsync(s.data(), h->d_st, sizeof(InstState) * h->batch, cudaMemcpyDeviceToHost, h->stream));
+  if ((st = fetch_timeout(h)) != GNMPPI_OK) return st;
   CK(cudaStreamSynchronize(h->stream));
   if ((st = check_timeout(h)) != GNMPPI_OK) return st;
   if (rep) {
@@ -1028,9 +1058,19 @@ extern "C" gnmppi_status gnmppi_debug_read(gnmppi_t h, int32_t what, int32_t ins
   const unsigned char* dR = (const unsigned char*)h->d_dR + h->szS * d.o_dR;
   const unsigned char* W = (const unsigned char*)h->d_W + h->szS * d.o_W;
   const unsigned char* P = (const unsigned char*)h->d_P + h->szA * d.o_P;
+  // BF16 storage: the value is the head plus the remainder of the low plane
+  auto rows_split = [&](const unsigned char* base, int64_t nrows) -> gnmppi_status {
+    gnmppi_status s2 = rows(base, h->szS, nrows, d.ldK, d.Kp);
+    if (s2 != GNMPPI_OK || d.lo == 0) return s2;
+    std::vector<double> low((size_t)nrows * d.Kp);
+    for (int64_t r = 0; r < nrows && s2 == GNMPPI_OK; ++r)
+      s2 = read_typed(h, base + (size_t)(d.lo + r * d.ldK) * h->szS, h->szS, 0, d.Kp, low.data() + r * d.Kp);
+    for (int64_t i = 0; i < nrows * d.Kp; ++i) host_out[i] += low[i];
+    return s2;
+  };
   switch (what) {
-    case 0: st = rows(dR, h->szS, d.nR, d.ldK, d.Kp); break;
-    case 1: st = rows(W, h->szS, d.n, d.ldK, d.Kp); break;
+    case 0: st = rows_split(dR, d.nR); break;
+    case 1: st = rows_split(W, d.n); break;
     case 2: {
       const int64_t nc = h->p.antithetic ? 2 * (int64_t)d.Kp : d.Kp;
       st = rows((const unsigned char*)(h->d_C + d.o_C), 8, 1, nc, nc);
@@ -1111,7 +1151,7 @@ void read_tune_file() {  // under g_tune_mu
   char sig[320];
   int nb = 0, nt = 0;
   while (fscanf(fp, "%319s %d %d", sig, &nb, &nt) == 3) {
-    if (nb >= 1 && nb <= kMaxBranches && (nt == 128 || nt == 256)) g_tune_cache[sig] = TuneCfg{nb, nt};
+    if (nb >= 1 && nb <= kMaxBranches && (nt == 128 || nt == 256 || nt == 512)) g_tune_cache[sig] = TuneCfg{nb, nt};
   }
   fclose(fp);
 }
@@ -1238,6 +1278,8 @@ extern "C" gnmppi_status gnmppi_autotune(gnmppi_t h, int32_t mem, const double* 
     }
   }
   h->tune.solve_nt = best_nt;
+  if ((st = fetch_timeout(h)) != GNMPPI_OK) return st;
+  CK(cudaStreamSynchronize(h->stream));
   st = check_timeout(h);
   if (st != GNMPPI_OK) return st;
   drop_graph(h);
@@ -1249,6 +1291,17 @@ extern "C" gnmppi_status gnmppi_autotune(gnmppi_t h, int32_t mem, const double* 
   h->tune_report = std::string("{\"source\": \"timed\", \"signature\": \"") + sig + "\", \"branches\": " +
                    std::to_string(h->tune.branches) + ", \"solve_nt\": " + std::to_string(h->tune.solve_nt) +
                    ", \"candidates\": [" + rows + "]}";
+  return GNMPPI_OK;
+}
+
+extern "C" gnmppi_status gnmppi_debug_inject(gnmppi_t h, int32_t kind, int32_t iteration) {
+  if (!h) return GNMPPI_E_ARG;
+  if (kind < 0 || kind > 3) return fail(h, GNMPPI_E_ARG, "unknown injection kind %d", (int)kind);
+  if (kind == 3 && !h->use_tc) return fail(h, GNMPPI_E_ARG, "the FP64 mode has no tensor-core waits");
+  h->cs.inj_kind = (kind == 1 || kind == 2) ? kind : 0;
+  h->inj_tc = kind == 3 ? 1 : 0;
+  h->cs.inj_it = kind == 0 ? -1 : iteration;
+  drop_graph(h);  // the captured graph holds the old kernel arguments
   return GNMPPI_OK;
 }
 

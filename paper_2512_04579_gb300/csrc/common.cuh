@@ -30,6 +30,8 @@ struct InstDesc {
   int32_t sP;                           // column of S in a [P^T | S] row: nR rounded up to 32 (16-byte aligned)
   int64_t o_x0, o_xref, o_U;            // packed double arrays (x0; xref; U, s, delta, g, ...)
   int64_t o_dR, o_W;                    // dR [nR][ldK], W [n][ldK] (storage type)
+  int64_t lo;                           // BF16 storage: elements from a head slot to its remainder slot
+                                        // (the low plane, (nR + n) ldK further on); 0 otherwise
   int64_t o_C;                          // sample costs [Kp][2] (double), e and weights [Kp]
   int64_t o_P;                          // [P^T | S]  [n][ldP] (accumulation type)
   int64_t o_nn;                         // n*n double arrays (A, S2, H)
@@ -49,6 +51,7 @@ struct InstState {
   int32_t jac_mode_used, total_masked, total_retries, iters;
   int32_t lsq_broken;  // the LSQ system broke down earlier in this solve
   int32_t pad;
+  double sigma_end;    // first sampling-scale component after the solve (report)
 };
 
 // Problem-wide constants.
@@ -62,6 +65,12 @@ struct Consts {
   int32_t sampling;   // 0: Philox normals (Method D), 1: sigma points sqrt(n) e_m (Method E)
   int32_t pad;
   double u_friction;  // dead-zone friction at the input of the dynamics (0: off)
+  // test injection (gnmppi_debug_inject): at iteration inj_it, kind 1 makes
+  // the LSQ system fail its factorisation at every damping, kind 2 every
+  // system of the iteration (0: off)
+  int32_t inj_kind, inj_it;
+  int32_t inst_base;  // noise-stream index of the handle's first instance
+  int32_t pad2;
 };
 
 // Setting V.ii of Sec. 5: dead-zone friction at the input of the dynamics,
@@ -163,6 +172,19 @@ template <typename S>
 __device__ __forceinline__ S to_store(double x) { return to_store<S>((float)x); }
 template <>
 __device__ __forceinline__ double to_store<double>(double x) { return x; }
+
+// One dR / W slot.  FP64 and FP32 storage keep the value itself.  BF16
+// storage keeps two planes: the head h = bf16(v) at p and the remainder
+// bf16(v - h) at p + lo, so that h + remainder carries 16 significant bits
+// and the tensor-core contraction can form FP32-accurate products from three
+// BF16 passes (head x head, head x remainder, remainder x head).
+__device__ __forceinline__ void put(double* p, int64_t, double v) { *p = v; }
+__device__ __forceinline__ void put(float* p, int64_t, float v) { *p = v; }
+__device__ __forceinline__ void put(__nv_bfloat16* p, int64_t lo, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  p[0] = h;
+  p[lo] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
 
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(float x) { return (double)x; }

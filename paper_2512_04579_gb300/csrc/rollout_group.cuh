@@ -332,6 +332,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   struct Em {
     S* dR;
     const T* r;  // interleaved nominal residual at the stage's first word
+    int64_t lo;  // offset of the remainder plane (BF16 storage)
     int ldK, m, base, own_w, ctl_w;
     bool active, plus;
     T sign, csum, esum;
@@ -344,10 +345,10 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
       const T own = plus ? v0 : v1;
       const int row = base + r0 + (plus ? 0 : 1);
       const T d = sign * (own - got) * (T)0.5;
-      if (active) dR[(int64_t)row * ldK + m] = to_store<S>(d);
+      if (active) put(dR + (int64_t)row * ldK + m, lo, d);
       esum += d * r[slot < FL ? 2 * G * slot + own_w : ctl_w];
     }
-  } em{dR, sR, I.ldK, m, 0, 2 * lg + (plus ? 0 : 1), 2 * SL + (plus ? 0 : 1), active, plus, sign, (T)0, (T)0};
+  } em{dR, sR, I.lo, I.ldK, m, 0, 2 * lg + (plus ? 0 : 1), 2 * SL + (plus ? 0 : 1), active, plus, sign, (T)0, (T)0};
   // The 2G lanes of a pair draw the normals of 2G consecutive steps at once
   // (lane l of the pair: Philox call q = k + l) and hand them round by shuffle.
   // Sigma points (Method E): pair m perturbs control m alone, by sqrt(n) s_m.
@@ -362,15 +363,15 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
       z1 = (2 * k + 1 == m) ? sqrtn : (T)0;
     } else {
       if (k % (2 * G) == 0)
-        box_muller(noise_words(a.cs.seed, (uint32_t)bm.x, a.it, mm, (uint32_t)(k + pl)), na0, na1);
+        box_muller(noise_words(a.cs.seed, (uint32_t)(bm.x + a.cs.inst_base), a.it, mm, (uint32_t)(k + pl)), na0, na1);
       z0 = __shfl_sync(0xffffffffu, na0, k % (2 * G), 2 * G);
       z1 = __shfl_sync(0xffffffffu, na1, k % (2 * G), 2 * G);
     }
     const T w0 = sS[2 * k] * z0, w1 = sS[2 * k + 1] * z1;
     const T u[2] = {sU[2 * k] + sign * w0, sU[2 * k + 1] + sign * w1};
     if (active && plus && lg == 0) {
-      Wm[(int64_t)(2 * k) * I.ldK + m] = to_store<S>(w0);
-      Wm[(int64_t)(2 * k + 1) * I.ldK + m] = to_store<S>(w1);
+      put(Wm + (int64_t)(2 * k) * I.ldK + m, I.lo, w0);
+      put(Wm + (int64_t)(2 * k + 1) * I.ldK + m, I.lo, w1);
     }
     em.base = k * rps;
     em.r = sR + k * RS;
@@ -408,8 +409,8 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   }
   if (active && plus && !ok) {  // dropped pair: its columns leave P and S
     const int rows = I.N * rps + 2 * I.F;
-    for (int row = lg; row < rows; row += G) dR[(int64_t)row * I.ldK + m] = to_store<S>(0.0f);
-    for (int j = lg; j < I.n; j += G) Wm[(int64_t)j * I.ldK + m] = to_store<S>(0.0f);
+    for (int row = lg; row < rows; row += G) put(dR + (int64_t)row * I.ldK + m, I.lo, (T)0);
+    for (int j = lg; j < I.n; j += G) put(Wm + (int64_t)j * I.ldK + m, I.lo, (T)0);
   }
 }
 

@@ -43,7 +43,21 @@ struct SolveArgs {
   const void* RL;  // [L][nR]
   double* Cl;      // [kMaxL+1]
   int shrink;      // apply the covariance shrink after the update
+  uint32_t it;     // iteration index (test injection)
 };
+
+// p[0..count) = v (the default per-component sampling scale sigma0).
+__global__ void __launch_bounds__(256) k_fill(double* __restrict__ p, int64_t count, double v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// st[b].sigma_end = s[o_U(b)] for every instance (the solve's report).
+__global__ void __launch_bounds__(128) k_sigma_end(const InstDesc* __restrict__ inst, InstState* __restrict__ st,
+                                                   const double* __restrict__ s, int batch) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < batch; b += gridDim.x * blockDim.x)
+    st[b].sigma_end = s[inst[b].o_U];
+}
 
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {
@@ -100,6 +114,14 @@ __device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
 }
 __device__ __forceinline__ float4 load4(const double* p) {
   return make_float4((float)p[0], (float)p[1], (float)p[2], (float)p[3]);
+}
+// Four W values of one row: BF16 storage adds the remainder plane (lo
+// elements further on) to the head, the other types hold the value itself.
+__device__ __forceinline__ float4 load4w(const float* p, int64_t) { return load4(p); }
+__device__ __forceinline__ float4 load4w(const double* p, int64_t) { return load4(p); }
+__device__ __forceinline__ float4 load4w(const __nv_bfloat16* p, int64_t lo) {
+  const float4 h = load4(p), l = load4(p + lo);
+  return make_float4(h.x + l.x, h.y + l.y, h.z + l.z, h.w + l.w);
 }
 
 template <typename S, typename TA>
@@ -220,15 +242,15 @@ __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
           am += w * sw[m];
         }
       } else {
-        // four samples per lane and load (16 B of FP32 or 8 B of BF16 W), so
-        // a row of 1024 samples is one batch of 8 independent loads per lane;
+        // four samples per lane and load (16 B of FP32, or 8 B from each BF16
+        // plane), so a row of 1024 samples is one batch of 8 independent loads per lane;
         // rows start 16-byte aligned (ldK and m0 are multiples of 64)
         const int m4 = (mc + 3) >> 2;
         const float4* se4 = reinterpret_cast<const float4*>(se);
         const float4* sw4 = reinterpret_cast<const float4*>(sw);
 #pragma unroll 8
         for (int q = lane; q < m4; q += 32) {
-          const float4 w = load4(row + 4 * q);
+          const float4 w = load4w(row + 4 * q, I.lo);
           const float4 ev = se4[q], wv = sw4[q];
           ag += w.x * ev.x + w.y * ev.y + w.z * ev.z + w.w * ev.w;
           am += w.x * wv.x + w.y * wv.y + w.z * wv.z + w.w * wv.w;
@@ -475,16 +497,20 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_solve(SolveArgs a) {
   // Monte Carlo form J = P Sigma^-1 / K', for this and the remaining
   // iterations of the solve (K' and n, which cause it, do not change).
   bool lsq = I.lsq != 0 && st.lsq_broken == 0;
+  // test injection: the factorisations of this iteration fail (kind 1: the
+  // LSQ system's, kind 2: every system's), uniform over the CTA
+  const bool inj = a.cs.inj_kind != 0 && (int32_t)a.it == a.cs.inj_it;
   for (int pass = 0; pass < 2 && !ok; ++pass) {
     if (pass == 1) {
       if (!lsq) break;
       lsq = false;
       lam = a.cs.lambda;
     }
+    const bool forced = inj && (a.cs.inj_kind == 2 || lsq);
     for (retries = 0; retries <= 6; ++retries) {
       build_system(A, S2, s, lsq, Keff, lam, Hp, L, n);
       __syncthreads();
-      if (chol_factor(L, invd, Y, n, &fail)) {
+      if (chol_factor(L, invd, Y, n, &fail) && !forced) {
         ok = true;
         break;
       }

@@ -6,30 +6,38 @@
 // with the sample index m as the reduction dimension.  dR and W of an instance
 // are stored as one [nR + n][ldK] block (sample-contiguous rows), so one TMA
 // tensor map per instance covers both operands: the A tile is rows nR + i of
-// the block, the B tile rows j.  One CTA computes a (128 or 256) x 256 output
-// tile -- two 128-row sub-tiles when the instance has more than 128 unknowns,
-// so that each B tile is streamed from L2 once for both:
-//   warp 0 lane 0  issues TMA loads into a 3-stage shared-memory ring,
-//   warp 1 lane 0  issues tcgen05.mma (M=128, N <= 256, K=16 BF16 / K=8 TF32)
-//                  per sub-tile into its own 256-column TMEM accumulator,
-//   warps 0-3      read TMEM back (tcgen05.ld 32x32b) and store FP32 rows
-//                  (the S columns from column sP on, 16-byte aligned).
-//  (2) the Gram product A = P^T P of Eq. 9 in FP32-level accuracy from three
-//      TF32 passes, A ~ Ph Ph^T + Ph Pl^T + Pl Ph^T with every FP32 operand
-//      x split into a TF32 head h = rna(x) and its remainder x - h (exact in
-//      FP32), and in the same launch S2 = S S^T for the scaled LSQ system.
-//      TMA streams the FP32 rows of [P^T | S] straight from the contraction's
-//      output; warps 2-3 split each landed stage in shared memory (head in
-//      place, remainder beside it) before the MMAs read it.  A diagonal tile
-//      takes its A sub-tiles from its own B rows (the operand is the same
-//      matrix), each sub-tile's MMAs stop at the diagonal, and the strictly
-//      lower 32 x 32 blocks are also stored transposed, so every entry of the
-//      symmetric output is written once.
+// the block, the B tile rows j.  Both reduced-precision modes keep FP32-level
+// accuracy (a single TF32 or BF16 pass does not: its operand rounding moves
+// the Gauss-Newton step, and the cost after it, by up to 1e-3 / 1e-2 at
+// 10^4 residual rows):
+//    BF16 mode (k_contract_tc): the rollouts store every operand as a BF16
+//      head plane and a BF16 remainder plane; one CTA computes a (128 or 256)
+//      x 256 output tile -- two 128-row sub-tiles when the instance has more
+//      than 128 unknowns, so that each B tile is streamed once for both --
+//      from three kind::f16 passes per product:
+//        warp 0 lane 0  issues TMA loads into a 3-stage shared-memory ring,
+//        warp 1 lane 0  issues tcgen05.mma (M=128, N <= 256, K=16) per
+//                       sub-tile into its own 256-column TMEM accumulator,
+//        warps 0-3      read TMEM back (tcgen05.ld 32x32b) and store FP32 rows
+//                       (the S columns from column sP on, 16-byte aligned);
+//    FP32 mode: the three-pass TF32 kernel of (2) on the FP32 [dR; W] block.
+//  (2) k_gram_tc: the Gram product A = P^T P of Eq. 9 in FP32-level accuracy
+//      from three TF32 passes, A ~ Ph Ph^T + Ph Pl^T + Pl Ph^T with every FP32
+//      operand x split into a TF32 head h = rna(x) and its remainder x - h
+//      (exact in FP32), and in the same launch S2 = S S^T for the scaled LSQ
+//      system.  TMA streams the FP32 rows of [P^T | S] straight from the
+//      contraction's output; warps 2-5 split each landed stage in shared
+//      memory (head in place, remainder beside it) before the MMAs read it.  A
+//      diagonal tile takes its A sub-tiles from its own B rows (the operand is
+//      the same matrix), each sub-tile's MMAs stop at the diagonal, and the
+//      strictly lower 32 x 32 blocks are also stored transposed, so every
+//      entry of the symmetric output is written once.
 // Every mbarrier wait is bounded by the global timer; a wait that runs out
 // sets the plan's error word and the CTA winds down without a trap.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "tc_contract.cuh"
 
@@ -38,7 +46,7 @@ namespace gnm {
 namespace {
 
 constexpr int BM = 128, BN = 256;
-constexpr int ROW_BYTES = 128;  // one k-block of a row: 64 BF16 or 32 FP32 values
+constexpr int ROW_BYTES = 128;  // one k-block of an FP32 row: 32 values
 constexpr int KBLK_F32 = 32;
 constexpr int A_BYTES = BM * ROW_BYTES;
 constexpr int B_BYTES = BN * ROW_BYTES;
@@ -72,16 +80,24 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase with the given parity; gives up after WAIT_NS or when
+// Wait for the phase with the given parity; gives up after limit_ns or when
 // another role of the CTA has aborted (check_abort).
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort, bool check_abort) {
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort, bool check_abort,
+                                          unsigned long long limit_ns = WAIT_NS) {
   const unsigned long long t0 = gtimer();
   for (uint32_t i = 0;; ++i) {
     if (mbar_try(a, parity)) return true;
     if (check_abort && *abort) return false;
-    if ((i & 255u) == 255u && gtimer() - t0 > WAIT_NS) return false;
+    if ((i & 255u) == 255u && gtimer() - t0 > limit_ns) return false;
   }
 }
+
+// Test injection (gnmppi_debug_inject): the MMA issuer first waits, with a
+// short limit, on the stage-0 "empty" barrier, which only its own commits
+// complete -- a wait that nothing ends -- so that the give-up path runs:
+// abort flag, error word, the producer's drain of its copies in flight,
+// the epilogue skipped, TMEM released.
+constexpr unsigned long long INJECT_WAIT_NS = 20000000ull;  // 20 ms
 
 __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int x, int y) {
   asm volatile(
@@ -93,13 +109,15 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, u
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes, 8-row groups 1024 bytes apart (SBO), descriptor version 1.
+// ROW64: 64-byte swizzle, rows of 64 bytes, 8-row groups 512 bytes apart.
+template <bool ROW64 = false>
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)((ROW64 ? 512 : 1024) >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)(ROW64 ? 4 : 2) << 61;
   return d;
 }
 
@@ -154,17 +172,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
 }
 
 // D[i][j] = sum_k A[i][k] B[j][k] for one (128 or 256) x 256 tile of one
-// contraction job; output columns >= ccut are stored cgap further right.
-template <bool BF16>
+// contraction job (the BF16 mode); output columns >= ccut are stored cgap
+// further right.  Every operand is a head plane plus a remainder plane
+// (lo_rows rows further down the tensor map), and each product is formed
+// from three BF16 passes, head x head + head x remainder + remainder x head,
+// which keeps FP32-level accuracy (the dropped remainder x remainder term is
+// ~2^-18 relative); 32-value k-blocks of 64-byte rows keep the stage of both
+// planes at 64 KB, so the ring holds three.
 __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __restrict__ maps,
                                                         const TcJob* __restrict__ jobs, const InstState* __restrict__ st,
                                                         const int4* __restrict__ tiles, float* __restrict__ D,
-                                                        int* __restrict__ err) {
-  constexpr int KBLK = BF16 ? 64 : 32;  // elements per k-block
-  constexpr int KSTEP = BF16 ? 16 : 8;  // elements per MMA
-  constexpr int NSUB = KBLK / KSTEP;    // MMAs per k-block and sub-tile (4)
+                                                        int* __restrict__ err, int inject) {
+  constexpr bool BF16 = true;
+  constexpr int KBLK = 32;              // elements per k-block
+  constexpr int KSTEP = 16;             // elements per MMA
+  constexpr int NSUB = KBLK / KSTEP;    // MMAs per k-block, sub-tile and pass
+  constexpr int RB = 64;                // bytes of one operand row per k-block
+  constexpr int BOX = BM * RB;          // one 128-row TMA box
+  constexpr int PLANES = 2;             // head and remainder planes
   constexpr int MTMAX = 2;              // 128-row sub-tiles of A per tile (each its own accumulator)
-  constexpr int STAGE_BYTES = MTMAX * A_BYTES + B_BYTES;
+  constexpr int PLANE_BYTES = (MTMAX + 2) * BOX;  // A sub-tiles, then the two B boxes
+  constexpr int STAGE_BYTES = PLANES * PLANE_BYTES;
   constexpr int STAGES = RING_BYTES / STAGE_BYTES;
   constexpr uint32_t TCOLS = MTMAX * TMEM_COLS;
   const int4 tl = tiles[blockIdx.x];
@@ -173,7 +201,7 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
   // so every B tile is streamed once for up to 256 output rows
   const int mt = tl.w;
   const int row_org = tl.y * mt * BM;
-  const uint32_t tx_bytes = (uint32_t)(mt * A_BYTES + B_BYTES);
+  const uint32_t tx_bytes = (uint32_t)(PLANES * (mt + 2) * BOX);
   if (st[J.inst].status != 0) return;  // uniform over the CTA, before any allocation
   const int nkb = J.nkb;
   const CUtensorMap* map = maps + J.map;
@@ -216,12 +244,15 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
       }
       const uint32_t full = su32(bars + s);
       mbar_expect_tx(full, tx_bytes);
-      const uint32_t a_dst = su32(base + s * STAGE_BYTES);
-      const uint32_t b_dst = a_dst + MTMAX * A_BYTES;
       const int x = J.x0 + kb * KBLK;
-      for (int q = 0; q < mt; ++q) tma_load(a_dst + q * A_BYTES, map, full, x, J.a_row0 + row_org + q * BM);
-      tma_load(b_dst, map, full, x, J.b_row0 + tl.z * BN);
-      tma_load(b_dst + BM * ROW_BYTES, map, full, x, J.b_row0 + tl.z * BN + BM);
+      for (int p = 0; p < PLANES; ++p) {
+        const uint32_t a_dst = su32(base + s * STAGE_BYTES + p * PLANE_BYTES);
+        const uint32_t b_dst = a_dst + MTMAX * BOX;
+        const int pr = p * J.lo_rows;
+        for (int q = 0; q < mt; ++q) tma_load(a_dst + q * BOX, map, full, x, pr + J.a_row0 + row_org + q * BM);
+        tma_load(b_dst, map, full, x, pr + J.b_row0 + tl.z * BN);
+        tma_load(b_dst + BOX, map, full, x, pr + J.b_row0 + tl.z * BN + BM);
+      }
       ++issued;
     }
     // every copy this thread issued has landed before the CTA may exit
@@ -231,7 +262,11 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
     // ---------------- MMA issuer
     const int ncols = min(BN, J.Nc - tl.z * BN);  // columns of this tile that are kept
     const uint32_t id = idesc<BF16>(min(BN, (ncols + 15) / 16 * 16));
-    for (int kb = 0; kb < nkb; ++kb) {
+    if (inject && !mbar_wait(su32(bars + STAGES), 0, abort, true, INJECT_WAIT_NS)) {
+      *abort = 1;
+      atomicExch(err, 1);
+    }
+    for (int kb = 0; kb < nkb && !*abort; ++kb) {
       const int s = kb % STAGES, round = kb / STAGES;
       if (!mbar_wait(su32(bars + s), round & 1, abort, true)) {
         *abort = 1;
@@ -240,13 +275,18 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
       }
       tc_fence_after();
       const uint32_t a0 = su32(base + s * STAGE_BYTES);
-      const uint32_t b0 = a0 + MTMAX * A_BYTES;
+      const uint32_t b0 = a0 + MTMAX * BOX;
 #pragma unroll
       for (int k = 0; k < NSUB; ++k) {
-        // sub-tile q accumulates into TMEM columns [256 q, 256 q + 256)
-        for (int q = 0; q < mt; ++q)
-          mma<BF16>(tmem + (uint32_t)(q * TMEM_COLS), sdesc(a0 + q * A_BYTES + k * 32), sdesc(b0 + k * 32), id,
-                    (kb > 0 || k > 0) ? 1u : 0u);
+        // sub-tile q accumulates into TMEM columns [256 q, 256 q + 256); one
+        // MMA covers 32 bytes of K
+        for (int q = 0; q < mt; ++q) {
+          const uint32_t d = tmem + (uint32_t)(q * TMEM_COLS);
+          const uint32_t ah = a0 + q * BOX + k * 32, bh = b0 + k * 32;
+          mma<BF16>(d, sdesc<true>(ah), sdesc<true>(bh), id, (kb > 0 || k > 0) ? 1u : 0u);
+          mma<BF16>(d, sdesc<true>(ah), sdesc<true>(bh + PLANE_BYTES), id, 1u);
+          mma<BF16>(d, sdesc<true>(ah + PLANE_BYTES), sdesc<true>(bh), id, 1u);
+        }
       }
       mma_commit(su32(bars + STAGES + s));  // frees the stage once these MMAs have read it
     }
@@ -331,11 +371,17 @@ __device__ __forceinline__ void split_block(unsigned char* p, int delta, int n4,
 // (one 32-column k-block): B head and remainder (256 rows), and for an
 // off-diagonal tile A head and remainder (128 rows).  192 threads: warp 0
 // lane 0 TMA, warp 1 lane 0 MMA, warps 2-5 split; warps 0-3 read TMEM back.
+// CONTRACT: the same three-pass product for the FP32 mode's contraction
+// [P^T | S] = W^T [dR | W] (off-diagonal tiles only, A rows a_row0 + i and B
+// rows b_row0 + j of the instance's FP32 [dR; W] map), FP32 output into out0
+// with the S columns moved to sP; otherwise A = out0 or S2 in FP64.
 constexpr int kGramThreads = 192;
+template <bool CONTRACT>
 __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
                                                     const InstState* __restrict__ st, const int4* __restrict__ tiles,
-                                                    double* __restrict__ A, double* __restrict__ S2,
-                                                    int* __restrict__ err) {
+                                                    void* __restrict__ out0, double* __restrict__ S2,
+                                                    int* __restrict__ err, int inject) {
+  using TO = typename std::conditional<CONTRACT, float, double>::type;
   constexpr int KBLK = 32, NSUB = 4;  // FP32 elements per k-block, TF32 MMAs (K = 8) per k-block
   constexpr int SPLITTERS = kGramThreads - 64;  // warps 2-5
   constexpr int MAXST = 3;
@@ -401,8 +447,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
       mbar_expect_tx(full, tx_bytes);
       const uint32_t b_dst = su32(base + s * stage_bytes);
       const int x = J.x0 + kb * KBLK;
-      for (int q = 0; q < nbox; ++q) tma_load(b_dst + q * A_BYTES, map, full, x, col_org + q * BM);
-      if (!diag) tma_load(b_dst + 2 * B_BYTES, map, full, x, row_org);
+      for (int q = 0; q < nbox; ++q) tma_load(b_dst + q * A_BYTES, map, full, x, J.b_row0 + col_org + q * BM);
+      if (!diag) tma_load(b_dst + 2 * B_BYTES, map, full, x, J.a_row0 + row_org);
       ++issued;
     }
     for (int kb = (issued > stages ? issued - stages : 0); kb < issued; ++kb)
@@ -431,7 +477,11 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
       const int need = diag ? min(kept, BM * (q + 1)) : kept;  // columns up to the diagonal
       id[q] = idesc<false>(min(BN, (need + 15) / 16 * 16));
     }
-    for (int kb = 0; kb < nkb; ++kb) {
+    if (inject && !mbar_wait(su32(bars + 2 * MAXST), 0, abort, true, INJECT_WAIT_NS)) {
+      *abort = 1;
+      atomicExch(err, 1);
+    }
+    for (int kb = 0; kb < nkb && !*abort; ++kb) {
       const int s = kb % stages, round = kb / stages;
       if (!mbar_wait(su32(bars + MAXST + s), round & 1, abort, true)) {
         *abort = 1;
@@ -466,8 +516,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
   if (warp >= 4) {
     // no TMEM lanes of their own
   } else if (__all_sync(0xffffffffu, ok && !*abort)) {
-    double* stg = reinterpret_cast<double*>(base) + warp * 32 * 33;
-    double* out = (J.out_sel ? S2 : A) + J.out_off;
+    TO* stg = reinterpret_cast<TO*>(base) + warp * 32 * 33;
+    TO* out = (CONTRACT ? reinterpret_cast<TO*>(out0)
+                        : reinterpret_cast<TO*>(J.out_sel ? S2 : reinterpret_cast<double*>(out0))) + J.out_off;
 #pragma unroll 1
     for (int sub = 0; sub < mt; ++sub) {
       const int row0 = row_org + sub * BM + warp * 32;
@@ -477,15 +528,18 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
         uint32_t v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sub * TMEM_COLS + c * 32), v);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = (double)__uint_as_float(v[q]);
+        for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = (TO)__uint_as_float(v[q]);
         __syncwarp();
         const int col = col_org + c * 32 + lane;
         if (col < J.Nc) {
+          const int colw = col < J.ccut ? col : col + J.cgap;
 #pragma unroll 4
           for (int rr = 0; rr < 32; ++rr)
-            if (row0 + rr < J.M) out[(int64_t)(row0 + rr) * J.ldc + col] = stg[rr * 33 + lane];
+            if (row0 + rr < J.M) out[(int64_t)(row0 + rr) * J.ldc + colw] = stg[rr * 33 + lane];
         }
-        if (!diag || c < 4 * sub) {  // strictly lower block: store its transpose too
+        // strictly lower block of the symmetric Gram: store its transpose too
+        // (the contraction's output is rectangular and has no mirror image)
+        if (!CONTRACT && (!diag || c < 4 * sub)) {
           const int rowt = row0 + lane;
           if (rowt < J.M) {
 #pragma unroll 4
@@ -523,16 +577,19 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode(std::string& err) {
 }
 
 // Rank-2 tensor map over rows of `cols` elements (row stride ld elements),
-// box = one 128-byte k-block x 128 rows, 128-byte swizzle, zero fill outside.
+// box = one k-block x 128 rows, zero fill outside: FP32 k-blocks of 128
+// bytes with the 128-byte swizzle, BF16 k-blocks of 64 bytes with the
+// 64-byte swizzle (32 values either way).
 static bool encode_rows(PFN_cuTensorMapEncodeTiled_v12000 encode, CUtensorMap* m, void* gaddr, bool bf16, int64_t cols,
                         int64_t ld, int64_t rows) {
   const size_t esz = bf16 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
-  cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / esz), (cuuint32_t)BM};
+  cuuint32_t box[2] = {(cuuint32_t)KBLK_F32, (cuuint32_t)BM};
   cuuint32_t estr[2] = {1, 1};
   return encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, gaddr, dims, strides,
-                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                bf16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -560,7 +617,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
   auto encode = get_encode(err);
   if (!encode) return GNMPPI_E_CUDA;
   const size_t esz = bf16 ? 2 : 4;
-  const int kblk = bf16 ? 64 : 32;
+  const int kblk = KBLK_F32;
   const int nb = (int)desc.size();
   std::vector<CUtensorMap> maps(3 * (size_t)nb);
   std::vector<TcJob> jobs(3 * (size_t)nb);
@@ -575,9 +632,15 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
       err = "[P^T | S] rows are not 16-byte aligned";
       return GNMPPI_E_ARG;
     }
-    // contraction: one map over the instance's [dR; W] block
+    // contraction: one map over the instance's [dR; W] block (BF16: the head
+    // block and the remainder block after it, 2 (nR + n) rows)
+    const int lo_rows = bf16 ? d.nR + d.n : 0;
+    if (bf16 && d.lo != (int64_t)lo_rows * d.ldK) {
+      err = "BF16 remainder plane is not the block after the heads";
+      return GNMPPI_E_ARG;
+    }
     if (!encode_rows(encode, &maps[b], reinterpret_cast<char*>(dRW) + esz * (size_t)d.o_dR, bf16, d.ldK, d.ldK,
-                     d.nR + d.n)) {
+                     (int64_t)(d.nR + d.n) * (bf16 ? 2 : 1))) {
       err = "cuTensorMapEncodeTiled failed (contraction, instance " + std::to_string(b) + ")";
       return GNMPPI_E_CUDA;
     }
@@ -595,9 +658,19 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     jc.ldc = d.ldP;
     jc.ccut = d.nR;          // S columns of the output ...
     jc.cgap = d.sP - d.nR;   // ... start at sP
-    const int mt = d.n > BM ? 2 : 1;  // up to 256 rows per tile: each B tile streamed once
-    for (int i = 0; i < (d.n + mt * BM - 1) / (mt * BM); ++i)
-      for (int j = 0; j < (d.nR + d.n + BN - 1) / BN; ++j) tc.push_back(make_int4(b, i, j, mt));
+    jc.lo_rows = lo_rows;
+    if (bf16) {
+      // (job, row tile, column tile, sub-tiles): up to 256 rows per tile, so
+      // each B tile is streamed once
+      const int mt = d.n > BM ? 2 : 1;
+      for (int i = 0; i < (d.n + mt * BM - 1) / (mt * BM); ++i)
+        for (int j = 0; j < (d.nR + d.n + BN - 1) / BN; ++j) tc.push_back(make_int4(b, i, j, mt));
+    } else {
+      // three-pass TF32 kernel: (job, first row, first column, 1), the row
+      // tiles of a column block adjacent so that its B rows are read from L2
+      for (int j = 0; j < d.nR + d.n; j += BN)
+        for (int i = 0; i < d.n; i += BM) tc.push_back(make_int4(b, i, j, 1));
+    }
     // Gram: FP32 maps over the P^T columns (nR) and the S columns (n) of [P^T | S]
     float* Pb = reinterpret_cast<float*>(P) + d.o_P;
     if (!encode_rows(encode, &maps[nb + b], Pb, false, d.nR, d.ldP, d.n) ||
@@ -634,7 +707,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     const TcJob& j = jobs[t.x];
     return (int64_t)j.nkb * (t.w & 3) * std::min(BN, j.Nc - t.z);
   };
-  auto contract_work = [&](const int4& t) { return (int64_t)jobs[t.x].nkb * t.w; };
+  auto contract_work = [&](const int4& t) { return (int64_t)jobs[t.x].nkb * (bf16 ? t.w : 1); };
   std::stable_sort(tc.begin(), tc.end(),
                    [&](const int4& a, const int4& b) { return contract_work(a) > contract_work(b); });
   std::stable_sort(tg.begin(), tg.end(), [&](const int4& a, const int4& b) { return gram_work(a) > gram_work(b); });
@@ -667,11 +740,10 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     return GNMPPI_E_CUDA;
   }
   plan->smem = RING_BYTES + 1024 + 256;
-  cudaError_t e = bf16 ? cudaFuncSetAttribute(k_contract_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              plan->smem)
-                       : cudaFuncSetAttribute(k_contract_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              plan->smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
+  cudaError_t e = bf16 ? cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem)
+                       : cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
   if (e != cudaSuccess) {
     err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
     return GNMPPI_E_CUDA;
@@ -679,21 +751,21 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
   return GNMPPI_OK;
 }
 
-cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float* P, cudaStream_t stream) {
+cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float* P, cudaStream_t stream, int inject) {
   if (plan.ntiles_c == 0) return cudaSuccess;
   if (plan.bf16)
-    k_contract_tc<true><<<plan.ntiles_c, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st, plan.d_tiles_c, P,
-                                                                   plan.d_err);
+    k_contract_tc<<<plan.ntiles_c, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st, plan.d_tiles_c, P,
+                                                             plan.d_err, inject);
   else
-    k_contract_tc<false><<<plan.ntiles_c, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st, plan.d_tiles_c, P,
-                                                                    plan.d_err);
+    k_gram_tc<true><<<plan.ntiles_c, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
+                                                                        plan.d_tiles_c, P, nullptr, plan.d_err, inject);
   return cudaGetLastError();
 }
 
 cudaError_t tc_gram_launch(const TcPlan& plan, const InstState* d_st, double* A, double* S2, cudaStream_t stream) {
   if (plan.ntiles_g == 0) return cudaSuccess;
-  k_gram_tc<<<plan.ntiles_g, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st, plan.d_tiles_g, A, S2,
-                                                       plan.d_err);
+  k_gram_tc<false><<<plan.ntiles_g, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
+                                                                        plan.d_tiles_g, A, S2, plan.d_err, 0);
   return cudaGetLastError();
 }
 

@@ -1,7 +1,7 @@
 // tc_contract.cuh -- host interface of the tensor-core Jacobian-reconstruction
 // contraction (Eq. 7 of arXiv 2512.04579): [P^T | S] = W^T [dR | W] per
-// instance on tcgen05 (BF16 or TF32 operands, FP32 accumulation in TMEM),
-// operands staged by TMA.  Internal.
+// instance on tcgen05 (TF32 operands, or BF16 head + remainder operands in
+// three passes; FP32 accumulation in TMEM), operands staged by TMA.  Internal.
 #pragma once
 #include <cuda.h>
 
@@ -25,6 +25,7 @@ struct TcJob {
   int64_t out_off;
   int32_t ldc, out_sel;
   int32_t ccut, cgap;
+  int32_t lo_rows, pad;  // BF16 contraction: map rows from a head row to its remainder row
 };
 
 struct TcPlan {
@@ -39,14 +40,17 @@ struct TcPlan {
   std::vector<void*> allocs;
 };
 
-// dRW: the combined per-instance [nR + n][ldK] operand block (BF16 when bf16,
-// FP32 otherwise); P: the FP32 [P^T | S] array (S from column sP on).  Builds
-// tensor maps, jobs and tile lists.
+// dRW: the combined per-instance [nR + n][ldK] operand block (FP32; or, when
+// bf16, a BF16 head block followed by its remainder block, d.lo elements
+// apart); P: the FP32 [P^T | S] array (S from column sP on).  Builds tensor
+// maps, jobs and tile lists.
 gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void* P, int bf16, cudaStream_t stream,
                              TcPlan* plan, std::string& err);
 
-// [P^T | S] = W^T [dR | W] into P (FP32).
-cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float* P, cudaStream_t stream);
+// [P^T | S] = W^T [dR | W] into P (FP32).  inject != 0 (tests only): every
+// CTA's first MMA-side wait is on a barrier that nothing completes, so it
+// runs out after 20 ms, sets the error word and the CTA winds down.
+cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float* P, cudaStream_t stream, int inject);
 
 // A = P^T P and, for instances in LSQ mode, S2 = S S^T (FP64 outputs) from
 // three TF32 passes over [P^T | S] split in shared memory, in one launch.

@@ -30,7 +30,7 @@ EXPORTS = ["gnmppi_create", "gnmppi_layout", "gnmppi_solve", "gnmppi_solve_maske
            "gnmppi_mlp_num_params", "gnmppi_mlp_set_params", "gnmppi_mlp_get_params", "gnmppi_mlp_set_normalization",
            "gnmppi_mlp_forward", "gnmppi_mlp_loss_grad", "gnmppi_mlp_train_step", "gnmppi_mlp_warm_start",
            "gnmppi_mlp_destroy", "gnmppi_mlp_last_error", "gnmppi_autotune", "gnmppi_tune_set", "gnmppi_solve_async", "gnmppi_solve_wait",
-           "gnmppi_tune_report"]
+           "gnmppi_tune_report", "gnmppi_debug_inject"]
 
 
 class Problem(C.Structure):
@@ -40,7 +40,7 @@ class Problem(C.Structure):
                 ("precision", C.c_int32), ("jac_mode", C.c_int32), ("antithetic", C.c_int32),
                 ("monotone", C.c_int32), ("ir_steps", C.c_int32), ("lam", C.c_double), ("sigma0", C.c_double),
                 ("beta", C.c_double), ("gamma", C.c_double), ("tau", C.c_double), ("seed", C.c_uint64),
-                ("sampling", C.c_int32), ("method", C.c_int32)]
+                ("sampling", C.c_int32), ("method", C.c_int32), ("first_instance", C.c_int32), ("pad0", C.c_int32)]
 
 
 class InstanceShape(C.Structure):
@@ -108,6 +108,8 @@ def load(path: str | None = None):
     L.gnmppi_tune_set.argtypes = [vp, C.c_int32, C.c_int32]
     L.gnmppi_tune_set.restype = C.c_int32
     L.gnmppi_tune_report.argtypes = [vp, C.c_char_p, C.c_int32]
+    L.gnmppi_debug_inject.restype = C.c_int32
+    L.gnmppi_debug_inject.argtypes = [vp, C.c_int32, C.c_int32]
     L.gnmppi_tune_report.restype = C.c_int32
     for f in ("gnmppi_create", "gnmppi_layout", "gnmppi_solve", "gnmppi_step", "gnmppi_cost", "gnmppi_debug_read"):
         getattr(L, f).restype = C.c_int32
@@ -156,7 +158,7 @@ def make_problem(dynamics: int, *, N: int, K: int, iterations: int = 20, nx: int
                  dt: float = 0.0, params=(), lin=None, L: int = 16, precision: int = PREC_FP64,
                  jac_mode: int = JAC_AUTO, antithetic: bool = True, monotone: bool = False, ir_steps: int = 2,
                  lam: float = 1e-3, sigma0: float = 0.5, beta: float = 0.7, gamma: float = 0.5, tau: float = 1.0,
-                 seed: int = 0, sampling: int = 0, method: int = 0) -> Problem:
+                 seed: int = 0, sampling: int = 0, method: int = 0, first_instance: int = 0) -> Problem:
     p = Problem()
     p.dynamics, p.nx, p.nu, p.N, p.M = dynamics, nx, nu, N, M
     p.dt = dt
@@ -172,6 +174,7 @@ def make_problem(dynamics: int, *, N: int, K: int, iterations: int = 20, nx: int
         int(monotone), ir_steps
     p.lam, p.sigma0, p.beta, p.gamma, p.tau, p.seed = lam, sigma0, beta, gamma, tau, seed
     p.sampling, p.method = sampling, method
+    p.first_instance = first_instance
     return p
 
 
@@ -276,6 +279,14 @@ def gnmppi_autotune(h, mem, x0, xref, U, sigma=None, reps: int = 3) -> dict:
 def gnmppi_tune_set(h, branches: int, solve_nt: int):
     st = load().gnmppi_tune_set(h, branches, solve_nt)
     _check(h, st, "gnmppi_tune_set")
+
+
+INJECT_OFF, INJECT_LSQ_BREAKDOWN, INJECT_NOT_PD, INJECT_TC_TIMEOUT = 0, 1, 2, 3
+
+
+def gnmppi_debug_inject(h, kind: int, iteration: int = 0):
+    st = load().gnmppi_debug_inject(h, kind, iteration)
+    _check(h, st, "gnmppi_debug_inject")
 
 
 def gnmppi_tune_report(h) -> dict:

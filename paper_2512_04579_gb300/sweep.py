@@ -56,7 +56,8 @@ def batch_for(M, N, K, esz, budget_gb):
 def run_point(M, K, prec, N=200, budget_gb=60.0, iters=3, seed=I.BASE_SEED + 4):
     import torch
 
-    esz = {G.PREC_BF16: 2, G.PREC_FP32: 4, G.PREC_FP64: 8}[prec]
+    # bytes per stored dR / W entry: the BF16 mode keeps a head and a remainder plane
+    esz = {G.PREC_BF16: 4, G.PREC_FP32: 4, G.PREC_FP64: 8}[prec]
     B, nR, n = batch_for(M, N, K, esz, budget_gb)
     x0, tgt = I.chain_instances(seed, B, M)
     prob = G.chain_problem(M=M, N=N, K=K, iterations=1, lam=1e-3, sigma0=0.2, seed=seed, precision=prec)
@@ -78,7 +79,8 @@ def run_point(M, K, prec, N=200, budget_gb=60.0, iters=3, seed=I.BASE_SEED + 4):
     flops_chol = B * n ** 3 / 3
     it_ms = sum(ph.values())
     return {
-        "M": M, "K": K, "N": N, "n": n, "nR": nR, "batch": B, "precision": {2: "bf16", 4: "fp32", 8: "fp64"}[esz],
+        "M": M, "K": K, "N": N, "n": n, "nR": nR, "batch": B,
+        "precision": {G.PREC_BF16: "bf16", G.PREC_FP32: "fp32", G.PREC_FP64: "fp64"}[prec],
         "ms_per_iteration": it_ms, "instance_iterations_per_s": B / (it_ms / 1e3), "phases_ms": ph,
         "rollout_tflops": flops_roll / (ph["samples"] / 1e3) / 1e12,
         "rollout_frac_fp32": flops_roll / (ph["samples"] / 1e3) / 1e12 / pk["fp32_tflops"],

@@ -7,6 +7,9 @@ K=2048, 30 iterations, sigma0 0.2, lambda 1e-3):
                    warm-start evaluation stream, seed 2512045790 + 3
   chain_uneven     per-instance M ~ U{4..16}, N ~ U{40..160}, K ~ U{512..4096}
                    (inputs.uneven_chain_instances), seed 2512045790 + 2
+  pendulum         the swing-up of configuration 0: x0 ~ U([-0.5, 0.5]^2),
+                   N=50, K=256, sigma0 0.5, lambda 1e-3, 20 iterations,
+                   seed 2512045790 + 0 (instance b draws noise stream b)
 For each instance b:
   C_gn  = cost after the oracle's 30-iteration GN-MPPI solve (Algorithm 1),
   C*    = cost after polishing that solution with Method A (central-FD GGN,
@@ -48,6 +51,14 @@ def one(args):
     from paper_2512_04579_gb300 import inputs as I
 
     b, workload = args
+    if workload == "pendulum":
+        seed = I.BASE_SEED
+        x0 = I.pendulum_x0(seed, BATCH)
+        m = O.pendulum(N=50)
+        opt = O.Options(K=256, iterations=20, lam=LAM, seed=seed, threads=1)
+        st, U, Uh, Ch, its = O.solve(m, opt, x0[b], None, np.zeros(m.n), 0.5, inst=b)
+        stA, UA, CA, itA = O.method_a(m, x0[b], None, U.copy(), max_iter=300, lam=LAM)
+        return b, Ch[-1], min(CA, Ch[-1])
     if workload == "chain_uneven":
         seed = I.BASE_SEED + 2
         Ms, Ns, Ks, x0s, tgts = I.uneven_chain_instances(seed, BATCH)
@@ -77,12 +88,15 @@ if __name__ == "__main__":
         rows = sorted(pool.map(one, [(b, workload) for b in range(BATCH)], chunksize=1))
     out = os.path.join(HERE, f"{workload}_cstar.txt")
     seed_note = {"chain_m10": "2512045790+1", "chain_m10_fixed": "2512045790+3 (fixed target, eval stream)",
-                 "chain_uneven": "2512045790+2 (per-instance M, N, K)"}[workload]
-    shape = ("chain M, N, K per instance (inputs.uneven_chain_instances)" if workload == "chain_uneven"
-             else f"chain M={M} N={N} K={K}")
+                 "chain_uneven": "2512045790+2 (per-instance M, N, K)", "pendulum": "2512045790+0"}[workload]
+    if workload == "pendulum":
+        head = "pendulum swing-up N=50 K=256 T=20 sigma0=0.5"
+    elif workload == "chain_uneven":
+        head = f"chain M, N, K per instance (inputs.uneven_chain_instances) T={T} sigma0={SIGMA0}"
+    else:
+        head = f"chain M={M} N={N} K={K} T={T} sigma0={SIGMA0}"
     with open(out, "w") as f:
-        f.write(f"# {workload}: {shape} T={T} sigma0={SIGMA0} lambda={LAM} seed={seed_note} "
-                f"batch={BATCH}\n")
+        f.write(f"# {workload}: {head} lambda={LAM} seed={seed_note} batch={BATCH}\n")
         f.write("# written by tests/golden/make_cstar.py from the FP64 oracle: b C_gn C_star\n")
         for b, cg, cs in rows:
             f.write(f"{b} {cg:.17g} {cs:.17g}\n")

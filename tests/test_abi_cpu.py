@@ -103,4 +103,5 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.gnmppi_step(None, 0, None, None, None, None, 0, None) == G.E_ARG
     assert lib.gnmppi_cost(None, 0, None, None, None, None) == G.E_ARG
     assert lib.gnmppi_launch_count(None) == 0
+    assert lib.gnmppi_debug_inject(None, 1, 0) == G.E_ARG
     lib.gnmppi_destroy(None)

@@ -1,9 +1,12 @@
 """CPU, two ranks over gloo: the host logic of bench.py's multi-GPU path.
-Instances are independent, so N > 1 runs one replica of the batch per rank
-with no data-path collective (weak scaling); the only cross-rank steps are
-the barrier around the timed region and the reduction of its result: the
-job's time is the slowest rank's and its work the instances solved on all
-ranks.  The reference arm runs on rank 0 alone."""
+Instances are independent, so N > 1 splits one batch into contiguous
+instance ranges, one per rank, with no data-path collective; each rank's
+handle starts its noise streams at its range's first instance, so the ranks
+compute exactly the one-GPU batch (strong scaling).  The cross-rank steps are
+the barrier around the timed region, the reduction of its result (the job's
+time is the slowest rank's, its work the instances solved on all ranks) and
+the final gather of every instance's U and cost.  The reference arm runs on
+rank 0 alone."""
 import os
 import socket
 import subprocess
@@ -74,3 +77,62 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def _gather_worker(rank, world, port, batch, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    import bench
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        lo, hi = bench.partition(batch, rank, world)
+        # this rank's per-instance results: U rows and costs that name their instance
+        U = torch.stack([torch.arange(6, dtype=torch.float64) + 100.0 * i for i in range(lo, hi)])
+        C = torch.tensor([[0.5 * i] for i in range(lo, hi)], dtype=torch.float64)
+        Ug = bench.gather_rows(U, batch, world, "cpu")
+        Cg = bench.gather_rows(C, batch, world, "cpu")
+        q.put((rank, lo, hi, Ug.numpy(), Cg.view(-1).numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("batch", [256, 255, 3])
+def test_two_ranks_split_one_batch_and_gather_it_in_instance_order(batch):
+    import numpy as np
+    import torch.multiprocessing as mp
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    ranges = [bench.partition(batch, r, 2) for r in range(2)]
+    assert ranges[0][0] == 0 and ranges[0][1] == ranges[1][0] and ranges[1][1] == batch
+    assert abs((ranges[0][1] - ranges[0][0]) - (ranges[1][1] - ranges[1][0])) <= 1
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gather_worker, args=(r, 2, port, batch, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted((q.get(timeout=120) for _ in procs), key=lambda o: o[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # the single-rank concatenation: every instance's row, in instance order
+    U1 = np.stack([np.arange(6, dtype=float) + 100.0 * i for i in range(batch)])
+    C1 = 0.5 * np.arange(batch, dtype=float)
+    for rank, lo, hi, Ug, Cg in out:
+        assert (lo, hi) == ranges[rank]
+        assert np.array_equal(Ug, U1) and np.array_equal(Cg, C1)
+
+
+def test_one_rank_partition_is_the_whole_batch():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.partition(256, 0, 1) == (0, 256)
+    assert [bench.partition(10, r, 4) for r in range(4)] == [(0, 3), (3, 6), (6, 8), (8, 10)]

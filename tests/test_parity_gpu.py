@@ -4,9 +4,13 @@ on the same seeded inputs.
 FP64 mode: relative 1e-10 (normwise for vectors) per Algorithm-1 iteration,
 with the oracle's iterate U_k fed to both sides so that the comparison never
 drifts; the step delta (and U_{k+1}) within max(1e-10, 4 kappa_2 u) of the
-damped normal equations, the forward-error bound of a backward-stable solve.  Reduced-precision modes: 1e-4 relative on costs.
+damped normal equations, the forward-error bound of a backward-stable solve.
+Reduced-precision modes (FP32 rollouts; tensor-core contractions of
+FP32-level accuracy): 1e-4 relative on every cost -- nominal, per sample,
+line search, after each step, converged.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -19,6 +23,7 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-10
 TOLRED = 1e-4
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -46,6 +51,7 @@ def sigmas(s0, beta, T, n):
 
 
 U64 = np.finfo(float).eps / 2  # unit roundoff of FP64
+U32 = float(np.finfo(np.float32).eps) / 2  # unit roundoff of FP32
 
 
 def step_tol(big, it, tol):
@@ -275,13 +281,10 @@ def test_reduced_precision_chain_full_size_iteration(prec):
     assert st == 0
     assert rep[0].C_nom == pytest.approx(it.C_nom, rel=TOLRED)
     np.testing.assert_allclose(Cs, it.C_samp, rtol=TOLRED)
-    # The step itself follows a Jacobian estimate whose TF32/BF16 operands carry
-    # ~1e-3 relative rounding, so one step's cost agrees to ~1e-3; the 1e-4 bar
-    # applies to rollout costs (above) and to converged solves (next test).
-    assert rep[0].C_new == pytest.approx(it.C_new, rel=3e-3)
-    # U_0 = 0, so U_1 = alpha* delta on both sides: the step directions agree
-    cosang = float(np.dot(U, it.U_next) / (np.linalg.norm(U) * np.linalg.norm(it.U_next)))
-    assert cosang > 0.99
+    assert rep[0].j_star == it.j_star
+    assert rep[0].C_new == pytest.approx(it.C_new, rel=TOLRED)
+    # U_0 = 0, so U_1 = alpha* delta on both sides: the steps agree
+    assert rel(U, it.U_next) < 1e-2
 
 
 @pytest.mark.parametrize("prec", [G.PREC_FP32, G.PREC_BF16])
@@ -303,12 +306,77 @@ def test_reduced_precision_chain_solve_cost(prec):
     assert O.cost(m, x0[0], tgt[0], U) == pytest.approx(C, rel=1e-12)
 
 
-@pytest.mark.parametrize("prec,tol", [(G.PREC_FP32, 2e-3), (G.PREC_BF16, 1.5e-2)])
+@pytest.mark.parametrize("prec", [G.PREC_FP32, G.PREC_BF16])
+def test_reduced_precision_per_iteration_full_size(prec):
+    """Chain M=10, N=100 (n=200, nR=2018), K=2048: four Algorithm-1
+    iterations along the oracle's own trajectory (its U_k and sampling scale
+    fed to both sides, so nothing drifts): nominal, sample and line-search
+    costs and the cost after each step within 1e-4."""
+    seed = I.BASE_SEED + 1
+    M, N, K, T = 10, 100, 2048, 4
+    x0, tgt = I.chain_instances(seed, 1, M)
+    m = O.chain(M=M, N=N)
+    opt = O.Options(K=K, iterations=T, lam=1e-3, seed=seed, threads=16)
+    st, Uo, Uh, Ch, its = O.solve(m, opt, x0[0], tgt[0], np.zeros(m.n), 0.2)
+    assert st == 0
+    ss = sigmas(0.2, opt.beta, T, m.n)
+    gp = G.chain_problem(M=M, N=N, K=K, iterations=1, lam=1e-3, sigma0=0.2, seed=seed, precision=prec)
+    s = G.Solver(gp, 1)
+    try:
+        for k in range(T):
+            stg, Ug, rep = s.step(x0[0], tgt[0], Uh[k], ss[k], k)
+            r, it = rep[0], its[k]
+            assert stg == 0 and r.status == 0
+            assert r.C_nom == pytest.approx(it.C_nom, rel=TOLRED)
+            np.testing.assert_allclose(s.debug("C"), it.C_samp, rtol=TOLRED)
+            np.testing.assert_allclose(s.debug("Cline"), it.C_line[: opt.L], rtol=TOLRED)
+            assert r.C_new == pytest.approx(it.C_new, rel=TOLRED), k
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("prec", [G.PREC_FP32, G.PREC_BF16])
+def test_reduced_precision_full_size_solves_reach_the_reference_optima(prec):
+    """The benchmark problem at full size: chain M=10, N=100, K=2048,
+    30 iterations, 8 instances in one handle and one CUDA graph.  Every final
+    FP64 re-evaluated cost is within 1e-4 of the oracle's own 30-iteration
+    solve, and within 1e-6 of the reference optimum C* (the oracle's solve
+    polished by Method A) wherever the oracle's solve is."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "chain_m10_cstar.txt"), comments="#")
+    B = 8
+    seed = I.BASE_SEED + 1
+    x0, tgt = I.chain_instances(seed, len(rows), 10)
+    gp = G.chain_problem(M=10, N=100, K=2048, iterations=30, lam=1e-3, sigma0=0.2, seed=seed, precision=prec)
+    s = G.Solver(gp, B)
+    try:
+        st, U, rep = s.solve(x0[:B], tgt[:B], np.zeros(B * 200))
+        C = s.cost(x0[:B], tgt[:B], U)
+    finally:
+        s.close()
+    assert st == 0 and all(r.status == 0 and r.iterations == 30 for r in rep)
+    Cgn, Cs = rows[:B, 1], rows[:B, 2]
+    np.testing.assert_allclose(C, Cgn, rtol=TOLRED)
+    reached = (Cgn - Cs) / Cs <= 1e-6
+    assert reached.sum() >= B - 1
+    assert np.all((C - Cs)[reached] / Cs[reached] <= 1e-6)
+
+
+@pytest.mark.parametrize("prec,tol", [(G.PREC_FP32, 1e-4), (G.PREC_BF16, 1e-4)])
 def test_tensor_core_contraction_matches_oracle(prec, tol):
-    """[P^T | S] from the tcgen05 contraction (TF32 / BF16 operands, FP32
-    accumulation) against the oracle's P = sum dR W^T and S = sum W W^T, at
-    sizes spanning several 128 x 256 tiles with ragged edges (n = 150,
-    nR + n = 1130, K' = 700 pairs, padded to 704)."""
+    """[P^T | S] from the tcgen05 contraction (FP32 mode: three TF32 passes
+    over head/remainder splits of the FP32 operands; BF16 mode: head +
+    remainder BF16 operands in three passes; FP32 accumulation) against the
+    oracle's P = sum dR W^T and S = sum W W^T, at sizes spanning several
+    tiles with ragged edges (n = 150, nR + n = 1130, K' = 700 pairs, padded
+    to 704): normwise against the oracle, and entry by entry against the
+    FP64 products of the operands the GPU holds.  Each entry is a dot product
+    over the K' pairs, so its rounding error is bounded by a multiple of
+    sum_m |dR_m,i| |W_m,j| (and |W_m,i| |W_m,k| for S): the TF32 split leaves
+    ~2^-21 relative per product, the BF16 head + remainder pair 2^-17 per
+    operand (the dropped remainder x remainder term 2^-18), and the FP32
+    accumulation over 704 terms adds at most ~4e-5 of that sum.  A stale,
+    missing or misplaced tile leaves an O(|P|) error, about 1/sqrt(K') of the
+    bound's scale here, so it fails."""
     seed = 12
     M, N, K = 6, 75, 1400
     x0, tgt = I.chain_instances(seed, 1, M)
@@ -322,9 +390,17 @@ def test_tensor_core_contraction_matches_oracle(prec, tol):
     s.step(x0[0], tgt[0], np.zeros(m.n), np.full(m.n, 0.2), 0)
     PS = s.debug("PS").reshape(m.n, m.nR + m.n)
     A = s.debug("A").reshape(m.n, m.n)
+    Kp = K // 2
+    dRg = s.debug("dR").reshape(m.nR, Kp)
+    Wg = s.debug("W").reshape(m.n, Kp)
     s.close()
     assert rel(PS[:, : m.nR], P.T) < tol
     assert rel(PS[:, m.nR:], S) < tol
+    # entry by entry against the GPU's own operands
+    ent = 1e-4
+    for got, ref, bound in ((PS[:, : m.nR], Wg @ dRg.T, np.abs(Wg) @ np.abs(dRg).T),
+                            (PS[:, m.nR:], Wg @ Wg.T, np.abs(Wg) @ np.abs(Wg).T)):
+        assert np.all(np.abs(got - ref) <= ent * bound)
     # Gram A = P^T P on the tensor cores (three TF32 passes): its error is that of P
     assert rel(A, P.T @ P) < 2 * tol
     assert np.allclose(A, A.T, rtol=1e-5, atol=1e-5 * np.abs(A).max())
@@ -435,44 +511,55 @@ def test_bf16_long_chain_full_horizon_iteration():
     assert rep[0].C_nom == pytest.approx(it.C_nom, rel=TOLRED)
     np.testing.assert_allclose(Cs, it.C_samp, rtol=TOLRED)
     assert rep[0].C_new < rep[0].C_nom and it.C_new < it.C_nom
-    assert rep[0].C_new == pytest.approx(it.C_new, rel=1e-2)
+    assert rep[0].C_new == pytest.approx(it.C_new, rel=TOLRED)
 
 
 def test_reduced_precision_lsq_breakdown_takes_the_printed_form():
-    """K' = 256 pairs barely above n = 246: S is nearly singular, and with
-    FP32 operands P^T P + lambda S^2 has no Cholesky factor at any damping.
-    The iteration then takes the printed Monte Carlo form J = P Sigma^-1 / K'
-    (jac_mode_used 1) and must agree with the oracle run in that form; the
-    FP64 mode still solves the LSQ system, like the oracle in AUTO mode."""
+    """K' = 256 pairs barely above n = 246: S is nearly singular (kappa(S)
+    ~ 5.6e3), the case the LSQ-breakdown reading of Eq. 9 exists for.  With
+    the breakdown forced at iteration 0 (host-side injection, and the
+    oracle's hook) every precision takes the printed Monte Carlo form
+    J = P Sigma^-1 / K' (jac_mode_used 1) and agrees with the oracle run with
+    the same breakdown; without it the FP64 mode solves the LSQ system, like
+    the oracle in AUTO mode."""
     seed = I.BASE_SEED + 77
     Ms, Ns, Ks, x0s, tgts = I.uneven_chain_instances(seed, 24)
     b = 23
     M, N, K = int(Ms[b]), int(Ns[b]), int(Ks[b])
     assert (M, N, K) == (8, 123, 512)
     m = O.chain(M=M, N=N)
-    it_sig = O.iteration(m, O.Options(K=K, lam=1e-3, seed=seed, jac_mode="sigma"), x0s[b], tgts[b], np.zeros(m.n),
-                         0.2, inst=0, it=0)
-    it_auto = O.iteration(m, O.Options(K=K, lam=1e-3, seed=seed), x0s[b], tgts[b], np.zeros(m.n), 0.2, inst=0, it=0)
-    assert it_sig.status == 0 and it_auto.status == 0 and it_auto.jac_mode_used == 0
-    for prec, jm, ref in ((G.PREC_FP32, 1, it_sig), (G.PREC_FP64, 0, it_auto)):
+    it_brk = O.iteration(m, O.Options(K=K, lam=1e-3, seed=seed, break_it=0, break_kind="system", threads=8), x0s[b],
+                         tgts[b], np.zeros(m.n), 0.2, inst=0, it=0, want_big=True)
+    it_auto = O.iteration(m, O.Options(K=K, lam=1e-3, seed=seed, threads=8), x0s[b], tgts[b], np.zeros(m.n), 0.2,
+                          inst=0, it=0)
+    assert it_brk.status == 0 and it_auto.status == 0
+    assert it_brk.jac_mode_used == 1 and it_auto.jac_mode_used == 0
+    for prec, inject in ((G.PREC_FP64, True), (G.PREC_FP32, True), (G.PREC_BF16, True), (G.PREC_FP64, False)):
+        ref = it_brk if inject else it_auto
         gp = G.chain_problem(M=M, N=N, K=K, iterations=1, lam=1e-3, sigma0=0.2, seed=seed, precision=prec)
         s = G.Solver(gp, 1)
+        if inject:
+            G.gnmppi_debug_inject(s.h, G.INJECT_LSQ_BREAKDOWN, 0)
         st, U, rep = s.step(x0s[b], tgts[b], np.zeros(m.n), np.full(m.n, 0.2), 0)
         s.close()
         assert st == 0 and rep[0].status == 0
-        assert rep[0].jac_mode_used == jm
+        assert rep[0].jac_mode_used == ref.jac_mode_used
         assert rep[0].C_nom == pytest.approx(ref.C_nom, rel=TOLRED)
         assert rep[0].C_new < rep[0].C_nom
-        if prec == G.PREC_FP64:
+        if prec == G.PREC_FP64 and inject:
+            assert rep[0].C_new == pytest.approx(ref.C_new, rel=TOL64)
+        elif prec == G.PREC_FP64:
             # the scaled system (P^T P + lambda S^2) y = -b has kappa up to
             # kappa(S)^2 kappa(J^T J + lambda I) ~ 3e7 * 470 here, so the step,
             # and the cost after it, agree to ~kappa u = 1.6e-6
             assert rep[0].C_new == pytest.approx(ref.C_new, rel=2e-6)
         else:
-            # TF32 contraction operands give J ~1e-3 relative error, and the
-            # printed form has kappa(J^T J + lambda I) = 1.1e4 for this draw:
-            # the step moves by a few percent
-            assert rep[0].C_new == pytest.approx(ref.C_new, rel=5e-2)
+            # the printed form's system is ill-conditioned for this draw: the
+            # FP32 rounding of the rollouts that form J moves the step by up to
+            # kappa(J^T J + lambda I) u_FP32 (the forward-error bound of the
+            # FP64 tests with FP32's unit roundoff), and the cost after it with it
+            H = ref.J.T @ ref.J + ref.lambda_used * np.eye(m.n)
+            assert rep[0].C_new == pytest.approx(ref.C_new, rel=max(TOLRED, 4.0 * np.linalg.cond(H) * U32))
 
 
 # ------------------------------------------- Methods E and C (Sec. 5, Sec. 3)
@@ -527,7 +614,7 @@ def test_method_e_reduced_precision_and_group_chain():
     s.close()
     assert st == 0
     np.testing.assert_allclose(Cs, it.C_samp, rtol=TOLRED)
-    assert rep[0].C_new == pytest.approx(it.C_new, rel=3e-3)
+    assert rep[0].C_new == pytest.approx(it.C_new, rel=TOLRED)
 
 
 # -------------------------------------------- the test problems of Sec. 5 ----
@@ -612,3 +699,33 @@ def test_async_solves_on_two_streams_match_blocking_solves():
     finally:
         for h in hs:
             G.gnmppi_destroy(h)
+
+
+def test_split_batch_with_first_instance_matches_the_unsplit_batch():
+    """A batch split into contiguous ranges over several handles (as the
+    multi-GPU benchmark splits it over ranks), each handle given its range's
+    first instance, draws the same noise and gives bitwise the same solves as
+    the unsplit batch."""
+    seed = I.BASE_SEED + 14
+    M, N, K, B = 6, 20, 256, 8
+    x0, tgt = I.chain_instances(seed, B, M)
+    n = 2 * N
+    ref = G.Solver(G.chain_problem(M=M, N=N, K=K, iterations=4, lam=1e-3, sigma0=0.2, seed=seed,
+                                   precision=G.PREC_BF16), B)
+    st, U_all, rep_all = ref.solve(x0, tgt, np.zeros(B * n))
+    ref.close()
+    assert st == 0
+    for lo, hi in ((0, 3), (3, 8)):
+        s = G.Solver(G.chain_problem(M=M, N=N, K=K, iterations=4, lam=1e-3, sigma0=0.2, seed=seed,
+                                     precision=G.PREC_BF16, first_instance=lo), hi - lo)
+        st, U, rep = s.solve(x0[lo:hi], tgt[lo:hi], np.zeros((hi - lo) * n))
+        s.close()
+        assert st == 0
+        assert np.array_equal(U, U_all[lo * n: hi * n])
+        assert [r.C_final for r in rep] == [r.C_final for r in rep_all[lo:hi]]
+    # without the offset the second range draws other noise
+    s = G.Solver(G.chain_problem(M=M, N=N, K=K, iterations=4, lam=1e-3, sigma0=0.2, seed=seed,
+                                 precision=G.PREC_BF16), 5)
+    st, U, rep = s.solve(x0[3:8], tgt[3:8], np.zeros(5 * n))
+    s.close()
+    assert not np.array_equal(U, U_all[3 * n: 8 * n])
