@@ -74,10 +74,10 @@ enum {
                            on the tensor cores from three TF32 passes over FP32 operands
                            split into head and remainder (FP32-level accuracy, FP32
                            accumulation); FP64 Cholesky with iterative refinement         */
-  GNMPPI_PREC_BF16 = 2  /* as FP32, but residual differences and perturbations stored as
-                           a BF16 head plus a BF16 remainder and contracted by three BF16
-                           passes (head x head + head x remainder + remainder x head,
-                           FP32 accumulation; 16 significant bits per operand)             */
+  GNMPPI_PREC_BF16 = 2  /* as FP32, but the contraction's FP32 operands are split in shared
+                           memory into a BF16 head and a BF16 remainder and contracted by
+                           three BF16 passes (head x head + head x remainder + remainder x
+                           head, FP32 accumulation; 16 significant bits per operand)       */
 };
 
 /* Jacobian estimator (Eq. 7).  dR_m = (R(U+W_m) - R(U-W_m))/2 (antithetic) or

@@ -146,14 +146,10 @@ static gnmppi_status dalloc(gnmppi_t h, P** ptr, size_t bytes) {
 }
 
 static bool get_launchers(int prec, int dyn, int key, Launchers* o) {
-  if (dyn == kChain && key > kMaxChainF) {
-    if (prec == kFP64) return group_launchers_f64(key, o);
-    if (prec == kFP32) return group_launchers_f32(key, o);
-    return group_launchers_bf16(key, o);
-  }
-  if (prec == kFP64) return launchers_f64(dyn, key, o);
-  if (prec == kFP32) return launchers_f32(dyn, key, o);
-  return launchers_bf16(dyn, key, o);
+  // both reduced modes roll out and store dR / W in FP32; they differ in the
+  // tensor-core format of the contraction only
+  if (dyn == kChain && key > kMaxChainF) return prec == kFP64 ? group_launchers_f64(key, o) : group_launchers_f32(key, o);
+  return prec == kFP64 ? launchers_f64(dyn, key, o) : launchers_f32(dyn, key, o);
 }
 
 static gnmppi_status validate(const gnmppi_problem* p, int32_t batch, const gnmppi_instance_shape* shapes) {
@@ -258,7 +254,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   const gnmppi_problem& p = h->p;
   const int prec = p.precision;
   h->szT = prec == kFP64 ? 8 : 4;
-  h->szS = prec == kFP64 ? 8 : (prec == kFP32 ? 4 : 2);
+  h->szS = prec == kFP64 ? 8 : 4;
   h->szA = prec == kFP64 ? 8 : 4;
   const int anti = p.antithetic ? 1 : 0;
   // per-instance layout
@@ -308,13 +304,10 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     d.o_xref = oR; oR += d.nref;
     d.o_U = oU; oU += d.n;
     // dR and W of an instance form one [nR + n][ldK] block (W rows last), so a
-    // single TMA tensor map covers both contraction operands; BF16 storage
-    // holds the heads in that block and the remainders in a second one right
-    // after it (the low plane, `lo` elements on)
+    // single TMA tensor map covers both contraction operands
     d.o_dR = odR;
     d.o_W = odR + (int64_t)d.nR * d.ldK;
-    d.lo = prec == kBF16 ? (int64_t)(d.nR + d.n) * d.ldK : 0;
-    odR += (int64_t)(d.nR + d.n) * d.ldK * (prec == kBF16 ? 2 : 1);
+    odR += (int64_t)(d.nR + d.n) * d.ldK;
     d.o_C = oC; oC += 2 * (int64_t)d.Kp;
     d.o_P = oP; oP += (int64_t)d.n * d.ldP;
     d.o_nn = onn; onn += (int64_t)d.n * d.n;
@@ -465,7 +458,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   c.nx_lin = p.nx;
   c.nu_lin = p.nu;
   c.lin = h->d_lin;
-  // tensor-core contraction (TF32 on FP32 operands, or BF16)
+  // tensor-core contraction (three TF32 passes, or three BF16 passes, over FP32 operands)
   h->use_tc = prec != kFP64;
   if (h->use_tc) {
     st = tc_plan_create(h->desc, h->d_dR, h->d_P, prec == kBF16 ? 1 : 0, h->stream, &h->tc, h->err);
@@ -785,7 +778,7 @@ static gnmppi_status launch_iteration(gnmppi_t h, uint32_t it, int shrink, cudaE
   switch (h->p.precision) {
     case kFP64: return launch_iteration_t<double, double, double, double>(h, it, shrink, ev, mask);
     case kFP32: return launch_iteration_t<float, float, float, float>(h, it, shrink, ev, mask);
-    default: return launch_iteration_t<__nv_bfloat16, float, float, float>(h, it, shrink, ev, mask);
+    default: return launch_iteration_t<float, float, float, float>(h, it, shrink, ev, mask);
   }
 }
 
@@ -1016,22 +1009,11 @@ static void widen(const void* src, double* dst, int64_t count) {
   for (int64_t i = 0; i < count; ++i) dst[i] = (double)s[i];
 }
 
-static void widen_bf16(const void* src, double* dst, int64_t count) {
-  const uint16_t* s = reinterpret_cast<const uint16_t*>(src);
-  for (int64_t i = 0; i < count; ++i) {
-    uint32_t u = (uint32_t)s[i] << 16;
-    float f;
-    memcpy(&f, &u, 4);
-    dst[i] = f;
-  }
-}
-
 static gnmppi_status read_typed(gnmppi_t h, const void* dptr, size_t esz, int kind, int64_t count, double* out) {
   std::vector<unsigned char> tmp((size_t)count * esz);
   CK(cudaMemcpy(tmp.data(), dptr, tmp.size(), cudaMemcpyDeviceToHost));
   if (esz == 8) widen<double>(tmp.data(), out, count);
-  else if (esz == 4) widen<float>(tmp.data(), out, count);
-  else widen_bf16(tmp.data(), out, count);
+  else widen<float>(tmp.data(), out, count);
   (void)kind;
   return GNMPPI_OK;
 }
@@ -1058,19 +1040,9 @@ extern "C" gnmppi_status gnmppi_debug_read(gnmppi_t h, int32_t what, int32_t ins
   const unsigned char* dR = (const unsigned char*)h->d_dR + h->szS * d.o_dR;
   const unsigned char* W = (const unsigned char*)h->d_W + h->szS * d.o_W;
   const unsigned char* P = (const unsigned char*)h->d_P + h->szA * d.o_P;
-  // BF16 storage: the value is the head plus the remainder of the low plane
-  auto rows_split = [&](const unsigned char* base, int64_t nrows) -> gnmppi_status {
-    gnmppi_status s2 = rows(base, h->szS, nrows, d.ldK, d.Kp);
-    if (s2 != GNMPPI_OK || d.lo == 0) return s2;
-    std::vector<double> low((size_t)nrows * d.Kp);
-    for (int64_t r = 0; r < nrows && s2 == GNMPPI_OK; ++r)
-      s2 = read_typed(h, base + (size_t)(d.lo + r * d.ldK) * h->szS, h->szS, 0, d.Kp, low.data() + r * d.Kp);
-    for (int64_t i = 0; i < nrows * d.Kp; ++i) host_out[i] += low[i];
-    return s2;
-  };
   switch (what) {
-    case 0: st = rows_split(dR, d.nR); break;
-    case 1: st = rows_split(W, d.n); break;
+    case 0: st = rows(dR, h->szS, d.nR, d.ldK, d.Kp); break;
+    case 1: st = rows(W, h->szS, d.n, d.ldK, d.Kp); break;
     case 2: {
       const int64_t nc = h->p.antithetic ? 2 * (int64_t)d.Kp : d.Kp;
       st = rows((const unsigned char*)(h->d_C + d.o_C), 8, 1, nc, nc);

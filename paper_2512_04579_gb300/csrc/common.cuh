@@ -3,7 +3,6 @@
 // sums, and the dynamics / residual models (Sec. 2, Eq. 1-4 of arXiv
 // 2512.04579).  Internal; not part of the C ABI.
 #pragma once
-#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,8 +29,6 @@ struct InstDesc {
   int32_t sP;                           // column of S in a [P^T | S] row: nR rounded up to 32 (16-byte aligned)
   int64_t o_x0, o_xref, o_U;            // packed double arrays (x0; xref; U, s, delta, g, ...)
   int64_t o_dR, o_W;                    // dR [nR][ldK], W [n][ldK] (storage type)
-  int64_t lo;                           // BF16 storage: elements from a head slot to its remainder slot
-                                        // (the low plane, (nR + n) ldK further on); 0 otherwise
   int64_t o_C;                          // sample costs [Kp][2] (double), e and weights [Kp]
   int64_t o_P;                          // [P^T | S]  [n][ldP] (accumulation type)
   int64_t o_nn;                         // n*n double arrays (A, S2, H)
@@ -160,35 +157,12 @@ struct Acc<float> {
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
-template <typename S>
-__device__ __forceinline__ S to_store(float x);
-template <>
-__device__ __forceinline__ float to_store<float>(float x) { return x; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
-template <>
-__device__ __forceinline__ double to_store<double>(float x) { return (double)x; }
-template <typename S>
-__device__ __forceinline__ S to_store(double x) { return to_store<S>((float)x); }
-template <>
-__device__ __forceinline__ double to_store<double>(double x) { return x; }
-
-// One dR / W slot.  FP64 and FP32 storage keep the value itself.  BF16
-// storage keeps two planes: the head h = bf16(v) at p and the remainder
-// bf16(v - h) at p + lo, so that h + remainder carries 16 significant bits
-// and the tensor-core contraction can form FP32-accurate products from three
-// BF16 passes (head x head, head x remainder, remainder x head).
-__device__ __forceinline__ void put(double* p, int64_t, double v) { *p = v; }
-__device__ __forceinline__ void put(float* p, int64_t, float v) { *p = v; }
-__device__ __forceinline__ void put(__nv_bfloat16* p, int64_t lo, float v) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  p[0] = h;
-  p[lo] = __float2bfloat16_rn(v - __bfloat162float(h));
-}
+// One dR / W slot in the storage type (FP64 in the FP64 mode, FP32 otherwise).
+__device__ __forceinline__ void put(double* p, double v) { *p = v; }
+__device__ __forceinline__ void put(float* p, float v) { *p = v; }
 
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(float x) { return (double)x; }
-__device__ __forceinline__ double to_d(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
 
 // ------------------------------------------------------------------------
 // Models.  Each provides NX, NU, RPS (rows per stage), RT (terminal rows),

@@ -1,5 +1,5 @@
 // launch.cuh -- host-side launch table of the model-templated rollout kernels.
-// Internal; one table per storage precision (rollout_{f64,f32,bf16}.cu).
+// Internal; one table per rollout precision (rollout_{f64,f32}.cu).
 #pragma once
 #include "rollout_group.cuh"
 
@@ -18,11 +18,9 @@ struct Launchers {
 // key: chain -> free masses F; linear -> nx * 16 + nu; pendulum -> 0.
 bool launchers_f64(int dyn, int key, Launchers* out);
 bool launchers_f32(int dyn, int key, Launchers* out);
-bool launchers_bf16(int dyn, int key, Launchers* out);
 // chains of 17..64 free masses: a group of 4 or 8 lanes per rollout
 bool group_launchers_f64(int F, Launchers* out);
 bool group_launchers_f32(int F, Launchers* out);
-bool group_launchers_bf16(int F, Launchers* out);
 
 template <class Model, typename T, typename S>
 void launch_samples(const RollArgs& a, int nb, int smem, cudaStream_t s) {

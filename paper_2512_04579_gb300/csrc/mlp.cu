@@ -2,11 +2,19 @@
 // a nominal control sequence mu (U_0 of Algorithm 1) and one log sampling
 // scale per control step (Sigma_0), trained on solutions of plain GN-MPPI with
 // a Gaussian negative log-likelihood.  Training and inference run in these
-// kernels: strided SIMT GEMMs with fused bias / GELU / GELU' epilogues (FP32
-// accumulation; weights optionally rounded to BF16 for the forward and
-// input-gradient products), the loss and its output gradient, column sums for
-// the bias gradients, and Adam with bias correction.  Parameter layout per
-// layer: W [d_out][d_in] row-major, then b [d_out].
+// kernels.  Every product -- forward, input gradient, weight gradient -- is a
+// tcgen05 GEMM on the sm_103a tensor cores: its operands are stored as a BF16
+// head plane and a BF16 remainder plane (K-major rows, loaded by TMA), each
+// product is formed from three BF16 passes (head x head + head x remainder +
+// remainder x head, FP32 accumulation in TMEM, FP32-level accuracy), and the
+// epilogue fuses the bias, GELU (keeping the pre-activation) or the GELU'
+// factor of the layer below.  Weights optionally rounded to BF16 (their
+// remainder plane is then zero) for the forward and input-gradient products.
+// Then the loss and its output gradient, column sums for the bias gradients,
+// and Adam with bias correction.  Parameter layout per layer: W [d_out][d_in]
+// row-major, then b [d_out].
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -17,89 +25,196 @@
 #include <vector>
 
 #include "../../include/gnmppi.h"
+#include "tc_ptx.cuh"
 
+namespace gnm {
 namespace {
 
 constexpr int kMaxLayers = 8;
-
-struct MlpGemm {
-  // C[i][j] = sum_k A[i * a_i + k * a_k] * B[j * b_j + k * b_k]
-  const float* A;
-  int64_t a_i, a_k;
-  const void* B;
-  int64_t b_j, b_k;
-  float* C;
-  int64_t ldc;
-  int M, N, K;
-  const float* bias;   // [N] (modes 0, 1)
-  float* Z;            // pre-activations out (mode 1)
-  const float* Zprev;  // [M][ldc] pre-activations of the layer below (mode 2)
-  int mode;            // 0: acc + bias; 1: GELU(acc + bias), Z = acc + bias; 2: acc * GELU'(Zprev); 3: acc
-};
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_df(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
-__device__ __forceinline__ float ldw(const float* p, int64_t i) { return p[i]; }
-__device__ __forceinline__ float ldw(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
 
-template <typename TB>
-__global__ void __launch_bounds__(256) k_mlp_gemm(MlpGemm g) {
-  constexpr int BM = 64, BN = 64, BK = 16;
-  __shared__ float As[BK][BM + 1];
-  __shared__ float Bs[BK][BN + 1];
-  const TB* Bp = reinterpret_cast<const TB*>(g.B);
-  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[4][4];
-#pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
-    for (int e = threadIdx.x; e < BM * BK; e += 256) {
-      const int r = e / BK, kk = e % BK;
-      const int i = i0 + r, k = k0 + kk;
-      As[kk][r] = (i < g.M && k < g.K) ? g.A[(int64_t)i * g.a_i + (int64_t)k * g.a_k] : 0.f;
-      const int j = j0 + r;
-      Bs[kk][r] = (j < g.N && k < g.K) ? ldw(Bp, (int64_t)j * g.b_j + (int64_t)k * g.b_k) : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      float av[4], bv[4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) av[p] = As[kk][ty * 4 + p];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) bv[q] = Bs[kk][tx * 4 + q];
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
-    }
-    __syncthreads();
+// One product C[i][j] = sum_k A[i][k] B[j][k] (i < M, j < N, k < K) with the
+// epilogue `mode`: 0 acc + bias[j]; 1 Z = acc + bias[j], C = GELU(Z);
+// 2 acc * GELU'(Zprev); 3 acc.  C, Z and Zprev share the row stride ldc.
+struct MlpTc {
+  float* C;
+  int64_t ldc;
+  int M, N, K;
+  const float* bias;
+  float* Z;
+  const float* Zprev;
+  int mode;
+};
+
+constexpr int kTcBox = 128 * 128;           // one 128-row x 64-value BF16 box (128-byte rows), 16 KB
+constexpr int kTcStage = 4 * kTcBox;         // A head, A remainder, B head, B remainder
+constexpr int kTcStages = 3;
+constexpr int kTcSmem = kTcStages * kTcStage + 1024 + 256;
+
+// 128 x 128 output tile per CTA.  Warp 0 lane 0 issues the TMA loads of the
+// four operand boxes of a 64-value k-block into a 3-stage ring, warp 1 lane 0
+// the three BF16 passes (M = N = 128, K = 16 per MMA) into one TMEM
+// accumulator, warps 0-3 read it back (one TMEM lane per output row) and
+// store through a padded shared-memory transpose, whole rows per warp store.
+// Every wait is bounded; a wait that runs out sets *err and the CTA winds down.
+__global__ void __launch_bounds__(128, 1) k_mlp_tc(const __grid_constant__ CUtensorMap ah,
+                                                   const __grid_constant__ CUtensorMap al,
+                                                   const __grid_constant__ CUtensorMap bh,
+                                                   const __grid_constant__ CUtensorMap bl, MlpTc g,
+                                                   int* __restrict__ err) {
+  const int i0 = blockIdx.y * 128, j0 = blockIdx.x * 128;
+  const int nkb = (g.K + 63) / 64;
+  extern __shared__ unsigned char smem_dyn[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + kTcStages * kTcStage);
+  // bars[0..3): full, [3..6): empty, [6]: done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2 * kTcStages + 1; ++s) mbar_init(su32(bars + s), 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-#pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const int i = i0 + ty * 4 + p;
-    if (i >= g.M) continue;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = j0 + tx * 4 + q;
-      if (j >= g.N) continue;
-      const int64_t o = (int64_t)i * g.ldc + j;
-      float v = acc[p][q];
-      if (g.mode == 0) {
-        v += g.bias[j];
-      } else if (g.mode == 1) {
-        v += g.bias[j];
-        g.Z[o] = v;
-        v = gelu_f(v);
-      } else if (g.mode == 2) {
-        v *= gelu_df(g.Zprev[o]);
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(128)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t done = su32(bars + 2 * kTcStages);
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kTcStages, round = kb / kTcStages;
+      if (kb >= kTcStages && !mbar_wait(su32(bars + kTcStages + s), (round - 1) & 1, abort, true)) {
+        *abort = 1;
+        atomicExch(err, 1);
+        break;
       }
-      g.C[o] = v;
+      const uint32_t full = su32(bars + s);
+      mbar_expect_tx(full, (uint32_t)kTcStage);
+      const uint32_t d = su32(base + s * kTcStage);
+      tma_load(d, &ah, full, kb * 64, i0);
+      tma_load(d + kTcBox, &al, full, kb * 64, i0);
+      tma_load(d + 2 * kTcBox, &bh, full, kb * 64, j0);
+      tma_load(d + 3 * kTcBox, &bl, full, kb * 64, j0);
+      ++issued;
+    }
+    for (int kb = (issued > kTcStages ? issued - kTcStages : 0); kb < issued; ++kb)
+      mbar_wait(su32(bars + kb % kTcStages), (kb / kTcStages) & 1, abort, false);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t id = idesc<true>(min(128, (g.N - j0 + 15) / 16 * 16));
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kTcStages, round = kb / kTcStages;
+      if (!mbar_wait(su32(bars + s), round & 1, abort, true)) {
+        *abort = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = su32(base + s * kTcStage);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t xa = a0 + k * 32, xb = a0 + 2 * kTcBox + k * 32;
+        mma<true>(tmem, sdesc(xa), sdesc(xb), id, (kb > 0 || k > 0) ? 1u : 0u);
+        mma<true>(tmem, sdesc(xa), sdesc(xb + kTcBox), id, 1u);
+        mma<true>(tmem, sdesc(xa + kTcBox), sdesc(xb), id, 1u);
+      }
+      mma_commit(su32(bars + kTcStages + s));
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+
+  const bool ok = mbar_wait(done, 0, abort, false);
+  tc_fence_after();
+  if (__all_sync(0xffffffffu, ok && !*abort)) {
+    float* stg = reinterpret_cast<float*>(base) + warp * 32 * 33;
+    const int row0 = i0 + warp * 32;
+#pragma unroll 1
+    for (int c = 0; c < 4 && j0 + c * 32 < g.N; ++c) {  // uniform over the warp
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = __uint_as_float(v[q]);
+      __syncwarp();
+      const int j = j0 + c * 32 + lane;
+      if (j < g.N) {
+        const float bj = (g.mode <= 1) ? g.bias[j] : 0.f;
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+          const int i = row0 + rr;
+          if (i >= g.M) break;
+          const int64_t o = (int64_t)i * g.ldc + j;
+          float x = stg[rr * 33 + lane];
+          if (g.mode == 0) {
+            x += bj;
+          } else if (g.mode == 1) {
+            x += bj;
+            g.Z[o] = x;
+            x = gelu_f(x);
+          } else if (g.mode == 2) {
+            x *= gelu_df(g.Zprev[o]);
+          }
+          g.C[o] = x;
+        }
+      }
+      __syncwarp();
+    }
+  } else if (threadIdx.x == 0) {
+    atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+  }
+}
+
+// BF16 head / remainder planes of an FP32 [rows][cols] array (row stride
+// lds): hi[r ld + c] = bf16(x), lo[r ld + c] = bf16(x - hi) (0 when zero_lo,
+// for BF16-exact weights), and, when hiT is not NULL, the same planes of the
+// transpose, hiT[c ldt + r].  32 x 32 tiles through shared memory keep both
+// the row and the transposed stores coalesced; block (32, 8).
+__global__ void __launch_bounds__(256) k_planes(const float* __restrict__ src, int rows, int cols, int64_t lds,
+                                                __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                                int64_t ld, __nv_bfloat16* __restrict__ hiT,
+                                                __nv_bfloat16* __restrict__ loT, int64_t ldt, int zero_lo) {
+  __shared__ __nv_bfloat16 sh[32][33], sl[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int rr = threadIdx.y; rr < 32; rr += 8) {
+    const int r = r0 + rr, c = c0 + threadIdx.x;
+    __nv_bfloat16 h = __float2bfloat16_rn(0.f), l = h;
+    if (r < rows && c < cols) {
+      const float x = src[(int64_t)r * lds + c];
+      h = __float2bfloat16_rn(x);
+      l = zero_lo ? __float2bfloat16_rn(0.f) : __float2bfloat16_rn(x - __bfloat162float(h));
+      hi[(int64_t)r * ld + c] = h;
+      lo[(int64_t)r * ld + c] = l;
+    }
+    sh[rr][threadIdx.x] = h;
+    sl[rr][threadIdx.x] = l;
+  }
+  if (!hiT) return;  // uniform
+  __syncthreads();
+  for (int cc = threadIdx.y; cc < 32; cc += 8) {
+    const int c = c0 + cc, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) {
+      hiT[(int64_t)c * ldt + r] = sh[threadIdx.x][cc];
+      loT[(int64_t)c * ldt + r] = sl[threadIdx.x][cc];
     }
   }
 }
@@ -158,7 +273,7 @@ __global__ void k_colsum(const float* dZ, int B, int N, float* gb) {
 }
 
 __global__ void k_adam(int64_t np, float* p, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
-                       float c1, float c2, __nv_bfloat16* pb) {
+                       float c1, float c2) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
   const float gi = g[i];
@@ -168,14 +283,11 @@ __global__ void k_adam(int64_t np, float* p, const float* g, float* m, float* v,
   v[i] = vi;
   const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
   p[i] = pi;
-  if (pb) pb[i] = __float2bfloat16_rn(pi);
 }
 
-__global__ void k_d2f(const double* x, int64_t n, float* y, __nv_bfloat16* yb) {
+__global__ void k_d2f(const double* x, int64_t n, float* y) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  y[i] = (float)x[i];
-  if (yb) yb[i] = __float2bfloat16_rn((float)x[i]);
+  if (i < n) y[i] = (float)x[i];
 }
 __global__ void k_f2d(const float* x, int64_t n, double* y, double scale) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -194,6 +306,9 @@ __global__ void k_warm(const float* Y, int B, int dL, int nmu, int nu, float ysc
 }
 
 }  // namespace
+}  // namespace gnm
+
+using namespace gnm;
 
 struct gnmppi_mlp_s {
   int L = 0;
@@ -204,12 +319,25 @@ struct gnmppi_mlp_s {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
-  __nv_bfloat16* pb = nullptr;
   float *xmean = nullptr, *xstd = nullptr;
   float yscale = 1.f;
   float* H[kMaxLayers + 1] = {nullptr};  // activations (H[0] = normalised input)
   float* Z[kMaxLayers + 1] = {nullptr};  // pre-activations
   float *dA = nullptr, *dB = nullptr;    // gradient ping-pong buffers
+  // BF16 head / remainder planes of the tensor-core operands: activations
+  // H_l [B][ldh l] and their transposes [d_l][ldb] (l < L), weights W_l
+  // [d_l][ldh l-1] and their transposes [d_{l-1}][ldh l], output gradients
+  // dZ [B][ldd] and their transposes [d][ldb]
+  __nv_bfloat16 *Hh[kMaxLayers + 1] = {nullptr}, *Hl[kMaxLayers + 1] = {nullptr};
+  __nv_bfloat16 *HTh[kMaxLayers + 1] = {nullptr}, *HTl[kMaxLayers + 1] = {nullptr};
+  __nv_bfloat16 *Wh[kMaxLayers + 1] = {nullptr}, *Wl[kMaxLayers + 1] = {nullptr};
+  __nv_bfloat16 *WTh[kMaxLayers + 1] = {nullptr}, *WTl[kMaxLayers + 1] = {nullptr};
+  __nv_bfloat16 *dZh = nullptr, *dZl = nullptr, *dZTh = nullptr, *dZTl = nullptr;
+  int64_t ldh[kMaxLayers + 1] = {0};
+  int64_t ldb = 0, ldd = 0;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  int* d_err = nullptr;  // a bounded wait of the tensor-core GEMM ran out
+  int* h_err = nullptr;  // pinned copy
   double *loss_b = nullptr, *loss = nullptr;
   int t = 0;
   std::vector<void*> allocs;
@@ -253,6 +381,7 @@ extern "C" void gnmppi_mlp_destroy(gnmppi_mlp_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void* q : h->allocs) cudaFree(q);
+  if (h->h_err) cudaFreeHost(h->h_err);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -305,7 +434,6 @@ extern "C" gnmppi_status gnmppi_mlp_create(int32_t nlayers, const int32_t* dims,
   MA(h->g, 4 * np);
   MA(h->m, 4 * np);
   MA(h->v, 4 * np);
-  MA(h->pb, 2 * np);
   MA(h->xmean, 4 * (size_t)dims[0]);
   MA(h->xstd, 4 * (size_t)dims[0]);
   int maxd = 0;
@@ -316,9 +444,45 @@ extern "C" gnmppi_status gnmppi_mlp_create(int32_t nlayers, const int32_t* dims,
   }
   MA(h->dA, 4 * (size_t)max_batch * maxd);
   MA(h->dB, 4 * (size_t)max_batch * maxd);
+  // BF16 operand planes; row strides rounded up to 8 values (16 bytes, the TMA stride rule)
+  auto r8 = [](int64_t x) { return (x + 7) / 8 * 8; };
+  h->ldb = r8(max_batch);
+  h->ldd = r8(maxd);
+  for (int l = 0; l <= nlayers; ++l) h->ldh[l] = r8(dims[l]);
+  for (int l = 0; l < nlayers; ++l) {
+    MA(h->Hh[l], 2 * (size_t)max_batch * h->ldh[l]);
+    MA(h->Hl[l], 2 * (size_t)max_batch * h->ldh[l]);
+    MA(h->HTh[l], 2 * (size_t)dims[l] * h->ldb);
+    MA(h->HTl[l], 2 * (size_t)dims[l] * h->ldb);
+  }
+  for (int l = 1; l <= nlayers; ++l) {
+    MA(h->Wh[l], 2 * (size_t)dims[l] * h->ldh[l - 1]);
+    MA(h->Wl[l], 2 * (size_t)dims[l] * h->ldh[l - 1]);
+    MA(h->WTh[l], 2 * (size_t)dims[l - 1] * h->ldh[l]);
+    MA(h->WTl[l], 2 * (size_t)dims[l - 1] * h->ldh[l]);
+  }
+  MA(h->dZh, 2 * (size_t)max_batch * h->ldd);
+  MA(h->dZl, 2 * (size_t)max_batch * h->ldd);
+  MA(h->dZTh, 2 * (size_t)maxd * h->ldb);
+  MA(h->dZTl, 2 * (size_t)maxd * h->ldb);
+  MA(h->d_err, sizeof(int));
   MA(h->loss_b, 8 * (size_t)max_batch);
   MA(h->loss, 8);
 #undef MA
+  {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn ||
+        cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) != cudaSuccess ||
+        cudaMallocHost((void**)&h->h_err, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      gnmppi_mlp_destroy(h);
+      return mfail(nullptr, GNMPPI_E_CUDA, "tensor-core GEMM set-up failed (cuTensorMapEncodeTiled, shared memory)");
+    }
+    h->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    *h->h_err = 0;
+  }
   std::vector<float> one(dims[0], 1.f);
   if (cudaMemcpyAsync(h->xstd, one.data(), 4 * one.size(), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -331,8 +495,9 @@ extern "C" gnmppi_status gnmppi_mlp_create(int32_t nlayers, const int32_t* dims,
 
 extern "C" int64_t gnmppi_mlp_num_params(gnmppi_mlp_t h) { return h ? h->np : 0; }
 
-static gnmppi_status to_device_f(gnmppi_mlp_t h, int32_t mem, const double* src, int64_t n, float* dst,
-                                 __nv_bfloat16* dstb) {
+static gnmppi_status refresh_weights(gnmppi_mlp_t h);
+
+static gnmppi_status to_device_f(gnmppi_mlp_t h, int32_t mem, const double* src, int64_t n, float* dst) {
   const double* dsrc = src;
   double* tmp = nullptr;
   if (mem == GNMPPI_MEM_HOST) {
@@ -340,7 +505,7 @@ static gnmppi_status to_device_f(gnmppi_mlp_t h, int32_t mem, const double* src,
     MCK(cudaMemcpyAsync(tmp, src, 8 * (size_t)n, cudaMemcpyHostToDevice, h->stream));
     dsrc = tmp;
   }
-  k_d2f<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(dsrc, n, dst, dstb);
+  k_d2f<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(dsrc, n, dst);
   MCKL();
   if (tmp) MCK(cudaFreeAsync(tmp, h->stream));
   MCK(cudaStreamSynchronize(h->stream));
@@ -350,8 +515,9 @@ static gnmppi_status to_device_f(gnmppi_mlp_t h, int32_t mem, const double* src,
 extern "C" gnmppi_status gnmppi_mlp_set_params(gnmppi_mlp_t h, int32_t mem, const double* params, int64_t count) {
   if (!h || !params) return mfail(h, GNMPPI_E_ARG, "NULL argument");
   if (count != h->np) return mfail(h, GNMPPI_E_ARG, "expected %lld parameters", (long long)h->np);
-  gnmppi_status st = to_device_f(h, mem, params, count, h->p, h->pb);
+  gnmppi_status st = to_device_f(h, mem, params, count, h->p);
   if (st != GNMPPI_OK) return st;
+  if ((st = refresh_weights(h)) != GNMPPI_OK) return st;
   MCK(cudaMemsetAsync(h->m, 0, 4 * (size_t)h->np, h->stream));
   MCK(cudaMemsetAsync(h->v, 0, 4 * (size_t)h->np, h->stream));
   h->t = 0;
@@ -391,28 +557,88 @@ extern "C" gnmppi_status gnmppi_mlp_set_normalization(gnmppi_mlp_t h, const doub
   return GNMPPI_OK;
 }
 
-static void gemm(gnmppi_mlp_t h, const MlpGemm& g, bool weights_b) {
-  dim3 grid((g.N + 63) / 64, (g.M + 63) / 64);
-  if (weights_b && h->bf16)
-    k_mlp_gemm<__nv_bfloat16><<<grid, 256, 0, h->stream>>>(g);
-  else
-    k_mlp_gemm<float><<<grid, 256, 0, h->stream>>>(g);
+// K-major BF16 plane [rows][ld] as a TMA operand: boxes of 64 values x 128
+// rows, 128-byte swizzle, zero fill outside the `cols` x `rows` extent.
+static bool encode_plane(gnmppi_mlp_t h, CUtensorMap* m, const __nv_bfloat16* p, int64_t cols, int64_t rows,
+                         int64_t ld) {
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {64, 128};
+  cuuint32_t estr[2] = {1, 1};
+  return h->encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(p), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Forward pass of B samples already in device memory (FP64), outputs in H[L].
-static gnmppi_status forward(gnmppi_mlp_t h, const double* dX, int B) {
+// C = A B^T on the tensor cores: A [M][K] (planes Ah, Al, row stride lda),
+// B [N][K] (planes Bh, Bl, row stride ldb); g carries C, the epilogue and M, N, K.
+static gnmppi_status tc_gemm(gnmppi_mlp_t h, const __nv_bfloat16* Ah, const __nv_bfloat16* Al, int64_t lda,
+                             const __nv_bfloat16* Bh, const __nv_bfloat16* Bl, int64_t ldb, MlpTc g) {
+  CUtensorMap m[4];
+  if (!encode_plane(h, &m[0], Ah, g.K, g.M, lda) || !encode_plane(h, &m[1], Al, g.K, g.M, lda) ||
+      !encode_plane(h, &m[2], Bh, g.K, g.N, ldb) || !encode_plane(h, &m[3], Bl, g.K, g.N, ldb))
+    return mfail(h, GNMPPI_E_CUDA, "cuTensorMapEncodeTiled failed (MLP operand)");
+  dim3 grid((unsigned)((g.N + 127) / 128), (unsigned)((g.M + 127) / 128));
+  k_mlp_tc<<<grid, 128, kTcSmem, h->stream>>>(m[0], m[1], m[2], m[3], g, h->d_err);
+  MCKL();
+  return GNMPPI_OK;
+}
+
+// Head / remainder planes (and, with hiT, those of the transpose) of an FP32 array.
+static gnmppi_status planes(gnmppi_mlp_t h, const float* src, int rows, int cols, int64_t lds, __nv_bfloat16* hi,
+                            __nv_bfloat16* lo, int64_t ld, __nv_bfloat16* hiT, __nv_bfloat16* loT, int64_t ldt,
+                            int zero_lo) {
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  k_planes<<<grid, dim3(32, 8), 0, h->stream>>>(src, rows, cols, lds, hi, lo, ld, hiT, loT, ldt, zero_lo);
+  MCKL();
+  return GNMPPI_OK;
+}
+
+// Weight planes W_l and W_l^T from the FP32 master parameters (the
+// remainder plane is zero when the products use BF16-rounded weights).
+static gnmppi_status refresh_weights(gnmppi_mlp_t h) {
+  for (int l = 1; l <= h->L; ++l) {
+    const int din = h->dims[l - 1], dout = h->dims[l];
+    gnmppi_status st = planes(h, h->p + h->off[l], dout, din, din, h->Wh[l], h->Wl[l], h->ldh[l - 1], h->WTh[l],
+                              h->WTl[l], h->ldh[l], h->bf16);
+    if (st != GNMPPI_OK) return st;
+  }
+  return GNMPPI_OK;
+}
+
+// The tensor-core error word: copied to pinned memory and cleared on the
+// stream (before the caller's final synchronisation), then checked.
+static gnmppi_status fetch_err(gnmppi_mlp_t h) {
+  MCK(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  MCK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+  return GNMPPI_OK;
+}
+static gnmppi_status check_err(gnmppi_mlp_t h) {
+  if (*h->h_err) {
+    *h->h_err = 0;
+    return mfail(h, GNMPPI_E_TIMEOUT, "a bounded wait in the MLP's tensor-core GEMM ran out");
+  }
+  return GNMPPI_OK;
+}
+static gnmppi_status finish(gnmppi_mlp_t h) {
+  gnmppi_status st = fetch_err(h);
+  if (st != GNMPPI_OK) return st;
+  MCK(cudaStreamSynchronize(h->stream));
+  return check_err(h);
+}
+
+// Forward pass of B samples already in device memory (FP64), outputs in H[L];
+// `train` also writes the transposed activation planes the weight gradients use.
+static gnmppi_status forward(gnmppi_mlp_t h, const double* dX, int B, bool train) {
   const int d0 = h->dims[0];
   k_mlp_input<<<(unsigned)(((int64_t)B * d0 + 255) / 256), 256, 0, h->stream>>>(dX, B, d0, h->xmean, h->xstd, h->H[0]);
   MCKL();
+  gnmppi_status st = planes(h, h->H[0], B, d0, d0, h->Hh[0], h->Hl[0], h->ldh[0], train ? h->HTh[0] : nullptr,
+                            h->HTl[0], h->ldb, 0);
+  if (st != GNMPPI_OK) return st;
   for (int l = 1; l <= h->L; ++l) {
     const int din = h->dims[l - 1], dout = h->dims[l];
-    MlpGemm g{};
-    g.A = h->H[l - 1];
-    g.a_i = din;
-    g.a_k = 1;
-    g.B = h->bf16 ? (const void*)(h->pb + h->off[l]) : (const void*)(h->p + h->off[l]);
-    g.b_j = din;
-    g.b_k = 1;
+    MlpTc g{};
     g.C = h->H[l];
     g.ldc = dout;
     g.M = B;
@@ -421,15 +647,20 @@ static gnmppi_status forward(gnmppi_mlp_t h, const double* dX, int B) {
     g.bias = h->p + h->off[l] + (int64_t)dout * din;
     g.Z = h->Z[l];
     g.mode = (l < h->L) ? 1 : 0;
-    gemm(h, g, true);
-    MCKL();
+    if ((st = tc_gemm(h, h->Hh[l - 1], h->Hl[l - 1], h->ldh[l - 1], h->Wh[l], h->Wl[l], h->ldh[l - 1], g)) !=
+        GNMPPI_OK)
+      return st;
+    if (l < h->L &&
+        (st = planes(h, h->H[l], B, dout, dout, h->Hh[l], h->Hl[l], h->ldh[l], train ? h->HTh[l] : nullptr,
+                     h->HTl[l], h->ldb, 0)) != GNMPPI_OK)
+      return st;
   }
   return GNMPPI_OK;
 }
 
 // Loss and gradient of B samples (device FP64 inputs) into h->g and h->loss.
 static gnmppi_status loss_grad(gnmppi_mlp_t h, const double* dX, const double* dT, int B) {
-  gnmppi_status st = forward(h, dX, B);
+  gnmppi_status st = forward(h, dX, B, true);
   if (st != GNMPPI_OK) return st;
   const int L = h->L, dL = h->dims[L];
   k_mlp_nll<<<(B + 127) / 128, 128, 0, h->stream>>>(h->H[L], B, dL, h->nmu, h->nu, dT, h->dA, h->loss_b);
@@ -438,35 +669,23 @@ static gnmppi_status loss_grad(gnmppi_mlp_t h, const double* dX, const double* d
   MCKL();
   float* dz = h->dA;  // dL/dz of layer l
   float* other = h->dB;
+  if ((st = planes(h, dz, B, dL, dL, h->dZh, h->dZl, h->ldd, h->dZTh, h->dZTl, h->ldb, 0)) != GNMPPI_OK) return st;
   for (int l = L; l >= 1; --l) {
     const int din = h->dims[l - 1], dout = h->dims[l];
-    // gW[o][i] = sum_b dz[b][o] h_{l-1}[b][i]
-    MlpGemm gw{};
-    gw.A = dz;
-    gw.a_i = 1;
-    gw.a_k = dout;
-    gw.B = h->H[l - 1];
-    gw.b_j = 1;
-    gw.b_k = din;
+    // gW[o][i] = sum_b dz[b][o] h_{l-1}[b][i]: the transposed planes, K = B
+    MlpTc gw{};
     gw.C = h->g + h->off[l];
     gw.ldc = din;
     gw.M = dout;
     gw.N = din;
     gw.K = B;
     gw.mode = 3;
-    gemm(h, gw, false);
-    MCKL();
+    if ((st = tc_gemm(h, h->dZTh, h->dZTl, h->ldb, h->HTh[l - 1], h->HTl[l - 1], h->ldb, gw)) != GNMPPI_OK) return st;
     k_colsum<<<(dout + 127) / 128, 128, 0, h->stream>>>(dz, B, dout, h->g + h->off[l] + (int64_t)dout * din);
     MCKL();
     if (l > 1) {
       // dz_{l-1}[b][i] = (sum_o dz[b][o] W[o][i]) * GELU'(z_{l-1}[b][i])
-      MlpGemm gx{};
-      gx.A = dz;
-      gx.a_i = dout;
-      gx.a_k = 1;
-      gx.B = h->bf16 ? (const void*)(h->pb + h->off[l]) : (const void*)(h->p + h->off[l]);
-      gx.b_j = 1;
-      gx.b_k = din;
+      MlpTc gx{};
       gx.C = other;
       gx.ldc = din;
       gx.M = B;
@@ -474,8 +693,9 @@ static gnmppi_status loss_grad(gnmppi_mlp_t h, const double* dX, const double* d
       gx.K = dout;
       gx.Zprev = h->Z[l - 1];
       gx.mode = 2;
-      gemm(h, gx, true);
-      MCKL();
+      if ((st = tc_gemm(h, h->dZh, h->dZl, h->ldd, h->WTh[l], h->WTl[l], h->ldh[l], gx)) != GNMPPI_OK) return st;
+      if ((st = planes(h, other, B, din, din, h->dZh, h->dZl, h->ldd, h->dZTh, h->dZTl, h->ldb, 0)) != GNMPPI_OK)
+        return st;
       float* tmp = dz;
       dz = other;
       other = tmp;
@@ -503,7 +723,7 @@ extern "C" gnmppi_status gnmppi_mlp_forward(gnmppi_mlp_t h, int32_t mem, const d
   double* tx;
   gnmppi_status st = stage_in(h, mem, X, (int64_t)B * h->dims[0], &dX, &tx);
   if (st != GNMPPI_OK) return st;
-  if ((st = forward(h, dX, B)) != GNMPPI_OK) return st;
+  if ((st = forward(h, dX, B, false)) != GNMPPI_OK) return st;
   const int64_t n = (int64_t)B * h->dims[h->L];
   double* dY = Y;
   if (mem == GNMPPI_MEM_HOST) MCK(cudaMallocAsync((void**)&dY, 8 * (size_t)n, h->stream));
@@ -514,8 +734,7 @@ extern "C" gnmppi_status gnmppi_mlp_forward(gnmppi_mlp_t h, int32_t mem, const d
     MCK(cudaFreeAsync(dY, h->stream));
   }
   if (tx) MCK(cudaFreeAsync(tx, h->stream));
-  MCK(cudaStreamSynchronize(h->stream));
-  return GNMPPI_OK;
+  return finish(h);
 }
 
 extern "C" gnmppi_status gnmppi_mlp_loss_grad(gnmppi_mlp_t h, int32_t mem, const double* X, const double* T,
@@ -541,8 +760,7 @@ extern "C" gnmppi_status gnmppi_mlp_loss_grad(gnmppi_mlp_t h, int32_t mem, const
   if (loss) MCK(cudaMemcpyAsync(loss, h->loss, 8, cudaMemcpyDeviceToHost, h->stream));
   if (tx) MCK(cudaFreeAsync(tx, h->stream));
   if (tt) MCK(cudaFreeAsync(tt, h->stream));
-  MCK(cudaStreamSynchronize(h->stream));
-  return GNMPPI_OK;
+  return finish(h);
 }
 
 extern "C" gnmppi_status gnmppi_mlp_train_step(gnmppi_mlp_t h, int32_t mem, const double* X, const double* T,
@@ -560,13 +778,13 @@ extern "C" gnmppi_status gnmppi_mlp_train_step(gnmppi_mlp_t h, int32_t mem, cons
   const double b1 = 0.9, b2 = 0.999;
   const float c1 = (float)(1.0 - std::pow(b1, h->t)), c2 = (float)(1.0 - std::pow(b2, h->t));
   k_adam<<<(unsigned)((h->np + 255) / 256), 256, 0, h->stream>>>(h->np, h->p, h->g, h->m, h->v, (float)lr, (float)b1,
-                                                                 (float)b2, 1e-8f, c1, c2, h->pb);
+                                                                 (float)b2, 1e-8f, c1, c2);
   MCKL();
+  if ((st = refresh_weights(h)) != GNMPPI_OK) return st;
   if (loss) MCK(cudaMemcpyAsync(loss, h->loss, 8, cudaMemcpyDeviceToHost, h->stream));
   if (tx) MCK(cudaFreeAsync(tx, h->stream));
   if (tt) MCK(cudaFreeAsync(tt, h->stream));
-  MCK(cudaStreamSynchronize(h->stream));
-  return GNMPPI_OK;
+  return finish(h);
 }
 
 extern "C" gnmppi_status gnmppi_mlp_warm_start(gnmppi_mlp_t h, int32_t mem, const double* X, int32_t B,
@@ -578,7 +796,7 @@ extern "C" gnmppi_status gnmppi_mlp_warm_start(gnmppi_mlp_t h, int32_t mem, cons
   double* tx;
   gnmppi_status st = stage_in(h, mem, X, (int64_t)B * h->dims[0], &dX, &tx);
   if (st != GNMPPI_OK) return st;
-  if ((st = forward(h, dX, B)) != GNMPPI_OK) return st;
+  if ((st = forward(h, dX, B, false)) != GNMPPI_OK) return st;
   const int64_t n = (int64_t)B * h->nmu;
   double *dU = U0, *dS = sigma;
   if (mem == GNMPPI_MEM_HOST) {
@@ -595,6 +813,5 @@ extern "C" gnmppi_status gnmppi_mlp_warm_start(gnmppi_mlp_t h, int32_t mem, cons
     MCK(cudaFreeAsync(dS, h->stream));
   }
   if (tx) MCK(cudaFreeAsync(tx, h->stream));
-  MCK(cudaStreamSynchronize(h->stream));
-  return GNMPPI_OK;
+  return finish(h);
 }

@@ -74,7 +74,6 @@ template <typename T, typename S, bool ANTI>
 struct SampleEmit {
   S* col;        // this sample's column of dR at the stage's first row
   const T* r;    // nominal residual at the stage's first row
-  int64_t lo;    // offset of the remainder plane (BF16 storage)
   int ldK, par;
   bool active;
   T sign, csum, esum;
@@ -84,12 +83,12 @@ struct SampleEmit {
       const T vo = __shfl_xor_sync(0xffffffffu, v, 1);
       if (par == (i & 1)) {
         const T d = sign * (v - vo) * (T)0.5;
-        if (active) put(col + (int64_t)i * ldK, lo, d);
+        if (active) put(col + (int64_t)i * ldK, d);
         esum += d * r[i];
       }
     } else {
       const T d = v - r[i];
-      if (active) put(col + (int64_t)i * ldK, lo, d);
+      if (active) put(col + (int64_t)i * ldK, d);
       esum += d * r[i];
     }
   }
@@ -106,7 +105,7 @@ struct SampleEmit {
       const T got = __shfl_xor_sync(0xffffffffu, give, 1);
       const T d = sign * (own - got) * (T)0.5;
       const int row = i + par;
-      if (active) put(col + (int64_t)row * ldK, lo, d);
+      if (active) put(col + (int64_t)row * ldK, d);
       esum += d * r[row];
     } else {
       (*this)(i, v0);
@@ -153,7 +152,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
   S* dR = reinterpret_cast<S*>(a.dR) + I.o_dR + m;  // this sample's column
   S* Wm = reinterpret_cast<S*>(a.W) + I.o_W;
   Acc<T> cost, eacc;
-  SampleEmit<T, S, ANTI> em{dR, sR, I.lo, I.ldK, par, active, sign, (T)0, (T)0};
+  SampleEmit<T, S, ANTI> em{dR, sR, I.ldK, par, active, sign, (T)0, (T)0};
   const uint32_t mm = active ? (uint32_t)m : 0u;
   const int64_t stage_stride = (int64_t)Model::RPS * I.ldK;
   // Two controls per step (nu = 2) with antithetic pairs: the normals of steps
@@ -173,7 +172,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
         const int j = k * NU + c;
         const T w = (j == m) ? sS[j] * sqrtn : (T)0;
         u[c] = sU[j] + sign * w;
-        if (active && par == 0) put(Wm + (int64_t)j * I.ldK + m, I.lo, w);
+        if (active && par == 0) put(Wm + (int64_t)j * I.ldK + m, w);
       }
     } else if (SHARE) {
       if ((k & 1) == 0) {
@@ -194,7 +193,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
         const int j = k * NU + c;
         const T w = sS[j] * (c ? z1 : z0);
         u[c] = sU[j] + sign * w;
-        if (active && par == c) put(Wm + (int64_t)j * I.ldK + m, I.lo, w);
+        if (active && par == c) put(Wm + (int64_t)j * I.ldK + m, w);
       }
     } else {
 #pragma unroll
@@ -207,7 +206,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
         }
         const T w = sS[j] * ((j & 1) ? z1 : z0);
         u[c] = sU[j] + sign * w;
-        if (active && par == (ANTI ? (j & 1) : 0)) put(Wm + (int64_t)j * I.ldK + m, I.lo, w);
+        if (active && par == (ANTI ? (j & 1) : 0)) put(Wm + (int64_t)j * I.ldK + m, w);
       }
     }
     em.col = dR + k * stage_stride;
@@ -245,8 +244,8 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
     if (par == 0) a.e[I.o_C / 2 + m] = ok ? ev : 0.0;
     if (!ok) {  // dropped pair: its columns leave P and S
       const int rows = I.N * Model::RPS + Model::RT;
-      for (int row = par; row < rows; row += (ANTI ? 2 : 1)) put(dR + (int64_t)row * I.ldK + m, I.lo, (T)0);
-      for (int j = par; j < I.n; j += (ANTI ? 2 : 1)) put(Wm + (int64_t)j * I.ldK + m, I.lo, (T)0);
+      for (int row = par; row < rows; row += (ANTI ? 2 : 1)) put(dR + (int64_t)row * I.ldK + m, (T)0);
+      for (int j = par; j < I.n; j += (ANTI ? 2 : 1)) put(Wm + (int64_t)j * I.ldK + m, (T)0);
     }
   }
 }

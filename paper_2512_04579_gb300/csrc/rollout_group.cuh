@@ -332,7 +332,6 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   struct Em {
     S* dR;
     const T* r;  // interleaved nominal residual at the stage's first word
-    int64_t lo;  // offset of the remainder plane (BF16 storage)
     int ldK, m, base, own_w, ctl_w;
     bool active, plus;
     T sign, csum, esum;
@@ -345,10 +344,10 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
       const T own = plus ? v0 : v1;
       const int row = base + r0 + (plus ? 0 : 1);
       const T d = sign * (own - got) * (T)0.5;
-      if (active) put(dR + (int64_t)row * ldK + m, lo, d);
+      if (active) put(dR + (int64_t)row * ldK + m, d);
       esum += d * r[slot < FL ? 2 * G * slot + own_w : ctl_w];
     }
-  } em{dR, sR, I.lo, I.ldK, m, 0, 2 * lg + (plus ? 0 : 1), 2 * SL + (plus ? 0 : 1), active, plus, sign, (T)0, (T)0};
+  } em{dR, sR, I.ldK, m, 0, 2 * lg + (plus ? 0 : 1), 2 * SL + (plus ? 0 : 1), active, plus, sign, (T)0, (T)0};
   // The 2G lanes of a pair draw the normals of 2G consecutive steps at once
   // (lane l of the pair: Philox call q = k + l) and hand them round by shuffle.
   // Sigma points (Method E): pair m perturbs control m alone, by sqrt(n) s_m.
@@ -370,8 +369,8 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
     const T w0 = sS[2 * k] * z0, w1 = sS[2 * k + 1] * z1;
     const T u[2] = {sU[2 * k] + sign * w0, sU[2 * k + 1] + sign * w1};
     if (active && plus && lg == 0) {
-      put(Wm + (int64_t)(2 * k) * I.ldK + m, I.lo, w0);
-      put(Wm + (int64_t)(2 * k + 1) * I.ldK + m, I.lo, w1);
+      put(Wm + (int64_t)(2 * k) * I.ldK + m, w0);
+      put(Wm + (int64_t)(2 * k + 1) * I.ldK + m, w1);
     }
     em.base = k * rps;
     em.r = sR + k * RS;
@@ -409,8 +408,8 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   }
   if (active && plus && !ok) {  // dropped pair: its columns leave P and S
     const int rows = I.N * rps + 2 * I.F;
-    for (int row = lg; row < rows; row += G) put(dR + (int64_t)row * I.ldK + m, I.lo, (T)0);
-    for (int j = lg; j < I.n; j += G) put(Wm + (int64_t)j * I.ldK + m, I.lo, (T)0);
+    for (int row = lg; row < rows; row += G) put(dR + (int64_t)row * I.ldK + m, (T)0);
+    for (int j = lg; j < I.n; j += G) put(Wm + (int64_t)j * I.ldK + m, (T)0);
   }
 }
 

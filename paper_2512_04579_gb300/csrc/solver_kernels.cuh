@@ -105,25 +105,11 @@ __device__ __forceinline__ double block_min(double v, double* red) {
 // the DFMA rate).
 constexpr int kSoftminSplit = 2;  // CTAs per instance (each takes every other group of rows of W)
 
-// Four consecutive W entries as FP32 (16-byte FP32 or 8-byte BF16 load).
+// Four consecutive W entries as FP32 (one 16-byte load of FP32).
 __device__ __forceinline__ float4 load4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
-  const uint2 u = *reinterpret_cast<const uint2*>(p);
-  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u), __uint_as_float(u.y << 16),
-                     __uint_as_float(u.y & 0xFFFF0000u));
-}
 __device__ __forceinline__ float4 load4(const double* p) {
   return make_float4((float)p[0], (float)p[1], (float)p[2], (float)p[3]);
 }
-// Four W values of one row: BF16 storage adds the remainder plane (lo
-// elements further on) to the head, the other types hold the value itself.
-__device__ __forceinline__ float4 load4w(const float* p, int64_t) { return load4(p); }
-__device__ __forceinline__ float4 load4w(const double* p, int64_t) { return load4(p); }
-__device__ __forceinline__ float4 load4w(const __nv_bfloat16* p, int64_t lo) {
-  const float4 h = load4(p), l = load4(p + lo);
-  return make_float4(h.x + l.x, h.y + l.y, h.z + l.z, h.w + l.w);
-}
-
 template <typename S, typename TA>
 __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
   constexpr int CH = 2048;  // samples staged per chunk
@@ -242,15 +228,15 @@ __global__ void __launch_bounds__(256) k_softmin_wvec(SolveArgs a) {
           am += w * sw[m];
         }
       } else {
-        // four samples per lane and load (16 B of FP32, or 8 B from each BF16
-        // plane), so a row of 1024 samples is one batch of 8 independent loads per lane;
+        // four samples per lane and load (16 B of FP32 W), so a row of 1024
+        // samples is one batch of 8 independent loads per lane;
         // rows start 16-byte aligned (ldK and m0 are multiples of 64)
         const int m4 = (mc + 3) >> 2;
         const float4* se4 = reinterpret_cast<const float4*>(se);
         const float4* sw4 = reinterpret_cast<const float4*>(sw);
 #pragma unroll 8
         for (int q = lane; q < m4; q += 32) {
-          const float4 w = load4w(row + 4 * q, I.lo);
+          const float4 w = load4(row + 4 * q);
           const float4 ev = se4[q], wv = sw4[q];
           ag += w.x * ev.x + w.y * ev.y + w.z * ev.z + w.w * ev.w;
           am += w.x * wv.x + w.y * wv.y + w.z * wv.z + w.w * wv.w;

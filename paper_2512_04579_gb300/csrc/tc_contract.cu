@@ -10,12 +10,13 @@
 // accuracy (a single TF32 or BF16 pass does not: its operand rounding moves
 // the Gauss-Newton step, and the cost after it, by up to 1e-3 / 1e-2 at
 // 10^4 residual rows):
-//    BF16 mode (k_contract_tc): the rollouts store every operand as a BF16
-//      head plane and a BF16 remainder plane; one CTA computes a (128 or 256)
-//      x 256 output tile -- two 128-row sub-tiles when the instance has more
-//      than 128 unknowns, so that each B tile is streamed once for both --
-//      from three kind::f16 passes per product:
-//        warp 0 lane 0  issues TMA loads into a 3-stage shared-memory ring,
+//    BF16 mode (k_contract_tc): one CTA computes a (128 or 256) x 256
+//      output tile -- two 128-row sub-tiles when the instance has more than
+//      128 unknowns, so that each B tile is streamed once for both -- from
+//      three kind::f16 passes per product:
+//        warp 0 lane 0  issues TMA loads of FP32 k-blocks into a 3-stage ring,
+//        warps 2-5      rewrite each landed box in place as a BF16 head tile
+//                       and a BF16 remainder tile,
 //        warp 1 lane 0  issues tcgen05.mma (M=128, N <= 256, K=16) per
 //                       sub-tile into its own 256-column TMEM accumulator,
 //        warps 0-3      read TMEM back (tcgen05.ld 32x32b) and store FP32 rows
@@ -34,12 +35,14 @@
 //      entry of the symmetric output is written once.
 // Every mbarrier wait is bounded by the global timer; a wait that runs out
 // sets the plan's error word and the CTA winds down without a trap.
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <type_traits>
 
 #include "tc_contract.cuh"
+#include "tc_ptx.cuh"
 
 namespace gnm {
 
@@ -52,148 +55,74 @@ constexpr int A_BYTES = BM * ROW_BYTES;
 constexpr int B_BYTES = BN * ROW_BYTES;
 constexpr int RING_BYTES = 4 * (A_BYTES + B_BYTES);  // 192 KB of operand ring
 constexpr int TMEM_COLS = 256;
-constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
+// BF16 heads of two adjacent FP32 values (round to nearest even) and the
+// BF16 roundings of their remainders x - head (exact in FP32), each pair
+// packed as the 32-bit word a K-major row holds (first value in the low half).
+__device__ __forceinline__ void bf16_split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for the phase with the given parity; gives up after limit_ns or when
-// another role of the CTA has aborted (check_abort).
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort, bool check_abort,
-                                          unsigned long long limit_ns = WAIT_NS) {
-  const unsigned long long t0 = gtimer();
-  for (uint32_t i = 0;; ++i) {
-    if (mbar_try(a, parity)) return true;
-    if (check_abort && *abort) return false;
-    if ((i & 255u) == 255u && gtimer() - t0 > limit_ns) return false;
+// Row `row` (32 FP32 values) of a landed 128-byte-swizzled TMA tile at p:
+// 16-byte chunk c of the row sits at chunk c ^ (row & 7).
+__device__ __forceinline__ void load_row_sw128(const unsigned char* p, int row, float* v) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float4 q = *reinterpret_cast<const float4*>(p + row * 128 + ((c ^ (row & 7)) << 4));
+    v[4 * c] = q.x;
+    v[4 * c + 1] = q.y;
+    v[4 * c + 2] = q.z;
+    v[4 * c + 3] = q.w;
   }
 }
 
-// Test injection (gnmppi_debug_inject): the MMA issuer first waits, with a
-// short limit, on the stage-0 "empty" barrier, which only its own commits
-// complete -- a wait that nothing ends -- so that the give-up path runs:
-// abort flag, error word, the producer's drain of its copies in flight,
-// the epilogue skipped, TMEM released.
-constexpr unsigned long long INJECT_WAIT_NS = 20000000ull;  // 20 ms
-
-__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          dst),
-      "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row groups 1024 bytes apart (SBO), descriptor version 1.
-// ROW64: 64-byte swizzle, rows of 64 bytes, 8-row groups 512 bytes apart.
-template <bool ROW64 = false>
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)((ROW64 ? 512 : 1024) >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)(ROW64 ? 4 : 2) << 61;
-  return d;
-}
-
-// Instruction descriptor: FP32 accumulator, A/B format (1 = BF16 for
-// kind::f16, 2 = TF32 for kind::tf32), both K-major, N >> 3 and M >> 4.
-// n_mma: the tile's MMA width, a multiple of 16 in [16, BN] (narrower for the
-// last column tile of a job, so no MMA work goes to columns that are dropped).
-template <bool BF16>
-__device__ __forceinline__ uint32_t idesc(int n_mma) {
-  const uint32_t fmt = BF16 ? 1u : 2u;
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n_mma >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
-
-template <bool BF16>
-__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  if (BF16) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem),
-        "l"(a), "l"(b), "r"(id), "r"(acc)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem),
-        "l"(a), "l"(b), "r"(id), "r"(acc)
-        : "memory");
+// The head and remainder of those 32 values as row `row` of two K-major
+// BF16 tiles with 64-byte rows and the 64-byte swizzle (16-byte chunk j of
+// the row at chunk j ^ ((row >> 1) & 3)), the layout TMA would have written.
+__device__ __forceinline__ void store_row_sw64(unsigned char* hi, unsigned char* lo, int row, const float* v) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    uint4 H, L;
+    bf16_split2(v[8 * j], v[8 * j + 1], H.x, L.x);
+    bf16_split2(v[8 * j + 2], v[8 * j + 3], H.y, L.y);
+    bf16_split2(v[8 * j + 4], v[8 * j + 5], H.z, L.z);
+    bf16_split2(v[8 * j + 6], v[8 * j + 7], H.w, L.w);
+    const int off = row * 64 + ((j ^ ((row >> 1) & 3)) << 4);
+    *reinterpret_cast<uint4*>(hi + off) = H;
+    *reinterpret_cast<uint4*>(lo + off) = L;
   }
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-#define GNM_R32(x) "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]), "=r"(x[7]), \
-                   "=r"(x[8]), "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]), "=r"(x[13]), "=r"(x[14]),       \
-                   "=r"(x[15]), "=r"(x[16]), "=r"(x[17]), "=r"(x[18]), "=r"(x[19]), "=r"(x[20]), "=r"(x[21]),     \
-                   "=r"(x[22]), "=r"(x[23]), "=r"(x[24]), "=r"(x[25]), "=r"(x[26]), "=r"(x[27]), "=r"(x[28]),     \
-                   "=r"(x[29]), "=r"(x[30]), "=r"(x[31])
-
-// 32 consecutive TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : GNM_R32(v)
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // D[i][j] = sum_k A[i][k] B[j][k] for one (128 or 256) x 256 tile of one
 // contraction job (the BF16 mode); output columns >= ccut are stored cgap
-// further right.  Every operand is a head plane plus a remainder plane
-// (lo_rows rows further down the tensor map), and each product is formed
-// from three BF16 passes, head x head + head x remainder + remainder x head,
-// which keeps FP32-level accuracy (the dropped remainder x remainder term is
-// ~2^-18 relative); 32-value k-blocks of 64-byte rows keep the stage of both
-// planes at 64 KB, so the ring holds three.
-__global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __restrict__ maps,
-                                                        const TcJob* __restrict__ jobs, const InstState* __restrict__ st,
-                                                        const int4* __restrict__ tiles, float* __restrict__ D,
-                                                        int* __restrict__ err, int inject) {
-  constexpr bool BF16 = true;
-  constexpr int KBLK = 32;              // elements per k-block
-  constexpr int KSTEP = 16;             // elements per MMA
-  constexpr int NSUB = KBLK / KSTEP;    // MMAs per k-block, sub-tile and pass
-  constexpr int RB = 64;                // bytes of one operand row per k-block
-  constexpr int BOX = BM * RB;          // one 128-row TMA box
-  constexpr int PLANES = 2;             // head and remainder planes
+// further right.  TMA lands FP32 k-blocks (32 values, 128-byte rows) of up to
+// two 128-row A sub-tiles and the 256 B rows; four splitter warps rewrite
+// each landed 16 KB tile in place as a BF16 head tile and a BF16 remainder
+// tile (64-byte rows, 8 KB each; the B heads of both boxes fill the first B
+// box, their remainders the second), and each product is formed from three
+// BF16 passes, head x head + head x remainder + remainder x head, which keeps
+// FP32-level accuracy (the dropped remainder x remainder term is ~2^-18
+// relative).  192 threads: warp 0 lane 0 TMA, warp 1 lane 0 MMA, warps 2-5
+// split; warps 0-3 read TMEM back.
+constexpr int kContractThreads = 192;
+__global__ void __launch_bounds__(kContractThreads, 1) k_contract_tc(const CUtensorMap* __restrict__ maps,
+                                                                    const TcJob* __restrict__ jobs,
+                                                                    const InstState* __restrict__ st,
+                                                                    const int4* __restrict__ tiles,
+                                                                    float* __restrict__ D, int* __restrict__ err,
+                                                                    int inject) {
+  constexpr int KBLK = 32;              // FP32 elements per k-block (one 128-byte row)
+  constexpr int NSUB = 2;               // BF16 MMAs (K = 16, 32 bytes) per k-block, sub-tile and pass
+  constexpr int TILE = BM * ROW_BYTES;  // one landed 128-row FP32 box (16 KB)
+  constexpr int HALF = TILE / 2;        // one 128-row BF16 tile of 64-byte rows (8 KB)
   constexpr int MTMAX = 2;              // 128-row sub-tiles of A per tile (each its own accumulator)
-  constexpr int PLANE_BYTES = (MTMAX + 2) * BOX;  // A sub-tiles, then the two B boxes
-  constexpr int STAGE_BYTES = PLANES * PLANE_BYTES;
+  constexpr int STAGE_BYTES = (MTMAX + 2) * TILE;
   constexpr int STAGES = RING_BYTES / STAGE_BYTES;
+  constexpr int SPLITTERS = kContractThreads - 64;
   constexpr uint32_t TCOLS = MTMAX * TMEM_COLS;
   const int4 tl = tiles[blockIdx.x];
   const TcJob J = jobs[tl.x];
@@ -201,7 +130,7 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
   // so every B tile is streamed once for up to 256 output rows
   const int mt = tl.w;
   const int row_org = tl.y * mt * BM;
-  const uint32_t tx_bytes = (uint32_t)(PLANES * (mt + 2) * BOX);
+  const uint32_t tx_bytes = (uint32_t)((mt + 2) * TILE);
   if (st[J.inst].status != 0) return;  // uniform over the CTA, before any allocation
   const int nkb = J.nkb;
   const CUtensorMap* map = maps + J.map;
@@ -209,13 +138,21 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
-  // bars[0..S): full, bars[S..2S): empty, bars[2S]: done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  // bars[0..S): full (TMA landed), [S..2S): split (tiles rewritten),
+  // [2S..3S): empty (MMAs done with the stage), [3S]: done, [3S+1]: the
+  // splitters' rendezvous between reading a box and overwriting it
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 2 * STAGES + 1; ++s) mbar_init(su32(bars + s), 1);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(su32(bars + s), 1);
+      mbar_init(su32(bars + STAGES + s), SPLITTERS);
+      mbar_init(su32(bars + 2 * STAGES + s), 1);
+    }
+    mbar_init(su32(bars + 3 * STAGES), 1);
+    mbar_init(su32(bars + 3 * STAGES + 1), SPLITTERS);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -229,7 +166,8 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t done = su32(bars + 2 * STAGES);
+  const uint32_t done = su32(bars + 3 * STAGES);
+  // stage layout: A sub-tile 0, A sub-tile 1, B box 0, B box 1 (16 KB each)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
@@ -237,58 +175,95 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
     int issued = 0;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES, round = kb / STAGES;
-      if (kb >= STAGES && !mbar_wait(su32(bars + STAGES + s), (round - 1) & 1, abort, true)) {
+      if (kb >= STAGES && !mbar_wait(su32(bars + 2 * STAGES + s), (round - 1) & 1, abort, true)) {
         *abort = 1;
         atomicExch(err, 1);
         break;
       }
       const uint32_t full = su32(bars + s);
       mbar_expect_tx(full, tx_bytes);
+      const uint32_t a_dst = su32(base + s * STAGE_BYTES);
+      const uint32_t b_dst = a_dst + MTMAX * TILE;
       const int x = J.x0 + kb * KBLK;
-      for (int p = 0; p < PLANES; ++p) {
-        const uint32_t a_dst = su32(base + s * STAGE_BYTES + p * PLANE_BYTES);
-        const uint32_t b_dst = a_dst + MTMAX * BOX;
-        const int pr = p * J.lo_rows;
-        for (int q = 0; q < mt; ++q) tma_load(a_dst + q * BOX, map, full, x, pr + J.a_row0 + row_org + q * BM);
-        tma_load(b_dst, map, full, x, pr + J.b_row0 + tl.z * BN);
-        tma_load(b_dst + BOX, map, full, x, pr + J.b_row0 + tl.z * BN + BM);
-      }
+      for (int q = 0; q < mt; ++q) tma_load(a_dst + q * TILE, map, full, x, J.a_row0 + row_org + q * BM);
+      tma_load(b_dst, map, full, x, J.b_row0 + tl.z * BN);
+      tma_load(b_dst + TILE, map, full, x, J.b_row0 + tl.z * BN + BM);
       ++issued;
     }
     // every copy this thread issued has landed before the CTA may exit
     for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
       mbar_wait(su32(bars + kb % STAGES), (kb / STAGES) & 1, abort, false);
+  } else if (warp >= 2) {
+    // ---------------- splitters: thread t owns row t of every 128-row box
+    const int t = threadIdx.x - 64;
+    const uint32_t rv = su32(bars + 3 * STAGES + 1);
+    uint32_t rphase = 0;
+    // every splitter has read the box before any overwrites it: arrive
+    // (releasing this thread's reads), then a bounded wait for the phase
+    auto rendezvous = [&]() -> bool {
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rv) : "memory");
+      return mbar_wait(rv, (rphase++) & 1, abort, true);
+    };
+    bool alive = true;
+    for (int kb = 0; kb < nkb && alive; ++kb) {
+      const int s = kb % STAGES, round = kb / STAGES;
+      if (!mbar_wait(su32(bars + s), round & 1, abort, true)) {
+        alive = false;
+        break;
+      }
+      unsigned char* sb = base + s * STAGE_BYTES;
+      float v[2 * KBLK];
+      for (int q = 0; q < mt && alive; ++q) {
+        unsigned char* a = sb + q * TILE;
+        load_row_sw128(a, t, v);
+        if (!(alive = rendezvous())) break;
+        store_row_sw64(a, a + HALF, t, v);
+      }
+      if (!alive) break;
+      unsigned char* b0 = sb + MTMAX * TILE;
+      load_row_sw128(b0, t, v);
+      load_row_sw128(b0 + TILE, t, v + KBLK);
+      if (!(alive = rendezvous())) break;
+      store_row_sw64(b0, b0 + TILE, t, v);              // B row t
+      store_row_sw64(b0, b0 + TILE, t + BM, v + KBLK);  // B row 128 + t
+      // the generic-proxy writes become visible to the tensor core's reads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bars + STAGES + s)) : "memory");
+    }
+    if (!alive) {
+      *abort = 1;
+      atomicExch(err, 1);
+    }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     const int ncols = min(BN, J.Nc - tl.z * BN);  // columns of this tile that are kept
-    const uint32_t id = idesc<BF16>(min(BN, (ncols + 15) / 16 * 16));
-    if (inject && !mbar_wait(su32(bars + STAGES), 0, abort, true, INJECT_WAIT_NS)) {
+    const uint32_t id = idesc<true>(min(BN, (ncols + 15) / 16 * 16));
+    if (inject && !mbar_wait(su32(bars + 2 * STAGES), 0, abort, true, INJECT_WAIT_NS)) {
       *abort = 1;
       atomicExch(err, 1);
     }
     for (int kb = 0; kb < nkb && !*abort; ++kb) {
       const int s = kb % STAGES, round = kb / STAGES;
-      if (!mbar_wait(su32(bars + s), round & 1, abort, true)) {
+      if (!mbar_wait(su32(bars + STAGES + s), round & 1, abort, true)) {
         *abort = 1;
         atomicExch(err, 1);
         break;
       }
       tc_fence_after();
       const uint32_t a0 = su32(base + s * STAGE_BYTES);
-      const uint32_t b0 = a0 + MTMAX * BOX;
+      const uint32_t bh = a0 + MTMAX * TILE, bl = bh + TILE;
 #pragma unroll
       for (int k = 0; k < NSUB; ++k) {
-        // sub-tile q accumulates into TMEM columns [256 q, 256 q + 256); one
-        // MMA covers 32 bytes of K
+        // sub-tile q accumulates into TMEM columns [256 q, 256 q + 256)
         for (int q = 0; q < mt; ++q) {
           const uint32_t d = tmem + (uint32_t)(q * TMEM_COLS);
-          const uint32_t ah = a0 + q * BOX + k * 32, bh = b0 + k * 32;
-          mma<BF16>(d, sdesc<true>(ah), sdesc<true>(bh), id, (kb > 0 || k > 0) ? 1u : 0u);
-          mma<BF16>(d, sdesc<true>(ah), sdesc<true>(bh + PLANE_BYTES), id, 1u);
-          mma<BF16>(d, sdesc<true>(ah + PLANE_BYTES), sdesc<true>(bh), id, 1u);
+          const uint32_t ah = a0 + q * TILE + k * 32, al = ah + HALF;
+          mma<true>(d, sdesc<true>(ah), sdesc<true>(bh + k * 32), id, (kb > 0 || k > 0) ? 1u : 0u);
+          mma<true>(d, sdesc<true>(ah), sdesc<true>(bl + k * 32), id, 1u);
+          mma<true>(d, sdesc<true>(al), sdesc<true>(bh + k * 32), id, 1u);
         }
       }
-      mma_commit(su32(bars + STAGES + s));  // frees the stage once these MMAs have read it
+      mma_commit(su32(bars + 2 * STAGES + s));  // frees the stage once these MMAs have read it
     }
     mma_commit(done);  // accumulator complete (or every issued MMA retired, on abort)
   }
@@ -302,7 +277,9 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(const CUtensorMap* __res
   const bool ok = mbar_wait(done, 0, abort, false);
   tc_fence_after();
   // tcgen05.ld is warp-collective: the whole warp takes the same branch
-  if (__all_sync(0xffffffffu, ok && !*abort)) {
+  if (warp >= 4) {
+    // no TMEM lanes of their own
+  } else if (__all_sync(0xffffffffu, ok && !*abort)) {
     float* stg = reinterpret_cast<float*>(base) + warp * 32 * 33;
     float* out = D + J.out_off;
 #pragma unroll 1
@@ -576,20 +553,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode(std::string& err) {
   return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
 }
 
-// Rank-2 tensor map over rows of `cols` elements (row stride ld elements),
-// box = one k-block x 128 rows, zero fill outside: FP32 k-blocks of 128
-// bytes with the 128-byte swizzle, BF16 k-blocks of 64 bytes with the
-// 64-byte swizzle (32 values either way).
-static bool encode_rows(PFN_cuTensorMapEncodeTiled_v12000 encode, CUtensorMap* m, void* gaddr, bool bf16, int64_t cols,
-                        int64_t ld, int64_t rows) {
-  const size_t esz = bf16 ? 2 : 4;
+// Rank-2 FP32 tensor map over rows of `cols` elements (row stride ld
+// elements), box = one 128-byte k-block x 128 rows, 128-byte swizzle, zero
+// fill outside.
+static bool encode_rows(PFN_cuTensorMapEncodeTiled_v12000 encode, CUtensorMap* m, void* gaddr, int64_t cols, int64_t ld,
+                        int64_t rows) {
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
   cuuint32_t box[2] = {(cuuint32_t)KBLK_F32, (cuuint32_t)BM};
   cuuint32_t estr[2] = {1, 1};
-  return encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, gaddr, dims, strides,
-                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                bf16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, gaddr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -616,7 +590,6 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
   plan->bf16 = bf16;
   auto encode = get_encode(err);
   if (!encode) return GNMPPI_E_CUDA;
-  const size_t esz = bf16 ? 2 : 4;
   const int kblk = KBLK_F32;
   const int nb = (int)desc.size();
   std::vector<CUtensorMap> maps(3 * (size_t)nb);
@@ -632,15 +605,9 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
       err = "[P^T | S] rows are not 16-byte aligned";
       return GNMPPI_E_ARG;
     }
-    // contraction: one map over the instance's [dR; W] block (BF16: the head
-    // block and the remainder block after it, 2 (nR + n) rows)
-    const int lo_rows = bf16 ? d.nR + d.n : 0;
-    if (bf16 && d.lo != (int64_t)lo_rows * d.ldK) {
-      err = "BF16 remainder plane is not the block after the heads";
-      return GNMPPI_E_ARG;
-    }
-    if (!encode_rows(encode, &maps[b], reinterpret_cast<char*>(dRW) + esz * (size_t)d.o_dR, bf16, d.ldK, d.ldK,
-                     (int64_t)(d.nR + d.n) * (bf16 ? 2 : 1))) {
+    // contraction: one FP32 map over the instance's [dR; W] block
+    if (!encode_rows(encode, &maps[b], reinterpret_cast<char*>(dRW) + 4 * (size_t)d.o_dR, d.ldK, d.ldK,
+                     d.nR + d.n)) {
       err = "cuTensorMapEncodeTiled failed (contraction, instance " + std::to_string(b) + ")";
       return GNMPPI_E_CUDA;
     }
@@ -658,7 +625,6 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     jc.ldc = d.ldP;
     jc.ccut = d.nR;          // S columns of the output ...
     jc.cgap = d.sP - d.nR;   // ... start at sP
-    jc.lo_rows = lo_rows;
     if (bf16) {
       // (job, row tile, column tile, sub-tiles): up to 256 rows per tile, so
       // each B tile is streamed once
@@ -673,8 +639,8 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     }
     // Gram: FP32 maps over the P^T columns (nR) and the S columns (n) of [P^T | S]
     float* Pb = reinterpret_cast<float*>(P) + d.o_P;
-    if (!encode_rows(encode, &maps[nb + b], Pb, false, d.nR, d.ldP, d.n) ||
-        !encode_rows(encode, &maps[2 * nb + b], Pb + d.sP, false, d.n, d.ldP, d.n)) {
+    if (!encode_rows(encode, &maps[nb + b], Pb, d.nR, d.ldP, d.n) ||
+        !encode_rows(encode, &maps[2 * nb + b], Pb + d.sP, d.n, d.ldP, d.n)) {
       err = "cuTensorMapEncodeTiled failed (Gram, instance " + std::to_string(b) + ")";
       return GNMPPI_E_CUDA;
     }
@@ -754,8 +720,8 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
 cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float* P, cudaStream_t stream, int inject) {
   if (plan.ntiles_c == 0) return cudaSuccess;
   if (plan.bf16)
-    k_contract_tc<<<plan.ntiles_c, 128, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st, plan.d_tiles_c, P,
-                                                             plan.d_err, inject);
+    k_contract_tc<<<plan.ntiles_c, kContractThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
+                                                                          plan.d_tiles_c, P, plan.d_err, inject);
   else
     k_gram_tc<true><<<plan.ntiles_c, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
                                                                         plan.d_tiles_c, P, nullptr, plan.d_err, inject);

@@ -1,7 +1,8 @@
 // tc_contract.cuh -- host interface of the tensor-core Jacobian-reconstruction
 // contraction (Eq. 7 of arXiv 2512.04579): [P^T | S] = W^T [dR | W] per
-// instance on tcgen05 (TF32 operands, or BF16 head + remainder operands in
-// three passes; FP32 accumulation in TMEM), operands staged by TMA.  Internal.
+// instance on tcgen05 from FP32 operands staged by TMA and split in shared
+// memory into TF32 or BF16 head + remainder parts (three passes, FP32
+// accumulation in TMEM).  Internal.
 #pragma once
 #include <cuda.h>
 
@@ -25,7 +26,6 @@ struct TcJob {
   int64_t out_off;
   int32_t ldc, out_sel;
   int32_t ccut, cgap;
-  int32_t lo_rows, pad;  // BF16 contraction: map rows from a head row to its remainder row
 };
 
 struct TcPlan {
@@ -40,10 +40,9 @@ struct TcPlan {
   std::vector<void*> allocs;
 };
 
-// dRW: the combined per-instance [nR + n][ldK] operand block (FP32; or, when
-// bf16, a BF16 head block followed by its remainder block, d.lo elements
-// apart); P: the FP32 [P^T | S] array (S from column sP on).  Builds tensor
-// maps, jobs and tile lists.
+// dRW: the combined per-instance FP32 [nR + n][ldK] operand block; P: the
+// FP32 [P^T | S] array (S from column sP on); bf16 selects the contraction's
+// BF16 passes (otherwise TF32).  Builds tensor maps, jobs and tile lists.
 gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void* P, int bf16, cudaStream_t stream,
                              TcPlan* plan, std::string& err);
 
