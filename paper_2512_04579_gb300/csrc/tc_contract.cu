@@ -10,17 +10,18 @@
 // accuracy (a single TF32 or BF16 pass does not: its operand rounding moves
 // the Gauss-Newton step, and the cost after it, by up to 1e-3 / 1e-2 at
 // 10^4 residual rows):
-//    BF16 mode (k_contract_tc): one CTA computes a (128 or 256) x 256
-//      output tile -- two 128-row sub-tiles when the instance has more than
-//      128 unknowns, so that each B tile is streamed once for both -- from
-//      three kind::f16 passes per product:
+//    BF16 mode (k_contract_tc): one CTA computes the products of up to 256
+//      rows of the [dR; W] block (two 128-row sub-tiles, each with its own
+//      256-column TMEM accumulator) with up to 256 W rows, from three
+//      kind::f16 passes per product:
 //        warp 0 lane 0  issues TMA loads of FP32 k-blocks into a 3-stage ring,
 //        warps 2-5      rewrite each landed box in place as a BF16 head tile
 //                       and a BF16 remainder tile,
-//        warp 1 lane 0  issues tcgen05.mma (M=128, N <= 256, K=16) per
-//                       sub-tile into its own 256-column TMEM accumulator,
-//        warps 0-3      read TMEM back (tcgen05.ld 32x32b) and store FP32 rows
-//                       (the S columns from column sP on, 16-byte aligned);
+//        warp 1 lane 0  issues tcgen05.mma (M=128, N = the W rows, K=16) per
+//                       sub-tile,
+//        warps 0-3      read TMEM back (tcgen05.ld 32x32b, one lane per
+//                       [P^T | S] column) and store 32 consecutive columns
+//                       per warp store (the S columns from column sP on);
 //    FP32 mode: the three-pass TF32 kernel of (2) on the FP32 [dR; W] block.
 //  (2) k_gram_tc: the Gram product A = P^T P of Eq. 9 in FP32-level accuracy
 //      from three TF32 passes, A ~ Ph Ph^T + Ph Pl^T + Pl Ph^T with every FP32
@@ -97,10 +98,14 @@ __device__ __forceinline__ void store_row_sw64(unsigned char* hi, unsigned char*
   }
 }
 
-// D[i][j] = sum_k A[i][k] B[j][k] for one (128 or 256) x 256 tile of one
-// contraction job (the BF16 mode); output columns >= ccut are stored cgap
-// further right.  TMA lands FP32 k-blocks (32 values, 128-byte rows) of up to
-// two 128-row A sub-tiles and the 256 B rows; four splitter warps rewrite
+// One (128 or 256) x (up to 256) tile of the BF16 mode's contraction: the A
+// side is rows a_row0 + i of the instance's [dR; W] block (i < Nc, the
+// columns of [P^T | S]), the B side its W rows b_row0 + j (j < M = n), and
+// D[i][j] = sum_k A[i][k] B[j][k] is stored transposed, into row j and column
+// i of [P^T | S] (columns >= ccut cgap further right): one TMEM lane per
+// output column i, so each warp store writes 32 consecutive columns.  TMA
+// lands FP32 k-blocks (32 values, 128-byte rows) of up to two 128-row A
+// sub-tiles and up to 256 B rows; four splitter warps rewrite
 // each landed 16 KB tile in place as a BF16 head tile and a BF16 remainder
 // tile (64-byte rows, 8 KB each; the B heads of both boxes fill the first B
 // box, their remainders the second), and each product is formed from three
@@ -126,10 +131,9 @@ __global__ void __launch_bounds__(kContractThreads, 1) k_contract_tc(const CUten
   constexpr uint32_t TCOLS = MTMAX * TMEM_COLS;
   const int4 tl = tiles[blockIdx.x];
   const TcJob J = jobs[tl.x];
-  // tl.w: sub-tiles of this tile (1, or 2 when the job has more than 128 rows),
-  // so every B tile is streamed once for up to 256 output rows
+  // tl.y: block of 256 A rows, tl.z: block of 256 B rows, tl.w: A sub-tiles (1 or 2)
   const int mt = tl.w;
-  const int row_org = tl.y * mt * BM;
+  const int row_org = tl.y * MTMAX * BM;
   const uint32_t tx_bytes = (uint32_t)((mt + 2) * TILE);
   if (st[J.inst].status != 0) return;  // uniform over the CTA, before any allocation
   const int nkb = J.nkb;
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(kContractThreads, 1) k_contract_tc(const CUten
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    const int ncols = min(BN, J.Nc - tl.z * BN);  // columns of this tile that are kept
+    const int ncols = min(BN, J.M - tl.z * BN);  // W rows of this tile
     const uint32_t id = idesc<true>(min(BN, (ncols + 15) / 16 * 16));
     if (inject && !mbar_wait(su32(bars + 2 * STAGES), 0, abort, true, INJECT_WAIT_NS)) {
       *abort = 1;
@@ -269,37 +273,33 @@ __global__ void __launch_bounds__(kContractThreads, 1) k_contract_tc(const CUten
   }
   __syncwarp();
 
-  // ---------------- epilogue: TMEM -> registers -> shared -> coalesced rows of D
-  // Once `done` fires every stage has been consumed, so the operand ring is
-  // free: each warp transposes its 32 x 32 slices through a padded staging
-  // block and writes whole rows (lane = column) instead of one column of 32
-  // rows per store.
+  // ---------------- epilogue: TMEM -> registers -> rows of [P^T | S]
+  // Lane l of warp w holds A row i = row_org + 128 sub + 32 w + l, i.e.
+  // output column i; a 32-column TMEM load gives it 32 consecutive output
+  // rows j, and each store of the warp covers 32 consecutive columns.
   const bool ok = mbar_wait(done, 0, abort, false);
   tc_fence_after();
   // tcgen05.ld is warp-collective: the whole warp takes the same branch
   if (warp >= 4) {
     // no TMEM lanes of their own
   } else if (__all_sync(0xffffffffu, ok && !*abort)) {
-    float* stg = reinterpret_cast<float*>(base) + warp * 32 * 33;
     float* out = D + J.out_off;
+    const int jn = min(BN, J.M - tl.z * BN);  // output rows of this tile
 #pragma unroll 1
     for (int sub = 0; sub < mt; ++sub) {
-      const int row0 = row_org + sub * BM + warp * 32;
+      const int i = row_org + sub * BM + warp * 32 + lane;
+      const bool live = i < J.Nc;
+      const int colw = i < J.ccut ? i : i + J.cgap;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32 && tl.z * BN + c * 32 < J.Nc; ++c) {  // uniform: kept 32-column chunks
+      for (int c = 0; c * 32 < jn; ++c) {  // uniform over the warp
         uint32_t v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sub * TMEM_COLS + c * 32), v);
-#pragma unroll
-        for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = __uint_as_float(v[q]);
-        __syncwarp();
-        const int col = tl.z * BN + c * 32 + lane;
-        if (col < J.Nc) {
-          const int colw = col < J.ccut ? col : col + J.cgap;
-#pragma unroll 4
-          for (int rr = 0; rr < 32; ++rr)
-            if (row0 + rr < J.M) out[(int64_t)(row0 + rr) * J.ldc + colw] = stg[rr * 33 + lane];
+        const int j0 = tl.z * BN + c * 32;
+        if (live) {
+#pragma unroll 8
+          for (int jj = 0; jj < 32; ++jj)
+            if (c * 32 + jj < jn) out[(int64_t)(j0 + jj) * J.ldc + colw] = __uint_as_float(v[jj]);
         }
-        __syncwarp();
       }
     }
   } else if (threadIdx.x == 0) {
@@ -615,8 +615,10 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     jc = TcJob{};
     jc.inst = b;
     jc.map = b;
-    jc.a_row0 = d.nR;
-    jc.b_row0 = 0;
+    // BF16 kernel: A side = the [dR; W] rows, B side = the W rows; three-pass
+    // TF32 kernel: A side = the W rows, B side = the [dR; W] rows
+    jc.a_row0 = bf16 ? 0 : d.nR;
+    jc.b_row0 = bf16 ? d.nR : 0;
     jc.M = d.n;
     jc.Nc = d.nR + d.n;
     jc.nkb = d.ldK / kblk;
@@ -626,11 +628,11 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     jc.ccut = d.nR;          // S columns of the output ...
     jc.cgap = d.sP - d.nR;   // ... start at sP
     if (bf16) {
-      // (job, row tile, column tile, sub-tiles): up to 256 rows per tile, so
-      // each B tile is streamed once
-      const int mt = d.n > BM ? 2 : 1;
-      for (int i = 0; i < (d.n + mt * BM - 1) / (mt * BM); ++i)
-        for (int j = 0; j < (d.nR + d.n + BN - 1) / BN; ++j) tc.push_back(make_int4(b, i, j, mt));
+      // (job, block of 256 [dR; W] rows, block of 256 W rows, A sub-tiles);
+      // the W blocks of a row block adjacent (its A rows read once from HBM)
+      for (int i = 0; i * 2 * BM < d.nR + d.n; ++i)
+        for (int j = 0; j * BN < d.n; ++j)
+          tc.push_back(make_int4(b, i, j, d.nR + d.n - i * 2 * BM > BM ? 2 : 1));
     } else {
       // three-pass TF32 kernel: (job, first row, first column, 1), the row
       // tiles of a column block adjacent so that its B rows are read from L2
