@@ -42,7 +42,7 @@ DTYPE = "f32 rollouts, bf16 head+remainder contractions (3 passes, f32 accumulat
 
 # DRAM read + write of one k_samples launch of the default workload (256 instances), from one
 # full-size ncu capture of this command (one-pass metrics); null for other batch sizes.
-K_SAMPLES_TRAFFIC_B256 = 2.2790e9
+K_SAMPLES_TRAFFIC_B256 = 2.2802e9
 
 
 def load_cstar(path=CSTAR):
@@ -520,6 +520,8 @@ def run_gnmppi(args):
         if not args.no_uneven:
             out["uneven"] = uneven_arm(args, dev, stream)
         out["cpu_baseline"] = cpu_baseline(args)
+        if args.cpu_configs:
+            out["cpu_configs"] = cpu_configs(args)
         print(json.dumps(out))
     if world > 1:
         dist.barrier()
@@ -590,6 +592,65 @@ def cpu_baseline(args):
                            "sample": f"1 instance, 1 of {T} iterations, one thread"}}
 
 
+def cpu_configs(args):
+    """The oracle, as it stands, on this host's cores for the other
+    configurations (bounded samples, scaled, each stated): the pendulum
+    swing-up (one 20-iteration solve), the uneven batch (one iteration of 8 of
+    its 1024 instances, scaled to the batch and 30 iterations) and the
+    high-dimensional sweep (one iteration of one instance at K = 4096 per
+    chain size, scaled linearly in K: rollouts and the P / S sums are linear
+    in the sample count, the K-independent Jacobian / GGN work is a few %)."""
+    from oracle import oracle as O
+    from paper_2512_04579_gb300 import inputs as I
+
+    O.build()
+    cores = os.cpu_count() or 1
+    out = {"cores": cores, "kind": "oracle"}
+    # pendulum swing-up, FP64, N=50, K=256, 20 iterations
+    seed = I.BASE_SEED
+    x0 = I.pendulum_x0(seed, 1)[0]
+    m = O.pendulum(N=50)
+    res = {}
+    for th in (1, cores):
+        t0 = time.perf_counter()
+        O.solve(m, O.Options(K=256, iterations=20, lam=LAM, seed=seed, threads=th), x0, None, np.zeros(m.n), 0.5)
+        res[th] = time.perf_counter() - t0
+    out["pendulum"] = {"instance_solves_per_s_1thread": 1.0 / res[1], f"instance_solves_per_s_{cores}threads":
+                       1.0 / res[cores], "solves_per_s_to_gap": 0.0,
+                       "sample": "one 20-iteration solve of instance 0; none of the oracle's solves reach the 1e-6 gap"}
+    # uneven batch: one iteration of 8 instances
+    seed = I.BASE_SEED + 2
+    Ms, Ns, Ks, x0s, tgts = I.uneven_chain_instances(seed, 1024)
+    ts = []
+    for b in range(8):
+        mb = O.chain(M=int(Ms[b]), N=int(Ns[b]))
+        t0 = time.perf_counter()
+        O.iteration(mb, O.Options(K=int(Ks[b]), lam=LAM, seed=seed, threads=cores), x0s[b], tgts[b], np.zeros(mb.n),
+                    SIGMA0, inst=b)
+        ts.append(time.perf_counter() - t0)
+    t_inst = float(np.mean(ts)) * T  # one 30-iteration solve of an average instance
+    _, C_gn, Cs = load_cstar(CSTAR_UNEVEN)
+    frac = float(np.mean((C_gn - Cs) / Cs <= GAP))
+    out["uneven"] = {"solves_per_s": frac / t_inst, "instance_solves_per_s": 1.0 / t_inst,
+                     "sample": f"one iteration of instances 0-7 of the 1024, {cores} threads over samples; scaled by "
+                               f"30 iterations and the oracle's own solved fraction {frac:.3f}"}
+    # sweep: chain M in {16, 32, 64}, N = 200, one iteration at K = 4096
+    sw = []
+    seed = I.BASE_SEED + 4
+    for Mc in (16, 32, 64):
+        xs, tg = I.chain_instances(seed, 1, Mc)
+        mc = O.chain(M=Mc, N=200)
+        t0 = time.perf_counter()
+        O.iteration(mc, O.Options(K=4096, lam=LAM, seed=seed, threads=cores), xs[0], tg[0], np.zeros(mc.n), SIGMA0)
+        t = time.perf_counter() - t0
+        sw.append({"M": Mc, "N": 200, "K": 4096, "s_per_instance_iteration": t,
+                   "scaled": {str(Kc): t * Kc / 4096 for Kc in (4096, 16384, 65536)},
+                   "instance_iterations_per_s": {str(Kc): 4096 / (t * Kc) for Kc in (4096, 16384, 65536)}})
+    out["sweep"] = {"points": sw, "sample": f"one iteration of one instance at K = 4096, {cores} threads over "
+                                            "samples; K = 16384 and 65536 scaled linearly in K"}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -625,6 +686,8 @@ def main():
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch arm")
     ap.add_argument("--learned-eval", type=int, default=4096,
                     help="held-out instances of the second learned-warm-start evaluation (0: skip)")
+    ap.add_argument("--cpu-configs", action="store_true",
+                    help="also time the oracle on the pendulum, uneven-batch and sweep configurations")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

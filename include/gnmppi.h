@@ -358,6 +358,17 @@ int64_t gnmppi_mlp_num_params(gnmppi_mlp_t m);
 /* Copy parameters in (resets the Adam moments and step count) or out. */
 gnmppi_status gnmppi_mlp_set_params(gnmppi_mlp_t m, int32_t mem, const double* params, int64_t count);
 gnmppi_status gnmppi_mlp_get_params(gnmppi_mlp_t m, int32_t mem, double* params, int64_t count);
+/* Training checkpoint (the paper has no counterpart; the network itself is
+ * prior art, Sec. 1): the FP32 master parameters, Adam's first and second
+ * moments (count doubles each, in `mem` memory) and the step count.  Setting
+ * a state saved by get_state makes later train_step calls continue exactly
+ * where the saved handle would have (the state is held in FP32, so a round
+ * trip through doubles is exact).  Errors: E_ARG on NULL arrays, a count that
+ * is not the parameter count, or a negative step. */
+gnmppi_status gnmppi_mlp_get_state(gnmppi_mlp_t m, int32_t mem, double* params, double* m1, double* m2, int64_t count,
+                                   int32_t* step);
+gnmppi_status gnmppi_mlp_set_state(gnmppi_mlp_t m, int32_t mem, const double* params, const double* m1,
+                                   const double* m2, int64_t count, int32_t step);
 /* Input normalisation (host arrays of d_0) and the output scale: the network
  * is trained on the optimal controls divided by y_scale and warm-starts with U_0 = y_scale mu,
  * sigma = y_scale exp(s). */

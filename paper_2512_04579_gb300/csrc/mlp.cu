@@ -540,6 +540,47 @@ extern "C" gnmppi_status gnmppi_mlp_get_params(gnmppi_mlp_t h, int32_t mem, doub
   return GNMPPI_OK;
 }
 
+// Copy an FP32 device array out as doubles into `mem` memory.
+static gnmppi_status out_f(gnmppi_mlp_t h, int32_t mem, const float* src, int64_t n, double* dst_user) {
+  double* dst = dst_user;
+  if (mem == GNMPPI_MEM_HOST) MCK(cudaMallocAsync((void**)&dst, 8 * (size_t)n, h->stream));
+  k_f2d<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(src, n, dst, 1.0);
+  MCKL();
+  if (mem == GNMPPI_MEM_HOST) {
+    MCK(cudaMemcpyAsync(dst_user, dst, 8 * (size_t)n, cudaMemcpyDeviceToHost, h->stream));
+    MCK(cudaFreeAsync(dst, h->stream));
+  }
+  return GNMPPI_OK;
+}
+
+extern "C" gnmppi_status gnmppi_mlp_get_state(gnmppi_mlp_t h, int32_t mem, double* params, double* m1, double* m2,
+                                              int64_t count, int32_t* step) {
+  if (!h || !params || !m1 || !m2 || !step) return mfail(h, GNMPPI_E_ARG, "NULL argument");
+  if (count != h->np) return mfail(h, GNMPPI_E_ARG, "expected %lld parameters", (long long)h->np);
+  gnmppi_status st;
+  if ((st = out_f(h, mem, h->p, count, params)) != GNMPPI_OK) return st;
+  if ((st = out_f(h, mem, h->m, count, m1)) != GNMPPI_OK) return st;
+  if ((st = out_f(h, mem, h->v, count, m2)) != GNMPPI_OK) return st;
+  MCK(cudaStreamSynchronize(h->stream));
+  *step = h->t;
+  return GNMPPI_OK;
+}
+
+extern "C" gnmppi_status gnmppi_mlp_set_state(gnmppi_mlp_t h, int32_t mem, const double* params, const double* m1,
+                                              const double* m2, int64_t count, int32_t step) {
+  if (!h || !params || !m1 || !m2) return mfail(h, GNMPPI_E_ARG, "NULL argument");
+  if (count != h->np) return mfail(h, GNMPPI_E_ARG, "expected %lld parameters", (long long)h->np);
+  if (step < 0) return mfail(h, GNMPPI_E_ARG, "step must be >= 0");
+  gnmppi_status st;
+  if ((st = to_device_f(h, mem, params, count, h->p)) != GNMPPI_OK) return st;
+  if ((st = to_device_f(h, mem, m1, count, h->m)) != GNMPPI_OK) return st;
+  if ((st = to_device_f(h, mem, m2, count, h->v)) != GNMPPI_OK) return st;
+  if ((st = refresh_weights(h)) != GNMPPI_OK) return st;
+  MCK(cudaStreamSynchronize(h->stream));
+  h->t = step;
+  return GNMPPI_OK;
+}
+
 extern "C" gnmppi_status gnmppi_mlp_set_normalization(gnmppi_mlp_t h, const double* x_mean, const double* x_std,
                                                       double y_scale) {
   if (!h || !x_mean || !x_std) return mfail(h, GNMPPI_E_ARG, "NULL argument");

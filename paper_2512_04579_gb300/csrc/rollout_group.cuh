@@ -16,6 +16,7 @@ namespace gnm {
 template <typename T, int FL, int G>
 struct ChainGroup {
   static constexpr int NXL = 4 * FL;  // lane-local state: p (2FL), v (2FL)
+  static constexpr bool kRelative = false;  // positions are absolute
   T mass_inv, k, k3, c, g, l0, h, h2, h6;
   int F, lg;
   unsigned mask;  // lanes that execute this group's shuffles together
@@ -34,6 +35,7 @@ struct ChainGroup {
     h6 = (T)(cs.dt / 6.0);
   }
   __device__ __forceinline__ int mass(int j) const { return lg * FL + j + 1; }  // 1-based global index
+  __device__ __forceinline__ void set_reference(const double*) {}
   __device__ __forceinline__ void accel(const T* s, const T* u, T* acc) const {
     const T* v = s + 2 * FL;
     // position of the mass before this lane's first one (origin for lane 0)
@@ -141,12 +143,21 @@ struct ChainGroup {
 };
 
 // FP32 group chain on paired FP32 instructions (FFMA2 / FADD2 / FMUL2),
-// 1/m folded into the constants; same interface and layout as above.
+// 1/m folded into the constants; same interface and layout as above, except
+// that positions are kept relative to the instance's initial positions (the
+// reference): a hanging chain of M masses is some 3M m long, so absolute FP32
+// positions carry ~3M u m of rounding and every link vector would be the
+// difference of two large numbers.  Here a link vector is its reference
+// vector (formed in FP64, rounded once) plus the difference of two small
+// deviations, and the residual rows use the target's offset from the
+// reference.  Mathematically the same dynamics and residuals.
 template <int FL, int G>
 struct ChainGroup<float, FL, G> {
   static constexpr int NXL = 4 * FL;
+  static constexpr bool kRelative = true;
   float mass_inv, l0, km, k3m;
   float2 cneg, grav, two, hh2, hh, hh6, mneg1;
+  float2 dref[FL];  // reference link vectors ending at this lane's masses
   int F, lg;
   unsigned mask;
   const float* pref;
@@ -166,8 +177,22 @@ struct ChainGroup<float, FL, G> {
     hh = make_float2(h, h);
     hh6 = make_float2(h6, h6);
     mneg1 = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int j = 0; j < FL; ++j) dref[j] = make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ int mass(int j) const { return lg * FL + j + 1; }
+  // Reference link vectors from the initial positions x0p (FP64, packed
+  // [p_1 .. p_F]); mass 0 is fixed at the origin.
+  __device__ __forceinline__ void set_reference(const double* x0p) {
+#pragma unroll
+    for (int j = 0; j < FL; ++j) {
+      const int i = mass(j);
+      if (i <= F) {
+        const double bx = i > 1 ? x0p[2 * (i - 2)] : 0.0, by = i > 1 ? x0p[2 * (i - 2) + 1] : 0.0;
+        dref[j] = make_float2((float)(x0p[2 * (i - 1)] - bx), (float)(x0p[2 * (i - 1) + 1] - by));
+      }
+    }
+  }
   __device__ __forceinline__ void accel(const float2* p, const float2* v, float2 um, float2* acc) const {
     float2 prev;
     prev.x = __shfl_up_sync(mask, p[FL - 1].x, 1, G);
@@ -179,7 +204,7 @@ struct ChainGroup<float, FL, G> {
     float fr[FL];
 #pragma unroll
     for (int j = 0; j < FL; ++j) {
-      d[j] = __ffma2_rn((j == 0) ? prev : p[j - 1], mneg1, p[j]);
+      d[j] = __fadd2_rn(__ffma2_rn((j == 0) ? prev : p[j - 1], mneg1, p[j]), dref[j]);
       const bool real = mass(j) <= F;
       const float q = real ? fmaf(d[j].x, d[j].x, d[j].y * d[j].y) : 1.f;
       const float rinv = rsqrtf(q);
@@ -293,9 +318,12 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
     const int w = i < 2 * I.F ? (q % FL) * 2 * G + 2 * (q / FL) + (i & 1) : 2 * SL + (i - 2 * I.F);
     sR[k * RS + w] = rg[idx];
   }
+  // targets (FP32 model: their offsets from the initial positions)
+  constexpr bool REL = ChainGroup<T, FL, G>::kRelative;
   for (int idx = threadIdx.x; idx < 2 * SL; idx += blockDim.x) {
     const int q = idx >> 1;
-    sRef[(q % FL) * 2 * G + 2 * (q / FL) + (idx & 1)] = q < I.F ? (T)a.xref[I.o_xref + idx] : (T)0;
+    sRef[(q % FL) * 2 * G + 2 * (q / FL) + (idx & 1)] =
+        q < I.F ? (T)(a.xref[I.o_xref + idx] - (REL ? a.x0[I.o_x0 + idx] : 0.0)) : (T)0;
   }
   __syncthreads();
 
@@ -310,13 +338,15 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   ChainGroup<T, FL, G> md(a.cs, I.F, lg, 0xffffffffu);
   const T uf_t = friction_threshold<T>(a.cs);
   md.pref = sRef + 2 * lg;
+  md.set_reference(a.x0 + I.o_x0);
   alignas(16) T x[4 * FL];
 #pragma unroll
   for (int j = 0; j < FL; ++j) {
     const int i = md.mass(j);
     const bool real = i <= I.F;
-    x[2 * j] = real ? (T)a.x0[I.o_x0 + 2 * (i - 1)] : (T)0;
-    x[2 * j + 1] = real ? (T)a.x0[I.o_x0 + 2 * (i - 1) + 1] : (T)0;
+    const bool pos = real && !REL;  // FP32: deviations from the initial positions start at 0
+    x[2 * j] = pos ? (T)a.x0[I.o_x0 + 2 * (i - 1)] : (T)0;
+    x[2 * j + 1] = pos ? (T)a.x0[I.o_x0 + 2 * (i - 1) + 1] : (T)0;
     x[2 * FL + 2 * j] = real ? (T)a.x0[I.o_x0 + 2 * I.F + 2 * (i - 1)] : (T)0;
     x[2 * FL + 2 * j + 1] = real ? (T)a.x0[I.o_x0 + 2 * I.F + 2 * (i - 1) + 1] : (T)0;
   }
@@ -436,23 +466,29 @@ __global__ void __launch_bounds__(256) k_line_group(RollArgs a) {
   const unsigned gmask = ((G == 32) ? 0xffffffffu : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
   ChainGroup<T, FL, G> md(a.cs, I.F, lg, gmask);
   const T uf_t = friction_threshold<T>(a.cs);
+  // targets and initial positions: the FP32 model keeps positions relative
+  // to the initial ones (and the targets as offsets from them)
+  constexpr bool REL = ChainGroup<T, FL, G>::kRelative;
   T ref[2 * FL];
 #pragma unroll
   for (int q = 0; q < FL; ++q) {
     const int i = md.mass(q);
     const bool real = i <= I.F;
-    ref[2 * q] = real ? (T)a.xref[I.o_xref + 2 * (i - 1)] : (T)0;
-    ref[2 * q + 1] = real ? (T)a.xref[I.o_xref + 2 * (i - 1) + 1] : (T)0;
+    const int o = 2 * (i - 1);
+    ref[2 * q] = real ? (T)(a.xref[I.o_xref + o] - (REL ? a.x0[I.o_x0 + o] : 0.0)) : (T)0;
+    ref[2 * q + 1] = real ? (T)(a.xref[I.o_xref + o + 1] - (REL ? a.x0[I.o_x0 + o + 1] : 0.0)) : (T)0;
   }
   md.pref = ref;
   md.pref_local = true;
+  md.set_reference(a.x0 + I.o_x0);
   alignas(16) T x[4 * FL];
 #pragma unroll
   for (int q = 0; q < FL; ++q) {
     const int i = md.mass(q);
     const bool real = i <= I.F;
-    x[2 * q] = real ? (T)a.x0[I.o_x0 + 2 * (i - 1)] : (T)0;
-    x[2 * q + 1] = real ? (T)a.x0[I.o_x0 + 2 * (i - 1) + 1] : (T)0;
+    const bool pos = real && !REL;
+    x[2 * q] = pos ? (T)a.x0[I.o_x0 + 2 * (i - 1)] : (T)0;
+    x[2 * q + 1] = pos ? (T)a.x0[I.o_x0 + 2 * (i - 1) + 1] : (T)0;
     x[2 * FL + 2 * q] = real ? (T)a.x0[I.o_x0 + 2 * I.F + 2 * (i - 1)] : (T)0;
     x[2 * FL + 2 * q + 1] = real ? (T)a.x0[I.o_x0 + 2 * I.F + 2 * (i - 1) + 1] : (T)0;
   }

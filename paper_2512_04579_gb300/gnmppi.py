@@ -30,7 +30,7 @@ EXPORTS = ["gnmppi_create", "gnmppi_layout", "gnmppi_solve", "gnmppi_solve_maske
            "gnmppi_mlp_num_params", "gnmppi_mlp_set_params", "gnmppi_mlp_get_params", "gnmppi_mlp_set_normalization",
            "gnmppi_mlp_forward", "gnmppi_mlp_loss_grad", "gnmppi_mlp_train_step", "gnmppi_mlp_warm_start",
            "gnmppi_mlp_destroy", "gnmppi_mlp_last_error", "gnmppi_autotune", "gnmppi_tune_set", "gnmppi_solve_async", "gnmppi_solve_wait",
-           "gnmppi_tune_report", "gnmppi_debug_inject"]
+           "gnmppi_tune_report", "gnmppi_debug_inject", "gnmppi_mlp_get_state", "gnmppi_mlp_set_state"]
 
 
 class Problem(C.Structure):
@@ -120,6 +120,8 @@ def load(path: str | None = None):
     L.gnmppi_mlp_set_params.argtypes = [vp, C.c_int32, vp, C.c_int64]
     L.gnmppi_mlp_get_params.argtypes = [vp, C.c_int32, vp, C.c_int64]
     L.gnmppi_mlp_set_normalization.argtypes = [vp, vp, vp, C.c_double]
+    L.gnmppi_mlp_get_state.argtypes = [vp, C.c_int32, vp, vp, vp, C.c_int64, C.POINTER(C.c_int32)]
+    L.gnmppi_mlp_set_state.argtypes = [vp, C.c_int32, vp, vp, vp, C.c_int64, C.c_int32]
     L.gnmppi_mlp_forward.argtypes = [vp, C.c_int32, vp, C.c_int32, vp]
     L.gnmppi_mlp_loss_grad.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, vp, vp]
     L.gnmppi_mlp_train_step.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, C.c_double, vp]
@@ -129,7 +131,8 @@ def load(path: str | None = None):
     L.gnmppi_mlp_last_error.argtypes = [vp]
     L.gnmppi_mlp_last_error.restype = C.c_char_p
     for f in ("gnmppi_mlp_create", "gnmppi_mlp_set_params", "gnmppi_mlp_get_params", "gnmppi_mlp_set_normalization",
-              "gnmppi_mlp_forward", "gnmppi_mlp_loss_grad", "gnmppi_mlp_train_step", "gnmppi_mlp_warm_start"):
+              "gnmppi_mlp_forward", "gnmppi_mlp_loss_grad", "gnmppi_mlp_train_step", "gnmppi_mlp_warm_start",
+              "gnmppi_mlp_get_state", "gnmppi_mlp_set_state"):
         getattr(L, f).restype = C.c_int32
     _lib = L
     return L
@@ -469,6 +472,19 @@ class Mlp:
         out = np.zeros(self.np)
         self._chk(load().gnmppi_mlp_get_params(self.h, MEM_HOST, out.ctypes.data, self.np), "gnmppi_mlp_get_params")
         return out
+
+    def get_state(self):
+        """(params, Adam first moments, second moments, step count)."""
+        p, m1, m2 = np.zeros(self.np), np.zeros(self.np), np.zeros(self.np)
+        step = C.c_int32()
+        self._chk(load().gnmppi_mlp_get_state(self.h, MEM_HOST, p.ctypes.data, m1.ctypes.data, m2.ctypes.data,
+                                               self.np, C.byref(step)), "gnmppi_mlp_get_state")
+        return p, m1, m2, int(step.value)
+
+    def set_state(self, params, m1, m2, step):
+        arrs = [np.ascontiguousarray(a, float) for a in (params, m1, m2)]
+        self._chk(load().gnmppi_mlp_set_state(self.h, MEM_HOST, *(a.ctypes.data for a in arrs), self.np, int(step)),
+                  "gnmppi_mlp_set_state")
 
     def set_normalization(self, x_mean, x_std, y_scale):
         xm = np.ascontiguousarray(x_mean, float)

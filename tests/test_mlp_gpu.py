@@ -212,3 +212,37 @@ def test_full_width_training_step_matches_oracle():
     sure = np.abs(g1) >= 1e-2 * np.sqrt(np.mean(g1 ** 2))
     assert sure.mean() > 0.95
     assert rel((p_gpu - params)[sure], (p - params)[sure]) < 1e-3
+
+
+def test_training_resumes_exactly_from_a_saved_state():
+    """Three Adam steps, save (parameters, both moments, step count), two more
+    steps; a fresh handle given the saved state and the same two steps ends
+    bitwise at the same parameters and moments."""
+    import torch
+
+    params, X, T, xm, xs = _setup(6)
+    dX = torch.tensor(X, dtype=torch.float64, device="cuda")
+    dT = torch.tensor(T, dtype=torch.float64, device="cuda")
+    a = G.Mlp(DIMS, nu=2, weights_bf16=True, max_batch=128)
+    a.set_params(params)
+    a.set_normalization(xm, xs, 1.0)
+    for _ in range(3):
+        a.train_step(dX, dT, X.shape[0], 1e-2)
+    saved = a.get_state()
+    assert saved[3] == 3
+    for _ in range(2):
+        a.train_step(dX, dT, X.shape[0], 1e-2)
+    end_a = a.get_state()
+    a.close()
+    b = G.Mlp(DIMS, nu=2, weights_bf16=True, max_batch=128)
+    b.set_normalization(xm, xs, 1.0)
+    b.set_state(*saved)
+    for _ in range(2):
+        b.train_step(dX, dT, X.shape[0], 1e-2)
+    end_b = b.get_state()
+    b.close()
+    for x, y in zip(end_a[:3], end_b[:3]):
+        assert np.array_equal(x, y)
+    assert end_a[3] == end_b[3] == 5
+    # set_params, unlike set_state, starts a new optimisation (moments reset)
+    assert not np.array_equal(saved[1], np.zeros_like(saved[1]))
