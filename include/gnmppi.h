@@ -268,9 +268,11 @@ const char* gnmppi_phase_name(int32_t i);
 gnmppi_status gnmppi_autotune(gnmppi_t h, int32_t mem, const double* x0, const double* xref, const double* U,
                               const double* sigma, int32_t reps);
 
-/* Set the launch configuration by hand (branches 1..8, solve_nt 128, 256 or 512).
- * Errors: E_ARG for values out of range. */
-gnmppi_status gnmppi_tune_set(gnmppi_t h, int32_t branches, int32_t solve_nt);
+/* Set the launch configuration by hand: branches 1..8; solve_nt 128, 256 or
+ * 512; contract_mt the BF16-mode contraction tile, 2 (256 [dR; W] rows per
+ * CTA, one CTA per SM), 1 (128 rows, two CTAs per SM) or 0 (unchanged).
+ * None of them changes a result bit.  Errors: E_ARG for values out of range. */
+gnmppi_status gnmppi_tune_set(gnmppi_t h, int32_t branches, int32_t solve_nt, int32_t contract_mt);
 
 /* The handle's launch configuration as a JSON object (source "default",
  * "set", "cache" or "timed"; the timed candidates when tuned), NUL-terminated
@@ -395,6 +397,14 @@ const char* gnmppi_mlp_last_error(gnmppi_mlp_t m);
 
 /* Number of kernels the library launched on this handle since creation. */
 int64_t gnmppi_launch_count(gnmppi_t h);
+
+/* Bounds-check build (the paper has no counterpart; a stand-in for a memory
+ * checker): in a library compiled with -DGNMPPI_CHECK (libgnmppi_check.so)
+ * the hot kernels' global stores check their index against the instance's
+ * block and skip, and count, any that fall outside.  Returns the number of
+ * such stores since the last call on the current device (synchronising it)
+ * and clears the counters; -1 in the normal build, -2 on a CUDA error. */
+int64_t gnmppi_check_count(void);
 
 /* Release the handle and all its device memory.  NULL is ignored. */
 void gnmppi_destroy(gnmppi_t h);

@@ -42,6 +42,7 @@ constexpr int kMaxBranches = 8;
 struct TuneCfg {
   int branches = 1;   // concurrent graph branches for the per-size rollout groups
   int solve_nt = 256; // threads per k_solve CTA (512: one CTA per SM, 256: two, 128: four)
+  int contract_mt = 2; // BF16 contraction tile: A sub-tiles per CTA (2: one CTA per SM, 1: two)
 };
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -249,6 +250,25 @@ extern "C" void gnmppi_destroy(gnmppi_t h) {
 }
 
 extern "C" int64_t gnmppi_launch_count(gnmppi_t h) { return h ? h->launches : 0; }
+
+namespace gnm {
+GNM_CHECK_ACCESSOR(check_count_api)
+}
+
+extern "C" int64_t gnmppi_check_count(void) {
+#ifdef GNMPPI_CHECK
+  if (cudaDeviceSynchronize() != cudaSuccess) return -2;
+  int64_t n = 0;
+  for (unsigned int c : {check_count_rollout_f32(), check_count_rollout_f64(), check_count_group_f32(),
+                         check_count_group_f64(), check_count_api(), check_count_tc(), check_count_mlp()}) {
+    if (c == 0xffffffffu) return -2;
+    n += c;
+  }
+  return n;
+#else
+  return -1;
+#endif
+}
 
 static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   const gnmppi_problem& p = h->p;
@@ -709,7 +729,8 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
   if (ON(2)) {
     if (h->use_tc) {
       const int inject = h->inj_tc && (int32_t)it == h->cs.inj_it;
-      CK(tc_contract_launch(h->tc, h->d_st, reinterpret_cast<float*>(h->d_P), h->stream, inject));
+      CK(tc_contract_launch(h->tc, h->d_st, reinterpret_cast<float*>(h->d_P), h->stream, inject,
+                            h->tune.contract_mt));
       h->launches++;
     } else {
       ga.tiles = h->d_tiles[0];
@@ -1075,11 +1096,11 @@ extern "C" gnmppi_status gnmppi_debug_read(gnmppi_t h, int32_t what, int32_t ins
 // ---------------------------------------------------------------- autotuner
 // Picks the launch configuration of a handle by timing the candidates on its
 // own instances and inputs: the number of concurrent graph branches for the
-// per-size rollout groups (samples and line search) and the k_solve CTA shape.
-// Choices are cached per process under a signature of the device, the model
-// and the multiset of instance shapes, and appended to the text file named by
-// GNMPPI_TUNE_FILE (one "signature branches solve_nt" line per entry), which
-// later processes read back.
+// per-size rollout groups (samples and line search), the k_solve CTA shape and,
+// in BF16 mode, the contraction tile.  Choices are cached per process under a
+// signature of the device, the model and the multiset of instance shapes, and
+// appended to the text file named by GNMPPI_TUNE_FILE (one "signature branches
+// solve_nt contract_mt" line per entry), which later processes read back.
 namespace {
 
 std::mutex g_tune_mu;
@@ -1120,10 +1141,12 @@ void read_tune_file() {  // under g_tune_mu
   if (!path || !*path) return;
   FILE* fp = fopen(path, "r");
   if (!fp) return;
-  char sig[320];
-  int nb = 0, nt = 0;
-  while (fscanf(fp, "%319s %d %d", sig, &nb, &nt) == 3) {
-    if (nb >= 1 && nb <= kMaxBranches && (nt == 128 || nt == 256 || nt == 512)) g_tune_cache[sig] = TuneCfg{nb, nt};
+  char line[512], sig[320];
+  while (fgets(line, sizeof(line), fp)) {
+    int nb = 0, nt = 0, mt = 2;
+    const int got = sscanf(line, "%319s %d %d %d", sig, &nb, &nt, &mt);  // lines without the tile field: 2
+    if (got >= 3 && nb >= 1 && nb <= kMaxBranches && (nt == 128 || nt == 256 || nt == 512) && (mt == 1 || mt == 2))
+      g_tune_cache[sig] = TuneCfg{nb, nt, mt};
   }
   fclose(fp);
 }
@@ -1133,7 +1156,7 @@ void append_tune_file(const std::string& sig, const TuneCfg& c) {  // under g_tu
   if (!path || !*path) return;
   FILE* fp = fopen(path, "a");
   if (!fp) return;
-  fprintf(fp, "%s %d %d\n", sig.c_str(), c.branches, c.solve_nt);
+  fprintf(fp, "%s %d %d %d\n", sig.c_str(), c.branches, c.solve_nt, c.contract_mt);
   fclose(fp);
 }
 
@@ -1167,17 +1190,20 @@ static gnmppi_status time_phases(gnmppi_t h, unsigned mask, int reps, double* be
   return st;
 }
 
-extern "C" gnmppi_status gnmppi_tune_set(gnmppi_t h, int32_t branches, int32_t solve_nt) {
+extern "C" gnmppi_status gnmppi_tune_set(gnmppi_t h, int32_t branches, int32_t solve_nt, int32_t contract_mt) {
   if (!h) return GNMPPI_E_ARG;
   if (branches < 1 || branches > kMaxBranches) return fail(h, GNMPPI_E_ARG, "branches must be in 1..%d", kMaxBranches);
   if (solve_nt != 128 && solve_nt != 256 && solve_nt != 512)
     return fail(h, GNMPPI_E_ARG, "solve_nt must be 128, 256 or 512");
+  if (contract_mt != 0 && contract_mt != 1 && contract_mt != 2)
+    return fail(h, GNMPPI_E_ARG, "contract_mt must be 0 (keep), 1 or 2");
   set_branches(h, branches);
   h->tune.solve_nt = solve_nt;
+  if (contract_mt) h->tune.contract_mt = contract_mt;
   drop_graph(h);
-  char buf[160];
-  snprintf(buf, sizeof(buf), "{\"source\": \"set\", \"branches\": %d, \"solve_nt\": %d}", h->tune.branches,
-           h->tune.solve_nt);
+  char buf[192];
+  snprintf(buf, sizeof(buf), "{\"source\": \"set\", \"branches\": %d, \"solve_nt\": %d, \"contract_mt\": %d}",
+           h->tune.branches, h->tune.solve_nt, h->tune.contract_mt);
   h->tune_report = buf;
   return GNMPPI_OK;
 }
@@ -1194,10 +1220,12 @@ extern "C" gnmppi_status gnmppi_autotune(gnmppi_t h, int32_t mem, const double* 
     if (it != g_tune_cache.end()) {
       set_branches(h, it->second.branches);
       h->tune.solve_nt = it->second.solve_nt;
+      h->tune.contract_mt = it->second.contract_mt;
       drop_graph(h);
       char buf[512];
-      snprintf(buf, sizeof(buf), "{\"source\": \"cache\", \"signature\": \"%s\", \"branches\": %d, \"solve_nt\": %d}",
-               sig.c_str(), h->tune.branches, h->tune.solve_nt);
+      snprintf(buf, sizeof(buf),
+               "{\"source\": \"cache\", \"signature\": \"%s\", \"branches\": %d, \"solve_nt\": %d, \"contract_mt\": %d}",
+               sig.c_str(), h->tune.branches, h->tune.solve_nt, h->tune.contract_mt);
       h->tune_report = buf;
       return GNMPPI_OK;
     }
@@ -1250,6 +1278,25 @@ extern "C" gnmppi_status gnmppi_autotune(gnmppi_t h, int32_t mem, const double* 
     }
   }
   h->tune.solve_nt = best_nt;
+  // 3. BF16 contraction tile: two 128-row A sub-tiles per CTA (one CTA per
+  //    SM) or one (two CTAs per SM)
+  int best_mt = 2;
+  if (h->use_tc && h->p.precision == kBF16) {
+    double best = 1e300;
+    for (int mt : {2, 1}) {
+      h->tune.contract_mt = mt;
+      double ms = 0.0;
+      st = time_phases(h, 1u << 2, reps, &ms);
+      if (st != GNMPPI_OK) return st;
+      snprintf(buf, sizeof(buf), "%s{\"contract_mt\": %d, \"ms\": %.4f}", rows.empty() ? "" : ", ", mt, ms);
+      rows += buf;
+      if (ms < best * 0.98) {
+        best = ms;
+        best_mt = mt;
+      }
+    }
+  }
+  h->tune.contract_mt = best_mt;
   if ((st = fetch_timeout(h)) != GNMPPI_OK) return st;
   CK(cudaStreamSynchronize(h->stream));
   st = check_timeout(h);
@@ -1262,7 +1309,7 @@ extern "C" gnmppi_status gnmppi_autotune(gnmppi_t h, int32_t mem, const double* 
   }
   h->tune_report = std::string("{\"source\": \"timed\", \"signature\": \"") + sig + "\", \"branches\": " +
                    std::to_string(h->tune.branches) + ", \"solve_nt\": " + std::to_string(h->tune.solve_nt) +
-                   ", \"candidates\": [" + rows + "]}";
+                   ", \"contract_mt\": " + std::to_string(h->tune.contract_mt) + ", \"candidates\": [" + rows + "]}";
   return GNMPPI_OK;
 }
 
@@ -1282,8 +1329,8 @@ extern "C" gnmppi_status gnmppi_tune_report(gnmppi_t h, char* buf, int32_t cap) 
   std::string r = h->tune_report;
   if (r.empty()) {
     char b[160];
-    snprintf(b, sizeof(b), "{\"source\": \"default\", \"branches\": %d, \"solve_nt\": %d}", h->tune.branches,
-             h->tune.solve_nt);
+    snprintf(b, sizeof(b), "{\"source\": \"default\", \"branches\": %d, \"solve_nt\": %d, \"contract_mt\": %d}",
+             h->tune.branches, h->tune.solve_nt, h->tune.contract_mt);
     r = b;
   }
   if ((int32_t)r.size() + 1 > cap) return fail(h, GNMPPI_E_ARG, "report needs %d bytes", (int)r.size() + 1);

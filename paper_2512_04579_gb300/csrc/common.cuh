@@ -8,6 +8,45 @@
 
 namespace gnm {
 
+// ---------------------------------------------------------------------------
+// Bounds-check build.  Compiled with -DGNMPPI_CHECK (libgnmppi_check.so), the
+// hot kernels' global stores pass their index and the extent of the
+// instance's block (or of the output array) through GNM_IN(i, n): an index
+// outside [0, n) is counted in this translation unit's offence counter and
+// the store is skipped, so a wrong index shows up as a count instead of a
+// memory fault (no trap).  gnmppi_check_count() collects the counters.  In
+// the normal build GNM_IN(i, n) is `true` and costs nothing.
+#ifdef GNMPPI_CHECK
+static __device__ unsigned int g_check_offences;
+__device__ __forceinline__ bool gnm_in(int64_t i, int64_t n) {
+  if (i >= 0 && i < n) return true;
+  atomicAdd(&g_check_offences, 1u);
+  return false;
+}
+#define GNM_IN(i, n) ::gnm::gnm_in((int64_t)(i), (int64_t)(n))
+// Host side: returns and clears this translation unit's counter.
+#define GNM_CHECK_ACCESSOR(name)                                               \
+  unsigned int name() {                                                        \
+    unsigned int v = 0, z = 0;                                                 \
+    if (cudaMemcpyFromSymbol(&v, g_check_offences, sizeof(v)) != cudaSuccess) \
+      return 0xffffffffu;                                                      \
+    cudaMemcpyToSymbol(g_check_offences, &z, sizeof(z));                       \
+    return v;                                                                  \
+  }
+#else
+#define GNM_IN(i, n) true
+#define GNM_CHECK_ACCESSOR(name) \
+  unsigned int name() { return 0; }
+#endif
+// one accessor per translation unit that holds kernels
+unsigned int check_count_rollout_f32();
+unsigned int check_count_rollout_f64();
+unsigned int check_count_group_f32();
+unsigned int check_count_group_f64();
+unsigned int check_count_api();
+unsigned int check_count_tc();
+unsigned int check_count_mlp();
+
 constexpr int kPairsPerBlock = 64;   // antithetic pairs per rollout CTA (2 lanes each)
 constexpr int kSamplesPerBlock = 128;  // one-sided samples per rollout CTA
 constexpr int kPadK = 64;            // sample-dimension padding of dR / W rows

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "../../include/gnmppi.h"
+#include "common.cuh"
 #include "tc_ptx.cuh"
 
 namespace gnm {
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const __grid_constant__ CUten
           const int i = row0 + rr;
           if (i >= g.M) break;
           const int64_t o = (int64_t)i * g.ldc + j;
+          if (!GNM_IN(o, (int64_t)g.M * g.ldc)) continue;
           float x = stg[rr * 33 + lane];
           if (g.mode == 0) {
             x += bj;
@@ -306,6 +308,7 @@ __global__ void k_warm(const float* Y, int B, int dL, int nmu, int nu, float ysc
 }
 
 }  // namespace
+GNM_CHECK_ACCESSOR(check_count_mlp)
 }  // namespace gnm
 
 using namespace gnm;

@@ -75,6 +75,7 @@ struct SampleEmit {
   S* col;        // this sample's column of dR at the stage's first row
   const T* r;    // nominal residual at the stage's first row
   int ldK, par;
+  int row0, nrows;  // first row of the stage, rows of dR (bounds-check build)
   bool active;
   T sign, csum, esum;
   __device__ __forceinline__ void operator()(int i, T v) {
@@ -83,12 +84,12 @@ struct SampleEmit {
       const T vo = __shfl_xor_sync(0xffffffffu, v, 1);
       if (par == (i & 1)) {
         const T d = sign * (v - vo) * (T)0.5;
-        if (active) put(col + (int64_t)i * ldK, d);
+        if (active && GNM_IN(row0 + i, nrows)) put(col + (int64_t)i * ldK, d);
         esum += d * r[i];
       }
     } else {
       const T d = v - r[i];
-      if (active) put(col + (int64_t)i * ldK, d);
+      if (active && GNM_IN(row0 + i, nrows)) put(col + (int64_t)i * ldK, d);
       esum += d * r[i];
     }
   }
@@ -105,7 +106,7 @@ struct SampleEmit {
       const T got = __shfl_xor_sync(0xffffffffu, give, 1);
       const T d = sign * (own - got) * (T)0.5;
       const int row = i + par;
-      if (active) put(col + (int64_t)row * ldK, d);
+      if (active && GNM_IN(row0 + row, nrows)) put(col + (int64_t)row * ldK, d);
       esum += d * r[row];
     } else {
       (*this)(i, v0);
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
   S* dR = reinterpret_cast<S*>(a.dR) + I.o_dR + m;  // this sample's column
   S* Wm = reinterpret_cast<S*>(a.W) + I.o_W;
   Acc<T> cost, eacc;
-  SampleEmit<T, S, ANTI> em{dR, sR, I.ldK, par, active, sign, (T)0, (T)0};
+  SampleEmit<T, S, ANTI> em{dR, sR, I.ldK, par, 0, I.nR, active, sign, (T)0, (T)0};
   const uint32_t mm = active ? (uint32_t)m : 0u;
   const int64_t stage_stride = (int64_t)Model::RPS * I.ldK;
   // Two controls per step (nu = 2) with antithetic pairs: the normals of steps
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
         const int j = k * NU + c;
         const T w = (j == m) ? sS[j] * sqrtn : (T)0;
         u[c] = sU[j] + sign * w;
-        if (active && par == 0) put(Wm + (int64_t)j * I.ldK + m, w);
+        if (active && par == 0 && GNM_IN(j, I.n)) put(Wm + (int64_t)j * I.ldK + m, w);
       }
     } else if (SHARE) {
       if ((k & 1) == 0) {
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
         const int j = k * NU + c;
         const T w = sS[j] * (c ? z1 : z0);
         u[c] = sU[j] + sign * w;
-        if (active && par == c) put(Wm + (int64_t)j * I.ldK + m, w);
+        if (active && par == c && GNM_IN(j, I.n)) put(Wm + (int64_t)j * I.ldK + m, w);
       }
     } else {
 #pragma unroll
@@ -206,11 +207,12 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
         }
         const T w = sS[j] * ((j & 1) ? z1 : z0);
         u[c] = sU[j] + sign * w;
-        if (active && par == (ANTI ? (j & 1) : 0)) put(Wm + (int64_t)j * I.ldK + m, w);
+        if (active && par == (ANTI ? (j & 1) : 0) && GNM_IN(j, I.n)) put(Wm + (int64_t)j * I.ldK + m, w);
       }
     }
     em.col = dR + k * stage_stride;
     em.r = sR + k * Model::RPS;
+    em.row0 = k * Model::RPS;
     em.csum = (T)0;
     em.esum = (T)0;
     md.stage(x, u, em);
@@ -224,6 +226,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
   }
   em.col = dR + I.N * stage_stride;
   em.r = sR + I.N * Model::RPS;
+  em.row0 = I.N * Model::RPS;
   em.csum = (T)0;
   em.esum = (T)0;
   md.terminal(x, em);
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
     ev += __shfl_xor_sync(0xffffffffu, ev, 1);
   }
   const bool ok = isfinite(Cself) && isfinite(Cother) && isfinite(ev);
-  if (active) {
+  if (active && GNM_IN(m, I.Kp)) {
     a.C[I.o_C + (ANTI ? 2 * m + par : m)] = Cself;
     if (par == 0) a.e[I.o_C / 2 + m] = ok ? ev : 0.0;
     if (!ok) {  // dropped pair: its columns leave P and S
@@ -255,9 +258,10 @@ struct LineEmit {
   T* out;  // nullptr: cost only
   int base;
   T csum;
+  int nrows;  // rows of the residual (bounds-check build)
   __device__ __forceinline__ void operator()(int i, T v) {
     csum += v * v;
-    if (out) out[base + i] = v;
+    if (out && GNM_IN(base + i, nrows)) out[base + i] = v;
   }
   __device__ __forceinline__ void pair(int i, T v0, T v1) {
     (*this)(i, v0);
@@ -295,7 +299,7 @@ __global__ void __launch_bounds__(128) k_line(RollArgs a) {
   T* out = nullptr;
   if (a.mode == 0) out = reinterpret_cast<T*>(a.RL) + I.o_RL + (int64_t)j * I.nR;
   if (a.mode == 1) out = const_cast<T*>(reinterpret_cast<const T*>(a.r)) + I.o_R;
-  LineEmit<T> em{out, 0, (T)0};
+  LineEmit<T> em{out, 0, (T)0, I.nR};
   Acc<T> cost;
   const double* U = a.U + I.o_U;
   const double* D = a.delta + I.o_U;

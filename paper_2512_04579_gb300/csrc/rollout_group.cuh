@@ -363,6 +363,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
     S* dR;
     const T* r;  // interleaved nominal residual at the stage's first word
     int ldK, m, base, own_w, ctl_w;
+    int nrows;   // rows of dR (bounds-check build)
     bool active, plus;
     T sign, csum, esum;
     __device__ __forceinline__ void pair(int slot, int r0, T v0, T v1, bool valid) {
@@ -374,10 +375,10 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
       const T own = plus ? v0 : v1;
       const int row = base + r0 + (plus ? 0 : 1);
       const T d = sign * (own - got) * (T)0.5;
-      if (active) put(dR + (int64_t)row * ldK + m, d);
+      if (active && GNM_IN(row, nrows)) put(dR + (int64_t)row * ldK + m, d);
       esum += d * r[slot < FL ? 2 * G * slot + own_w : ctl_w];
     }
-  } em{dR, sR, I.ldK, m, 0, 2 * lg + (plus ? 0 : 1), 2 * SL + (plus ? 0 : 1), active, plus, sign, (T)0, (T)0};
+  } em{dR, sR, I.ldK, m, 0, 2 * lg + (plus ? 0 : 1), 2 * SL + (plus ? 0 : 1), I.nR, active, plus, sign, (T)0, (T)0};
   // The 2G lanes of a pair draw the normals of 2G consecutive steps at once
   // (lane l of the pair: Philox call q = k + l) and hand them round by shuffle.
   // Sigma points (Method E): pair m perturbs control m alone, by sqrt(n) s_m.
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
     }
     const T w0 = sS[2 * k] * z0, w1 = sS[2 * k + 1] * z1;
     const T u[2] = {sU[2 * k] + sign * w0, sU[2 * k + 1] + sign * w1};
-    if (active && plus && lg == 0) {
+    if (active && plus && lg == 0 && GNM_IN(2 * k + 1, I.n)) {
       put(Wm + (int64_t)(2 * k) * I.ldK + m, w0);
       put(Wm + (int64_t)(2 * k + 1) * I.ldK + m, w1);
     }
@@ -432,7 +433,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   const double evo = __shfl_xor_sync(0xffffffffu, ev, G);  // every lane shuffles
   ev = ev + evo;  // the two halves of the pair each hold half of the rows' terms
   const bool ok = isfinite(Cself) && isfinite(Cother) && isfinite(ev);
-  if (active && lg == 0) {
+  if (active && lg == 0 && GNM_IN(m, I.Kp)) {
     a.C[I.o_C + 2 * m + (plus ? 0 : 1)] = Cself;
     if (plus) a.e[I.o_C / 2 + m] = ok ? ev : 0.0;
   }
@@ -499,16 +500,17 @@ __global__ void __launch_bounds__(256) k_line_group(RollArgs a) {
     T* out;
     int base;
     T csum;
+    int nrows;  // rows of the residual (bounds-check build)
     __device__ __forceinline__ void operator()(int row_local, T v, bool valid) {
       if (!valid) return;
       csum += v * v;
-      if (out) out[base + row_local] = v;
+      if (out && GNM_IN(base + row_local, nrows)) out[base + row_local] = v;
     }
     __device__ __forceinline__ void pair(int, int r0, T v0, T v1, bool valid) {
       (*this)(r0, v0, valid);
       (*this)(r0 + 1, v1, valid);
     }
-  } em{out, 0, (T)0};
+  } em{out, 0, (T)0, I.nR};
   Acc<T> cost;
   const double* U = a.U + I.o_U;
   const double* D = a.delta + I.o_U;

@@ -41,4 +41,6 @@ bool group_launchers_f64(int F, Launchers* o) {
   }
 }
 
+GNM_CHECK_ACCESSOR(check_count_group_f64)
+
 }  // namespace gnm

@@ -546,8 +546,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_solve(SolveArgs a) {
     double acc;
     if (lsq) acc = srow_dot(P + (int64_t)i * I.ldP + I.sP, x, yh, yl, n);
     else acc = Keff * s[i] * s[i] * x[i];
-    a.delta[I.o_U + i] = acc;
-    a.y[I.o_U + i] = x[i];
+    if (GNM_IN(i, n)) {
+      a.delta[I.o_U + i] = acc;
+      a.y[I.o_U + i] = x[i];
+    }
     dsq += acc * acc;
   }
   dsq = block_sum(dsq, red);
@@ -625,6 +627,7 @@ __global__ void __launch_bounds__(128) k_update(SolveArgs a) {
   if (js < 0) return;
   const double al = alpha_s;
   for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
+    if (!GNM_IN(i, I.n)) continue;
     a.U[I.o_U + i] = a.U[I.o_U + i] + al * a.delta[I.o_U + i];
     if (a.shrink) a.s[I.o_U + i] *= a.cs.beta_sqrt;
   }

@@ -113,8 +113,13 @@ __device__ __forceinline__ void store_row_sw64(unsigned char* hi, unsigned char*
 // FP32-level accuracy (the dropped remainder x remainder term is ~2^-18
 // relative).  192 threads: warp 0 lane 0 TMA, warp 1 lane 0 MMA, warps 2-5
 // split; warps 0-3 read TMEM back.
+// MT: A sub-tiles per CTA.  MT = 2: 256 A rows, a 3-stage ring of 64 KB, one
+// CTA per SM; MT = 1: 128 A rows, a 2-stage ring of 48 KB (96 KB), two CTAs per
+// SM, whose pipelines hide each other's load latency (the W rows are then read
+// twice as often, from L2).  Same products, same accumulation order per output.
 constexpr int kContractThreads = 192;
-__global__ void __launch_bounds__(kContractThreads, 1) k_contract_tc(const CUtensorMap* __restrict__ maps,
+template <int MT>
+__global__ void __launch_bounds__(kContractThreads, 3 - MT) k_contract_tc(const CUtensorMap* __restrict__ maps,
                                                                     const TcJob* __restrict__ jobs,
                                                                     const InstState* __restrict__ st,
                                                                     const int4* __restrict__ tiles,
@@ -124,9 +129,9 @@ __global__ void __launch_bounds__(kContractThreads, 1) k_contract_tc(const CUten
   constexpr int NSUB = 2;               // BF16 MMAs (K = 16, 32 bytes) per k-block, sub-tile and pass
   constexpr int TILE = BM * ROW_BYTES;  // one landed 128-row FP32 box (16 KB)
   constexpr int HALF = TILE / 2;        // one 128-row BF16 tile of 64-byte rows (8 KB)
-  constexpr int MTMAX = 2;              // 128-row sub-tiles of A per tile (each its own accumulator)
+  constexpr int MTMAX = MT;             // 128-row sub-tiles of A per tile (each its own accumulator)
   constexpr int STAGE_BYTES = (MTMAX + 2) * TILE;
-  constexpr int STAGES = RING_BYTES / STAGE_BYTES;
+  constexpr int STAGES = (MT == 2 ? RING_BYTES : RING_BYTES / 2) / STAGE_BYTES;
   constexpr int SPLITTERS = kContractThreads - 64;
   constexpr uint32_t TCOLS = MTMAX * TMEM_COLS;
   const int4 tl = tiles[blockIdx.x];
@@ -298,7 +303,8 @@ __global__ void __launch_bounds__(kContractThreads, 1) k_contract_tc(const CUten
         if (live) {
 #pragma unroll 8
           for (int jj = 0; jj < 32; ++jj)
-            if (c * 32 + jj < jn) out[(int64_t)(j0 + jj) * J.ldc + colw] = __uint_as_float(v[jj]);
+            if (c * 32 + jj < jn && GNM_IN((int64_t)(j0 + jj) * J.ldc + colw, (int64_t)J.M * J.ldc))
+              out[(int64_t)(j0 + jj) * J.ldc + colw] = __uint_as_float(v[jj]);
         }
       }
     }
@@ -512,7 +518,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
           const int colw = col < J.ccut ? col : col + J.cgap;
 #pragma unroll 4
           for (int rr = 0; rr < 32; ++rr)
-            if (row0 + rr < J.M) out[(int64_t)(row0 + rr) * J.ldc + colw] = stg[rr * 33 + lane];
+            if (row0 + rr < J.M && GNM_IN((int64_t)(row0 + rr) * J.ldc + colw, (int64_t)J.M * J.ldc))
+              out[(int64_t)(row0 + rr) * J.ldc + colw] = stg[rr * 33 + lane];
         }
         // strictly lower block of the symmetric Gram: store its transpose too
         // (the contraction's output is rectangular and has no mirror image)
@@ -522,7 +529,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
 #pragma unroll 4
             for (int rr = 0; rr < 32; ++rr) {
               const int colt = col_org + c * 32 + rr;
-              if (colt < J.Nc) out[(int64_t)colt * J.ldc + rowt] = stg[lane * 33 + rr];
+              if (colt < J.Nc && GNM_IN((int64_t)colt * J.ldc + rowt, (int64_t)J.M * J.ldc))
+                out[(int64_t)colt * J.ldc + rowt] = stg[lane * 33 + rr];
             }
           }
         }
@@ -594,7 +602,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
   const int nb = (int)desc.size();
   std::vector<CUtensorMap> maps(3 * (size_t)nb);
   std::vector<TcJob> jobs(3 * (size_t)nb);
-  std::vector<int4> tc, tg, ts;
+  std::vector<int4> tc, tc1, tg, ts;
   for (int b = 0; b < nb; ++b) {
     const InstDesc& d = desc[b];
     if (d.ldK % kblk != 0) {
@@ -629,10 +637,13 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     jc.cgap = d.sP - d.nR;   // ... start at sP
     if (bf16) {
       // (job, block of 256 [dR; W] rows, block of 256 W rows, A sub-tiles);
-      // the W blocks of a row block adjacent (its A rows read once from HBM)
+      // the W blocks of a row block adjacent (its A rows read once from HBM);
+      // and the same with one 128-row A sub-tile per tile
       for (int i = 0; i * 2 * BM < d.nR + d.n; ++i)
         for (int j = 0; j * BN < d.n; ++j)
           tc.push_back(make_int4(b, i, j, d.nR + d.n - i * 2 * BM > BM ? 2 : 1));
+      for (int i = 0; i * BM < d.nR + d.n; ++i)
+        for (int j = 0; j * BN < d.n; ++j) tc1.push_back(make_int4(b, i, j, 1));
     } else {
       // three-pass TF32 kernel: (job, first row, first column, 1), the row
       // tiles of a column block adjacent so that its B rows are read from L2
@@ -678,16 +689,20 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
   auto contract_work = [&](const int4& t) { return (int64_t)jobs[t.x].nkb * (bf16 ? t.w : 1); };
   std::stable_sort(tc.begin(), tc.end(),
                    [&](const int4& a, const int4& b) { return contract_work(a) > contract_work(b); });
+  std::stable_sort(tc1.begin(), tc1.end(),
+                   [&](const int4& a, const int4& b) { return contract_work(a) > contract_work(b); });
   std::stable_sort(tg.begin(), tg.end(), [&](const int4& a, const int4& b) { return gram_work(a) > gram_work(b); });
   if (!plan_alloc(plan, &plan->d_maps, sizeof(CUtensorMap) * maps.size()) ||
       !plan_alloc(plan, &plan->d_jobs, sizeof(TcJob) * jobs.size()) ||
       !plan_alloc(plan, &plan->d_tiles_c, sizeof(int4) * std::max<size_t>(1, tc.size())) ||
+      !plan_alloc(plan, &plan->d_tiles_c1, sizeof(int4) * std::max<size_t>(1, tc1.size())) ||
       !plan_alloc(plan, &plan->d_tiles_g, sizeof(int4) * std::max<size_t>(1, tg.size())) ||
       !plan_alloc(plan, &plan->d_err, sizeof(int))) {
     err = "cudaMalloc failed for the tensor-core plan";
     return GNMPPI_E_NOMEM;
   }
   plan->ntiles_c = (int)tc.size();
+  plan->ntiles_c1 = (int)tc1.size();
   plan->ntiles_g = (int)tg.size();
   bool ok = cudaMemcpyAsync(plan->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
                             stream) == cudaSuccess;
@@ -695,6 +710,9 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
                  cudaSuccess;
   ok = ok && cudaMemcpyAsync(plan->d_tiles_c, tc.data(), sizeof(int4) * tc.size(), cudaMemcpyHostToDevice, stream) ==
                  cudaSuccess;
+  if (!tc1.empty())
+    ok = ok && cudaMemcpyAsync(plan->d_tiles_c1, tc1.data(), sizeof(int4) * tc1.size(), cudaMemcpyHostToDevice,
+                               stream) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(plan->d_tiles_g, tg.data(), sizeof(int4) * tg.size(), cudaMemcpyHostToDevice, stream) ==
                  cudaSuccess;
   ok = ok && cudaMemsetAsync(plan->d_err, 0, sizeof(int), stream) == cudaSuccess;
@@ -708,8 +726,11 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     return GNMPPI_E_CUDA;
   }
   plan->smem = RING_BYTES + 1024 + 256;
-  cudaError_t e = bf16 ? cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem)
+  plan->smem1 = RING_BYTES / 2 + 1024 + 256;
+  cudaError_t e = bf16 ? cudaFuncSetAttribute(k_contract_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem)
                        : cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
+  if (e == cudaSuccess && bf16)
+    e = cudaFuncSetAttribute(k_contract_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem1);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
   if (e != cudaSuccess) {
@@ -719,11 +740,15 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
   return GNMPPI_OK;
 }
 
-cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float* P, cudaStream_t stream, int inject) {
+cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float* P, cudaStream_t stream, int inject,
+                               int mt) {
   if (plan.ntiles_c == 0) return cudaSuccess;
-  if (plan.bf16)
-    k_contract_tc<<<plan.ntiles_c, kContractThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
-                                                                          plan.d_tiles_c, P, plan.d_err, inject);
+  if (plan.bf16 && mt == 1)
+    k_contract_tc<1><<<plan.ntiles_c1, kContractThreads, plan.smem1, stream>>>(plan.d_maps, plan.d_jobs, d_st,
+                                                                               plan.d_tiles_c1, P, plan.d_err, inject);
+  else if (plan.bf16)
+    k_contract_tc<2><<<plan.ntiles_c, kContractThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
+                                                                             plan.d_tiles_c, P, plan.d_err, inject);
   else
     k_gram_tc<true><<<plan.ntiles_c, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
                                                                         plan.d_tiles_c, P, nullptr, plan.d_err, inject);
@@ -736,5 +761,7 @@ cudaError_t tc_gram_launch(const TcPlan& plan, const InstState* d_st, double* A,
                                                                         plan.d_tiles_g, A, S2, plan.d_err, 0);
   return cudaGetLastError();
 }
+
+GNM_CHECK_ACCESSOR(check_count_tc)
 
 }  // namespace gnm

@@ -32,9 +32,10 @@ struct TcPlan {
   CUtensorMap* d_maps = nullptr;  // per instance: contraction [dR; W]; then P^T columns; then S columns
   TcJob* d_jobs = nullptr;        // same order as the maps (contraction, Gram, S2)
   int4* d_tiles_c = nullptr;      // (job, m tile, n tile, sub-tiles) of the contraction
+  int4* d_tiles_c1 = nullptr;     // the same with one A sub-tile per tile (BF16 mode)
   int4* d_tiles_g = nullptr;      // (job, first row, first column, sub-tiles | 4 diagonal) of the Gram products
-  int ntiles_c = 0, ntiles_g = 0;
-  int smem = 0;
+  int ntiles_c = 0, ntiles_c1 = 0, ntiles_g = 0;
+  int smem = 0, smem1 = 0;
   int bf16 = 1;
   int* d_err = nullptr;           // set to 1 when a bounded wait ran out
   std::vector<void*> allocs;
@@ -49,7 +50,9 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
 // [P^T | S] = W^T [dR | W] into P (FP32).  inject != 0 (tests only): every
 // CTA's first MMA-side wait is on a barrier that nothing completes, so it
 // runs out after 20 ms, sets the error word and the CTA winds down.
-cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float* P, cudaStream_t stream, int inject);
+// mt (BF16 mode): A sub-tiles per CTA, 2 (one CTA per SM) or 1 (two per SM).
+cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float* P, cudaStream_t stream, int inject,
+                               int mt);
 
 // A = P^T P and, for instances in LSQ mode, S2 = S S^T (FP64 outputs) from
 // three TF32 passes over [P^T | S] split in shared memory, in one launch.

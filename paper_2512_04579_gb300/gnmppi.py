@@ -30,7 +30,8 @@ EXPORTS = ["gnmppi_create", "gnmppi_layout", "gnmppi_solve", "gnmppi_solve_maske
            "gnmppi_mlp_num_params", "gnmppi_mlp_set_params", "gnmppi_mlp_get_params", "gnmppi_mlp_set_normalization",
            "gnmppi_mlp_forward", "gnmppi_mlp_loss_grad", "gnmppi_mlp_train_step", "gnmppi_mlp_warm_start",
            "gnmppi_mlp_destroy", "gnmppi_mlp_last_error", "gnmppi_autotune", "gnmppi_tune_set", "gnmppi_solve_async", "gnmppi_solve_wait",
-           "gnmppi_tune_report", "gnmppi_debug_inject", "gnmppi_mlp_get_state", "gnmppi_mlp_set_state"]
+           "gnmppi_tune_report", "gnmppi_debug_inject", "gnmppi_mlp_get_state", "gnmppi_mlp_set_state",
+           "gnmppi_check_count"]
 
 
 class Problem(C.Structure):
@@ -92,6 +93,8 @@ def load(path: str | None = None):
     L.gnmppi_softmin_noalloc.restype = C.c_int32
     L.gnmppi_launch_count.argtypes = [vp]
     L.gnmppi_launch_count.restype = C.c_int64
+    L.gnmppi_check_count.argtypes = []
+    L.gnmppi_check_count.restype = C.c_int64
     L.gnmppi_destroy.argtypes = [vp]
     L.gnmppi_destroy.restype = None
     L.gnmppi_last_error.argtypes = [vp]
@@ -105,7 +108,7 @@ def load(path: str | None = None):
     L.gnmppi_solve_wait.restype = C.c_int32
     L.gnmppi_autotune.argtypes = [vp, C.c_int32, vp, vp, vp, vp, C.c_int32]
     L.gnmppi_autotune.restype = C.c_int32
-    L.gnmppi_tune_set.argtypes = [vp, C.c_int32, C.c_int32]
+    L.gnmppi_tune_set.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
     L.gnmppi_tune_set.restype = C.c_int32
     L.gnmppi_tune_report.argtypes = [vp, C.c_char_p, C.c_int32]
     L.gnmppi_debug_inject.restype = C.c_int32
@@ -279,8 +282,8 @@ def gnmppi_autotune(h, mem, x0, xref, U, sigma=None, reps: int = 3) -> dict:
     return gnmppi_tune_report(h)
 
 
-def gnmppi_tune_set(h, branches: int, solve_nt: int):
-    st = load().gnmppi_tune_set(h, branches, solve_nt)
+def gnmppi_tune_set(h, branches: int, solve_nt: int, contract_mt: int = 0):
+    st = load().gnmppi_tune_set(h, branches, solve_nt, contract_mt)
     _check(h, st, "gnmppi_tune_set")
 
 

@@ -20,11 +20,11 @@ def lib():
     return G.load()
 
 
-def uneven_handle(seed, batch, iterations=3):
+def uneven_handle(seed, batch, iterations=3, precision=G.PREC_FP32):
     Ms, Ns, Ks, x0s, tgts = I.uneven_chain_instances(seed, batch)
     shapes = [(int(Ns[b]), int(Ms[b]), int(Ks[b])) for b in range(batch)]
     prob = G.chain_problem(M=int(Ms[0]), N=int(Ns[0]), K=int(Ks[0]), iterations=iterations, lam=1e-3, sigma0=0.2,
-                           seed=seed, precision=G.PREC_FP32)
+                           seed=seed, precision=precision)
     h = G.gnmppi_create(prob, batch, shapes)
     nU = int(sum(2 * n for n in Ns))
     return h, np.concatenate(x0s), np.concatenate(tgts), nU, len(set(int(m) for m in Ms))
@@ -44,10 +44,10 @@ def test_launch_configuration_does_not_change_the_solve():
     try:
         assert G.gnmppi_tune_report(h)["source"] == "default"
         ref_U, ref_C = None, None
-        for cfg in [(1, 256), (4, 128), (8, 256), (2, 128), (2, 512)]:
+        for cfg in [(1, 256, 2), (4, 128, 1), (8, 256, 2), (2, 128, 1), (2, 512, 2)]:
             G.gnmppi_tune_set(h, *cfg)
             rep = G.gnmppi_tune_report(h)
-            assert rep["source"] == "set" and (rep["branches"], rep["solve_nt"]) == cfg
+            assert rep["source"] == "set" and (rep["branches"], rep["solve_nt"], rep["contract_mt"]) == cfg
             U, C = solve(h, x0, xr, nU, batch)
             if ref_U is None:
                 ref_U, ref_C = U, C
@@ -78,8 +78,33 @@ def test_launch_configuration_does_not_change_the_solve():
 def test_tune_set_rejects_values_out_of_range():
     h, *_ = uneven_handle(I.BASE_SEED + 78, 4, iterations=1)
     try:
-        for cfg in [(0, 256), (9, 256), (2, 64), (2, 1024)]:
+        for cfg in [(0, 256, 0), (9, 256, 0), (2, 64, 0), (2, 1024, 0), (2, 256, 3), (2, 256, -1)]:
             with pytest.raises(G.GnmppiError):
                 G.gnmppi_tune_set(h, *cfg)
+    finally:
+        G.gnmppi_destroy(h)
+
+
+def test_contraction_tile_does_not_change_the_bf16_solve():
+    """The BF16-mode contraction's two tile shapes (256 or 128 [dR; W] rows per
+    CTA) form every output from the same products in the same order."""
+    seed, batch = I.BASE_SEED + 79, 12
+    h, x0, xr, nU, _ = uneven_handle(seed, batch, precision=G.PREC_BF16)
+    try:
+        ref = None
+        for mt in (2, 1, 2):
+            G.gnmppi_tune_set(h, 1, 256, mt)
+            assert G.gnmppi_tune_report(h)["contract_mt"] == mt
+            U, C = solve(h, x0, xr, nU, batch)
+            if ref is None:
+                ref = (U, C)
+            else:
+                assert np.array_equal(U, ref[0]) and C == ref[1], f"tile {mt} changed the solve"
+        rep = G.gnmppi_autotune(h, G.MEM_HOST, x0, xr, np.zeros(nU))
+        assert rep["source"] in ("timed", "cache") and rep["contract_mt"] in (1, 2)
+        if rep["source"] == "timed":
+            assert [c["contract_mt"] for c in rep["candidates"] if "contract_mt" in c] == [2, 1]
+        U, C = solve(h, x0, xr, nU, batch)
+        assert np.array_equal(U, ref[0])
     finally:
         G.gnmppi_destroy(h)

@@ -493,36 +493,40 @@ def test_group_rollout_cost_and_uneven_mix():
 
 
 _SWEEP_ORACLE = {}
+# (M, N, K, seed): the benchmark problem, then the high-dimensional sweep's sizes
+_STEP_SIZES = [(10, 100, 2048, I.BASE_SEED + 1), (32, 200, 4096, 32), (64, 200, 4096, 64)]
 
 
-def _sweep_oracle(M):
-    """The oracle's first iteration at a sweep size (chain M, N = 200, K = 4096), cached."""
-    if M not in _SWEEP_ORACLE:
-        x0, tgt = I.chain_instances(M, 1, M)
-        m = O.chain(M=M, N=200)
-        it = O.iteration(m, O.Options(K=4096, lam=1e-3, seed=M, threads=16), x0[0], tgt[0], np.zeros(m.n), 0.2,
+def _sweep_oracle(M, N, K, seed):
+    """The oracle's first iteration of a chain at U = 0, cached per size."""
+    key = (M, N, K, seed)
+    if key not in _SWEEP_ORACLE:
+        x0, tgt = I.chain_instances(seed, 1, M)
+        m = O.chain(M=M, N=N)
+        it = O.iteration(m, O.Options(K=K, lam=1e-3, seed=seed, threads=16), x0[0], tgt[0], np.zeros(m.n), 0.2,
                          want_big=True)
-        _SWEEP_ORACLE[M] = (m, x0[0], tgt[0], it)
-    return _SWEEP_ORACLE[M]
+        _SWEEP_ORACLE[key] = (m, x0[0], tgt[0], it)
+    return _SWEEP_ORACLE[key]
 
 
 @pytest.mark.parametrize("prec", [G.PREC_FP32, G.PREC_BF16])
-@pytest.mark.parametrize("M", [32, 64])
-def test_reduced_precision_iteration_at_sweep_sizes(M, prec):
-    """The high-dimensional sweep's sizes: chain M = 32 / 64 (nx = 124 / 252),
-    N = 200 (n = 400), nR = 12862 / 25726, K = 4096, one iteration against the
-    oracle (group-per-rollout kernels).  Every sample cost and the nominal
-    cost within 1e-4; dR within 1e-4 normwise (the FP32 model keeps positions
-    relative to the initial state); the cost after the step within
+@pytest.mark.parametrize("M,N,K,seed", _STEP_SIZES)
+def test_reduced_precision_iteration_at_sweep_sizes(M, N, K, seed, prec):
+    """One iteration against the oracle at the benchmark size (chain M = 10,
+    N = 100, K = 2048) and the high-dimensional sweep's sizes (M = 32 / 64,
+    nx = 124 / 252, N = 200, n = 400, nR = 12862 / 25726, K = 4096; group-per-
+    rollout kernels).  Every sample cost and the nominal cost within 1e-4; dR
+    within 1e-4 normwise (the FP32 group model keeps positions relative to the
+    initial state); the cost after the step within
     max(1e-4, 4 kappa(J^T J + lambda I) u_FP32): the Gram's FP32 accumulation
     over nR rows, amplified by the conditioning, moves the step.  Prints the
     measured deviations (pytest -s)."""
-    m, x0, tgt, it = _sweep_oracle(M)
-    gp = G.chain_problem(M=M, N=200, K=4096, iterations=1, lam=1e-3, sigma0=0.2, seed=M, precision=prec)
+    m, x0, tgt, it = _sweep_oracle(M, N, K, seed)
+    gp = G.chain_problem(M=M, N=N, K=K, iterations=1, lam=1e-3, sigma0=0.2, seed=seed, precision=prec)
     s = G.Solver(gp, 1)
     st, U, rep = s.step(x0, tgt, np.zeros(m.n), np.full(m.n, 0.2), 0)
     Cs = s.debug("C")
-    dR = s.debug("dR").reshape(m.nR, 2048)
+    dR = s.debug("dR").reshape(m.nR, K // 2)
     s.close()
     assert st == 0
     assert rep[0].C_nom == pytest.approx(it.C_nom, rel=TOLRED)
@@ -532,7 +536,7 @@ def test_reduced_precision_iteration_at_sweep_sizes(M, prec):
     H = it.J.T @ it.J + it.lambda_used * np.eye(m.n)
     kap = np.linalg.cond(H)
     e_new = abs(rep[0].C_new - it.C_new) / it.C_new
-    print(f"\nchain M={M} N=200 K=4096 prec={prec}: dR {e_dR:.2e}, samples max "
+    print(f"\nchain M={M} N={N} K={K} prec={prec}: dR {e_dR:.2e}, samples max "
           f"{np.max(np.abs(Cs - it.C_samp) / np.abs(it.C_samp)):.2e}, C_new {e_new:.2e}, "
           f"kappa(J^T J + lambda I) {kap:.3e}, bound {max(TOLRED, 4 * kap * U32):.2e}")
     assert rep[0].C_new < rep[0].C_nom and it.C_new < it.C_nom
