@@ -51,7 +51,8 @@ namespace {
 
 constexpr int BM = 128, BN = 256;
 constexpr int ROW_BYTES = 128;  // one k-block of an FP32 row: 32 values
-constexpr int KBLK_F32 = 32;
+constexpr int KBLK_F32 = 32;    // Gram and three-pass TF32 k-block (128-byte rows, 128-byte swizzle)
+constexpr int KBLK_BF16 = 16;   // BF16-mode contraction k-block (64-byte rows, 64-byte swizzle)
 constexpr int A_BYTES = BM * ROW_BYTES;
 constexpr int B_BYTES = BN * ROW_BYTES;
 constexpr int RING_BYTES = 4 * (A_BYTES + B_BYTES);  // 192 KB of operand ring
@@ -68,34 +69,37 @@ __device__ __forceinline__ void bf16_split2(float a, float b, uint32_t& hi, uint
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// Row `row` (32 FP32 values) of a landed 128-byte-swizzled TMA tile at p:
-// 16-byte chunk c of the row sits at chunk c ^ (row & 7).
-__device__ __forceinline__ void load_row_sw128(const unsigned char* p, int row, float* v) {
+// Row `row` of a landed 64-byte-swizzled TMA box at p (16 FP32 values, one
+// contraction k-block) rewritten in place as a 64-byte BF16 row [16 heads |
+// 16 remainders] with the same swizzle (16-byte chunk j of the row at chunk
+// j ^ ((row >> 1) & 3)).  The row's four chunks are read before any is
+// written and no other row's bytes are touched, so each thread splits its
+// own rows without waiting for the others.
+__device__ __forceinline__ void split_row_sw64(unsigned char* p, int row) {
+  unsigned char* r = p + row * 64;
+  const int sw = (row >> 1) & 3;
+  float v[16];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float4 q = *reinterpret_cast<const float4*>(p + row * 128 + ((c ^ (row & 7)) << 4));
+  for (int c = 0; c < 4; ++c) {
+    const float4 q = *reinterpret_cast<const float4*>(r + ((c ^ sw) << 4));
     v[4 * c] = q.x;
     v[4 * c + 1] = q.y;
     v[4 * c + 2] = q.z;
     v[4 * c + 3] = q.w;
   }
-}
-
-// The head and remainder of those 32 values as row `row` of two K-major
-// BF16 tiles with 64-byte rows and the 64-byte swizzle (16-byte chunk j of
-// the row at chunk j ^ ((row >> 1) & 3)), the layout TMA would have written.
-__device__ __forceinline__ void store_row_sw64(unsigned char* hi, unsigned char* lo, int row, const float* v) {
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint4 H, L;
-    bf16_split2(v[8 * j], v[8 * j + 1], H.x, L.x);
-    bf16_split2(v[8 * j + 2], v[8 * j + 3], H.y, L.y);
-    bf16_split2(v[8 * j + 4], v[8 * j + 5], H.z, L.z);
-    bf16_split2(v[8 * j + 6], v[8 * j + 7], H.w, L.w);
-    const int off = row * 64 + ((j ^ ((row >> 1) & 3)) << 4);
-    *reinterpret_cast<uint4*>(hi + off) = H;
-    *reinterpret_cast<uint4*>(lo + off) = L;
-  }
+  uint4 H0, L0, H1, L1;  // heads of values 0-7 and 8-15, remainders likewise
+  bf16_split2(v[0], v[1], H0.x, L0.x);
+  bf16_split2(v[2], v[3], H0.y, L0.y);
+  bf16_split2(v[4], v[5], H0.z, L0.z);
+  bf16_split2(v[6], v[7], H0.w, L0.w);
+  bf16_split2(v[8], v[9], H1.x, L1.x);
+  bf16_split2(v[10], v[11], H1.y, L1.y);
+  bf16_split2(v[12], v[13], H1.z, L1.z);
+  bf16_split2(v[14], v[15], H1.w, L1.w);
+  *reinterpret_cast<uint4*>(r + ((0 ^ sw) << 4)) = H0;
+  *reinterpret_cast<uint4*>(r + ((1 ^ sw) << 4)) = H1;
+  *reinterpret_cast<uint4*>(r + ((2 ^ sw) << 4)) = L0;
+  *reinterpret_cast<uint4*>(r + ((3 ^ sw) << 4)) = L1;
 }
 
 // One (128 or 256) x (up to 256) tile of the BF16 mode's contraction: the A
@@ -104,17 +108,17 @@ __device__ __forceinline__ void store_row_sw64(unsigned char* hi, unsigned char*
 // D[i][j] = sum_k A[i][k] B[j][k] is stored transposed, into row j and column
 // i of [P^T | S] (columns >= ccut cgap further right): one TMEM lane per
 // output column i, so each warp store writes 32 consecutive columns.  TMA
-// lands FP32 k-blocks (32 values, 128-byte rows) of up to two 128-row A
-// sub-tiles and up to 256 B rows; four splitter warps rewrite
-// each landed 16 KB tile in place as a BF16 head tile and a BF16 remainder
-// tile (64-byte rows, 8 KB each; the B heads of both boxes fill the first B
-// box, their remainders the second), and each product is formed from three
-// BF16 passes, head x head + head x remainder + remainder x head, which keeps
+// lands FP32 k-blocks of 16 values (64-byte rows, 64-byte swizzle) of up to
+// two 128-row A sub-tiles and 256 B rows; four splitter warps rewrite every
+// landed row in place as a BF16 [head | remainder] row, and each product is
+// formed from three BF16 MMAs of K = 16 (head x head, head x remainder,
+// remainder x head, the remainders 32 bytes into the rows), which keeps
 // FP32-level accuracy (the dropped remainder x remainder term is ~2^-18
 // relative).  192 threads: warp 0 lane 0 TMA, warp 1 lane 0 MMA, warps 2-5
 // split; warps 0-3 read TMEM back.
-// MT: A sub-tiles per CTA.  MT = 2: 256 A rows, a 3-stage ring of 64 KB, one
-// CTA per SM; MT = 1: 128 A rows, a 2-stage ring of 48 KB (96 KB), two CTAs per
+//
+// MT: A sub-tiles per CTA.  MT = 2: 256 A rows, a 6-stage ring of 32 KB, one
+// CTA per SM; MT = 1: 128 A rows, a 4-stage ring of 24 KB (96 KB), two CTAs per
 // SM, whose pipelines hide each other's load latency (the W rows are then read
 // twice as often, from L2).  Same products, same accumulation order per output.
 constexpr int kContractThreads = 192;
@@ -125,20 +129,17 @@ __global__ void __launch_bounds__(kContractThreads, 3 - MT) k_contract_tc(const 
                                                                     const int4* __restrict__ tiles,
                                                                     float* __restrict__ D, int* __restrict__ err,
                                                                     int inject) {
-  constexpr int KBLK = 32;              // FP32 elements per k-block (one 128-byte row)
-  constexpr int NSUB = 2;               // BF16 MMAs (K = 16, 32 bytes) per k-block, sub-tile and pass
-  constexpr int TILE = BM * ROW_BYTES;  // one landed 128-row FP32 box (16 KB)
-  constexpr int HALF = TILE / 2;        // one 128-row BF16 tile of 64-byte rows (8 KB)
-  constexpr int MTMAX = MT;             // 128-row sub-tiles of A per tile (each its own accumulator)
-  constexpr int STAGE_BYTES = (MTMAX + 2) * TILE;
+  constexpr int KBLK = KBLK_BF16;            // FP32 values per k-block (one 64-byte row)
+  constexpr int TILE = BM * 64;              // one landed 128-row box (8 KB)
+  constexpr int STAGE_BYTES = (MT + 2) * TILE;  // A sub-tiles, then 256 B rows
   constexpr int STAGES = (MT == 2 ? RING_BYTES : RING_BYTES / 2) / STAGE_BYTES;
   constexpr int SPLITTERS = kContractThreads - 64;
-  constexpr uint32_t TCOLS = MTMAX * TMEM_COLS;
+  constexpr uint32_t TCOLS = MT * TMEM_COLS;
   const int4 tl = tiles[blockIdx.x];
   const TcJob J = jobs[tl.x];
-  // tl.y: block of 256 A rows, tl.z: block of 256 B rows, tl.w: A sub-tiles (1 or 2)
+  // tl.y: block of MT x 128 A rows, tl.z: block of 256 B rows, tl.w: A sub-tiles (1 or 2)
   const int mt = tl.w;
-  const int row_org = tl.y * MTMAX * BM;
+  const int row_org = tl.y * MT * BM;
   const uint32_t tx_bytes = (uint32_t)((mt + 2) * TILE);
   if (st[J.inst].status != 0) return;  // uniform over the CTA, before any allocation
   const int nkb = J.nkb;
@@ -147,10 +148,9 @@ __global__ void __launch_bounds__(kContractThreads, 3 - MT) k_contract_tc(const 
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
-  // bars[0..S): full (TMA landed), [S..2S): split (tiles rewritten),
-  // [2S..3S): empty (MMAs done with the stage), [3S]: done, [3S+1]: the
-  // splitters' rendezvous between reading a box and overwriting it
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 2);
+  // bars[0..S): full (TMA landed), [S..2S): split (rows rewritten),
+  // [2S..3S): empty (MMAs done with the stage), [3S]: done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -161,7 +161,6 @@ __global__ void __launch_bounds__(kContractThreads, 3 - MT) k_contract_tc(const 
       mbar_init(su32(bars + 2 * STAGES + s), 1);
     }
     mbar_init(su32(bars + 3 * STAGES), 1);
-    mbar_init(su32(bars + 3 * STAGES + 1), SPLITTERS);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -176,7 +175,7 @@ __global__ void __launch_bounds__(kContractThreads, 3 - MT) k_contract_tc(const 
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t done = su32(bars + 3 * STAGES);
-  // stage layout: A sub-tile 0, A sub-tile 1, B box 0, B box 1 (16 KB each)
+  // stage layout: A sub-tile 0, [A sub-tile 1,] B rows 0-127, B rows 128-255 (8 KB each)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
@@ -192,7 +191,7 @@ __global__ void __launch_bounds__(kContractThreads, 3 - MT) k_contract_tc(const 
       const uint32_t full = su32(bars + s);
       mbar_expect_tx(full, tx_bytes);
       const uint32_t a_dst = su32(base + s * STAGE_BYTES);
-      const uint32_t b_dst = a_dst + MTMAX * TILE;
+      const uint32_t b_dst = a_dst + MT * TILE;
       const int x = J.x0 + kb * KBLK;
       for (int q = 0; q < mt; ++q) tma_load(a_dst + q * TILE, map, full, x, J.a_row0 + row_org + q * BM);
       tma_load(b_dst, map, full, x, J.b_row0 + tl.z * BN);
@@ -205,36 +204,17 @@ __global__ void __launch_bounds__(kContractThreads, 3 - MT) k_contract_tc(const 
   } else if (warp >= 2) {
     // ---------------- splitters: thread t owns row t of every 128-row box
     const int t = threadIdx.x - 64;
-    const uint32_t rv = su32(bars + 3 * STAGES + 1);
-    uint32_t rphase = 0;
-    // every splitter has read the box before any overwrites it: arrive
-    // (releasing this thread's reads), then a bounded wait for the phase
-    auto rendezvous = [&]() -> bool {
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rv) : "memory");
-      return mbar_wait(rv, (rphase++) & 1, abort, true);
-    };
     bool alive = true;
-    for (int kb = 0; kb < nkb && alive; ++kb) {
+    for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES, round = kb / STAGES;
       if (!mbar_wait(su32(bars + s), round & 1, abort, true)) {
         alive = false;
         break;
       }
       unsigned char* sb = base + s * STAGE_BYTES;
-      float v[2 * KBLK];
-      for (int q = 0; q < mt && alive; ++q) {
-        unsigned char* a = sb + q * TILE;
-        load_row_sw128(a, t, v);
-        if (!(alive = rendezvous())) break;
-        store_row_sw64(a, a + HALF, t, v);
-      }
-      if (!alive) break;
-      unsigned char* b0 = sb + MTMAX * TILE;
-      load_row_sw128(b0, t, v);
-      load_row_sw128(b0 + TILE, t, v + KBLK);
-      if (!(alive = rendezvous())) break;
-      store_row_sw64(b0, b0 + TILE, t, v);              // B row t
-      store_row_sw64(b0, b0 + TILE, t + BM, v + KBLK);  // B row 128 + t
+      for (int q = 0; q < mt; ++q) split_row_sw64(sb + q * TILE, t);
+      split_row_sw64(sb + MT * TILE, t);       // B row t
+      split_row_sw64(sb + MT * TILE, t + BM);  // B row 128 + t
       // the generic-proxy writes become visible to the tensor core's reads
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bars + STAGES + s)) : "memory");
@@ -260,17 +240,14 @@ __global__ void __launch_bounds__(kContractThreads, 3 - MT) k_contract_tc(const 
       }
       tc_fence_after();
       const uint32_t a0 = su32(base + s * STAGE_BYTES);
-      const uint32_t bh = a0 + MTMAX * TILE, bl = bh + TILE;
-#pragma unroll
-      for (int k = 0; k < NSUB; ++k) {
-        // sub-tile q accumulates into TMEM columns [256 q, 256 q + 256)
-        for (int q = 0; q < mt; ++q) {
-          const uint32_t d = tmem + (uint32_t)(q * TMEM_COLS);
-          const uint32_t ah = a0 + q * TILE + k * 32, al = ah + HALF;
-          mma<true>(d, sdesc<true>(ah), sdesc<true>(bh + k * 32), id, (kb > 0 || k > 0) ? 1u : 0u);
-          mma<true>(d, sdesc<true>(ah), sdesc<true>(bl + k * 32), id, 1u);
-          mma<true>(d, sdesc<true>(al), sdesc<true>(bh + k * 32), id, 1u);
-        }
+      const uint32_t bh = a0 + MT * TILE, bl = bh + 32;
+      // sub-tile q accumulates into TMEM columns [256 q, 256 q + 256)
+      for (int q = 0; q < mt; ++q) {
+        const uint32_t d = tmem + (uint32_t)(q * TMEM_COLS);
+        const uint32_t ah = a0 + q * TILE, al = ah + 32;
+        mma<true>(d, sdesc<true>(ah), sdesc<true>(bh), id, kb > 0 ? 1u : 0u);
+        mma<true>(d, sdesc<true>(ah), sdesc<true>(bl), id, 1u);
+        mma<true>(d, sdesc<true>(al), sdesc<true>(bh), id, 1u);
       }
       mma_commit(su32(bars + 2 * STAGES + s));  // frees the stage once these MMAs have read it
     }
@@ -564,15 +541,18 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode(std::string& err) {
 // Rank-2 FP32 tensor map over rows of `cols` elements (row stride ld
 // elements), box = one 128-byte k-block x 128 rows, 128-byte swizzle, zero
 // fill outside.
+// FP32 rows [rows x cols] with row stride ld (elements), boxes of 128 rows x
+// kblk values: kblk = 32 with the 128-byte swizzle (Gram, three-pass TF32
+// contraction), kblk = 16 with the 64-byte swizzle (BF16-mode contraction).
 static bool encode_rows(PFN_cuTensorMapEncodeTiled_v12000 encode, CUtensorMap* m, void* gaddr, int64_t cols, int64_t ld,
-                        int64_t rows) {
+                        int64_t rows, int kblk = KBLK_F32) {
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-  cuuint32_t box[2] = {(cuuint32_t)KBLK_F32, (cuuint32_t)BM};
+  cuuint32_t box[2] = {(cuuint32_t)kblk, (cuuint32_t)BM};
   cuuint32_t estr[2] = {1, 1};
   return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, gaddr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+                kblk == KBLK_BF16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <typename P>
@@ -615,7 +595,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     }
     // contraction: one FP32 map over the instance's [dR; W] block
     if (!encode_rows(encode, &maps[b], reinterpret_cast<char*>(dRW) + 4 * (size_t)d.o_dR, d.ldK, d.ldK,
-                     d.nR + d.n)) {
+                     d.nR + d.n, bf16 ? KBLK_BF16 : KBLK_F32)) {
       err = "cuTensorMapEncodeTiled failed (contraction, instance " + std::to_string(b) + ")";
       return GNMPPI_E_CUDA;
     }
@@ -629,7 +609,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
     jc.b_row0 = bf16 ? d.nR : 0;
     jc.M = d.n;
     jc.Nc = d.nR + d.n;
-    jc.nkb = d.ldK / kblk;
+    jc.nkb = d.ldK / (bf16 ? KBLK_BF16 : KBLK_F32);
     jc.x0 = 0;
     jc.out_off = d.o_P;
     jc.ldc = d.ldP;
