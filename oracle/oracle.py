@@ -187,7 +187,7 @@ class Options:
     antithetic: bool = True
     monotone: bool = False
     threads: int = 1
-    ir_steps: int = 2
+    ir_steps: int = 1
     lam: float = 1e-3
     beta: float = 0.7
     gamma: float = 0.5

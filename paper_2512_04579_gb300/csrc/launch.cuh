@@ -54,7 +54,7 @@ void fill(Launchers* o) {
 // shorter (same rows and costs, see k_line_group).  Measured at 256 chain
 // instances (16 candidates each): M = 10 0.18 / 0.127 / 0.096 / 0.105 ms with
 // 1 / 4 / 8 / 16 lanes per candidate, M = 16 0.152 / 0.094 / 0.107 ms with 4 / 8 / 16.
-template <typename T, int FL, int G>
+template <typename T, int FL, int G, int FX = 0>
 void launch_line_group(const RollArgs& a, int ncand_total, cudaStream_t s) {
   const long lanes = (long)ncand_total * G;
   if (lanes <= 0) return;
@@ -64,7 +64,7 @@ void launch_line_group(const RollArgs& a, int ncand_total, cudaStream_t s) {
   RollArgs b = a;
   const size_t smem = (size_t)(256 / G) * (size_t)a.nmax * sizeof(float2);
   b.pre = (sizeof(T) == 4 && a.mode != 2 && smem <= 48 * 1024) ? 1 : 0;
-  k_line_group<T, FL, G><<<(unsigned)((lanes + 255) / 256), 256, b.pre ? smem : 0, s>>>(b);
+  k_line_group<T, FL, G, FX><<<(unsigned)((lanes + 255) / 256), 256, b.pre ? smem : 0, s>>>(b);
 }
 template <typename T, typename S, int F>
 void fill_chain(Launchers* o) {

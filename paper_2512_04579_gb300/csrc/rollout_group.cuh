@@ -13,7 +13,10 @@
 
 namespace gnm {
 
-template <typename T, int FL, int G>
+// FX > 0: the chain has exactly FX free masses, known at compile time, so
+// that the "slot holds a real mass" and "slot holds the forced mass" tests
+// fold to constants for every slot but the last lanes' (FX = 0: F at run time).
+template <typename T, int FL, int G, int FX = 0>
 struct ChainGroup {
   static constexpr int NXL = 4 * FL;  // lane-local state: p (2FL), v (2FL)
   static constexpr bool kRelative = false;  // positions are absolute
@@ -35,6 +38,11 @@ struct ChainGroup {
     h6 = (T)(cs.dt / 6.0);
   }
   __device__ __forceinline__ int mass(int j) const { return lg * FL + j + 1; }  // 1-based global index
+  // slot j of this lane holds a real mass / the mass the control force acts on
+  __device__ __forceinline__ bool real(int j) const { return (FX > 0 && j + 1 + (G - 1) * FL <= FX) || mass(j) <= F; }
+  __device__ __forceinline__ bool ctrl(int j) const {
+    return FX > 0 ? (j == (FX - 1) % FL && lg == (FX - 1) / FL) : mass(j) == F;
+  }
   __device__ __forceinline__ void set_reference(const double*) {}
   __device__ __forceinline__ void accel(const T* s, const T* u, T* acc) const {
     const T* v = s + 2 * FL;
@@ -49,7 +57,7 @@ struct ChainGroup {
       const T py0 = (j == 0) ? pyp : s[2 * (j - 1) + 1];
       const T dx = s[2 * j] - px0;
       const T dy = s[2 * j + 1] - py0;
-      const bool real = mass(j) <= F;
+      const bool real = this->real(j);
       const T q = real ? dx * dx + dy * dy : (T)1;
       if constexpr (sizeof(T) == 4) {
         const T rinv = rsqrtf(q);
@@ -75,11 +83,11 @@ struct ChainGroup {
       const T ny = (j + 1 < FL) ? fy[j + 1] : fyn;
       T ax = -c * v[2 * j] - fx[j] + nx;
       T ay = -c * v[2 * j + 1] - fy[j] + ny;
-      if (mass(j) == F) {
+      if (ctrl(j)) {
         ax += u[0];
         ay += u[1];
       }
-      const bool real = mass(j) <= F;
+      const bool real = this->real(j);
       acc[2 * j] = real ? ax * mass_inv : (T)0;
       acc[2 * j + 1] = real ? ay * mass_inv - g : (T)0;
     }
@@ -131,7 +139,7 @@ struct ChainGroup {
 #pragma unroll
     for (int j = 0; j < FL; ++j) {
       const int i = mass(j);
-      const bool real = i <= F;
+      const bool real = this->real(j);
       const int r0 = real ? 2 * (i - 1) : 0;
       const T px = pref_local ? pref[2 * j] : pref[2 * G * j];
       const T py = pref_local ? pref[2 * j + 1] : pref[2 * G * j + 1];
@@ -151,8 +159,8 @@ struct ChainGroup {
 // vector (formed in FP64, rounded once) plus the difference of two small
 // deviations, and the residual rows use the target's offset from the
 // reference.  Mathematically the same dynamics and residuals.
-template <int FL, int G>
-struct ChainGroup<float, FL, G> {
+template <int FL, int G, int FX>
+struct ChainGroup<float, FL, G, FX> {
   static constexpr int NXL = 4 * FL;
   static constexpr bool kRelative = true;
   float mass_inv, l0, km, k3m;
@@ -181,6 +189,11 @@ struct ChainGroup<float, FL, G> {
     for (int j = 0; j < FL; ++j) dref[j] = make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ int mass(int j) const { return lg * FL + j + 1; }
+  // slot j of this lane holds a real mass / the mass the control force acts on
+  __device__ __forceinline__ bool real(int j) const { return (FX > 0 && j + 1 + (G - 1) * FL <= FX) || mass(j) <= F; }
+  __device__ __forceinline__ bool ctrl(int j) const {
+    return FX > 0 ? (j == (FX - 1) % FL && lg == (FX - 1) / FL) : mass(j) == F;
+  }
   // Reference link vectors from the initial positions x0p (FP64, packed
   // [p_1 .. p_F]); mass 0 is fixed at the origin.
   __device__ __forceinline__ void set_reference(const double* x0p) {
@@ -205,7 +218,7 @@ struct ChainGroup<float, FL, G> {
 #pragma unroll
     for (int j = 0; j < FL; ++j) {
       d[j] = __fadd2_rn(__ffma2_rn((j == 0) ? prev : p[j - 1], mneg1, p[j]), dref[j]);
-      const bool real = mass(j) <= F;
+      const bool real = this->real(j);
       const float q = real ? fmaf(d[j].x, d[j].x, d[j].y * d[j].y) : 1.f;
       const float rinv = rsqrtf(q);
       const float dd = fmaf(q, rinv, -l0);
@@ -223,8 +236,8 @@ struct ChainGroup<float, FL, G> {
       a = __ffma2_rn(make_float2(-fr[j], -fr[j]), d[j], a);
       const float fo = (j + 1 < FL) ? fr[j + 1] : frn;
       a = __ffma2_rn(make_float2(fo, fo), (j + 1 < FL) ? d[j + 1] : dn, a);
-      if (mass(j) == F) a = __fadd2_rn(a, um);
-      acc[j] = (mass(j) <= F) ? a : make_float2(0.f, 0.f);
+      if (ctrl(j)) a = __fadd2_rn(a, um);
+      acc[j] = real(j) ? a : make_float2(0.f, 0.f);
     }
   }
   __device__ __forceinline__ void step(float* xs, const float* u) const {
@@ -268,7 +281,7 @@ struct ChainGroup<float, FL, G> {
 #pragma unroll
     for (int j = 0; j < FL; ++j) {
       const int i = mass(j);
-      const bool real = i <= F;
+      const bool real = this->real(j);
       const int r0 = real ? 2 * (i - 1) : 0;
       const float px = pref_local ? pref[2 * j] : pref[2 * G * j];
       const float py = pref_local ? pref[2 * j + 1] : pref[2 * G * j + 1];
@@ -288,7 +301,7 @@ __device__ __forceinline__ T group_sum(T v, int G, unsigned mask) {
 // k_samples for groups.  Every lane of a group emits its rows in the same
 // order and the partner group emits the same rows, so the difference is taken
 // row by row with one xor-shuffle per emitted row.
-template <typename T, typename S, int FL, int G>
+template <typename T, typename S, int FL, int G, int FX = 0>
 __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   constexpr int PAIRS = 256 / (2 * G);
   const int2 bm = a.bmap[blockIdx.x];
@@ -319,7 +332,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
     sR[k * RS + w] = rg[idx];
   }
   // targets (FP32 model: their offsets from the initial positions)
-  constexpr bool REL = ChainGroup<T, FL, G>::kRelative;
+  constexpr bool REL = ChainGroup<T, FL, G, FX>::kRelative;
   for (int idx = threadIdx.x; idx < 2 * SL; idx += blockDim.x) {
     const int q = idx >> 1;
     sRef[(q % FL) * 2 * G + 2 * (q / FL) + (idx & 1)] =
@@ -335,7 +348,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   const T sign = plus ? (T)1 : (T)-1;
   // every lane of a block works on one instance with one horizon, so whole
   // warps stay converged and shuffles use the full mask
-  ChainGroup<T, FL, G> md(a.cs, I.F, lg, 0xffffffffu);
+  ChainGroup<T, FL, G, FX> md(a.cs, I.F, lg, 0xffffffffu);
   const T uf_t = friction_threshold<T>(a.cs);
   md.pref = sRef + 2 * lg;
   md.set_reference(a.x0 + I.o_x0);
@@ -445,7 +458,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
 }
 
 // Line search / nominal / FP64 cost for groups: one group per (instance, candidate).
-template <typename T, int FL, int G>
+template <typename T, int FL, int G, int FX = 0>
 __global__ void __launch_bounds__(256) k_line_group(RollArgs a) {
   const int gid = (int)((blockIdx.x * blockDim.x + threadIdx.x) / G);
   const int lg = threadIdx.x & (G - 1);
@@ -465,11 +478,11 @@ __global__ void __launch_bounds__(256) k_line_group(RollArgs a) {
   // groups of one warp may run different instances (different horizons):
   // every shuffle is confined to this group's lanes
   const unsigned gmask = ((G == 32) ? 0xffffffffu : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
-  ChainGroup<T, FL, G> md(a.cs, I.F, lg, gmask);
+  ChainGroup<T, FL, G, FX> md(a.cs, I.F, lg, gmask);
   const T uf_t = friction_threshold<T>(a.cs);
   // targets and initial positions: the FP32 model keeps positions relative
   // to the initial ones (and the targets as offsets from them)
-  constexpr bool REL = ChainGroup<T, FL, G>::kRelative;
+  constexpr bool REL = ChainGroup<T, FL, G, FX>::kRelative;
   T ref[2 * FL];
 #pragma unroll
   for (int q = 0; q < FL; ++q) {

@@ -162,7 +162,7 @@ def _ptr(a):
 
 def make_problem(dynamics: int, *, N: int, K: int, iterations: int = 20, nx: int = 0, nu: int = 0, M: int = 0,
                  dt: float = 0.0, params=(), lin=None, L: int = 16, precision: int = PREC_FP64,
-                 jac_mode: int = JAC_AUTO, antithetic: bool = True, monotone: bool = False, ir_steps: int = 2,
+                 jac_mode: int = JAC_AUTO, antithetic: bool = True, monotone: bool = False, ir_steps: int = 1,
                  lam: float = 1e-3, sigma0: float = 0.5, beta: float = 0.7, gamma: float = 0.5, tau: float = 1.0,
                  seed: int = 0, sampling: int = 0, method: int = 0, first_instance: int = 0) -> Problem:
     p = Problem()
