@@ -73,7 +73,10 @@ enum {
   GNMPPI_PREC_FP32 = 1, /* FP32 rollouts with compensated cost sums; contraction and Gram
                            on the tensor cores from three TF32 passes over FP32 operands
                            split into head and remainder (FP32-level accuracy, FP32
-                           accumulation); FP64 Cholesky with iterative refinement         */
+                           accumulation); FP64 Cholesky with iterative refinement.  An
+                           LSQ system that does not factor is retried with 1e-5, 1e-4,
+                           1e-3 of diag(P^T P) added before lambda grows (the Gram's
+                           rounding can leave it indefinite when K' is close to n)       */
   GNMPPI_PREC_BF16 = 2  /* as FP32, but the contraction's FP32 operands are split in shared
                            memory into a BF16 head and a BF16 remainder and contracted by
                            three BF16 passes (head x head + head x remainder + remainder x

@@ -382,10 +382,13 @@ __global__ void __launch_bounds__(256) k_gemm_nt(GemmArgs g) {
 // H = A + lambda T (T = S^2 in LSQ mode, diag((K' s^2)^2) in SIGMA mode),
 // taken from its lower triangle into the packed copy Hp (kept for the
 // refinement residual) and the factor scratch L.  Coalesced along the packed
-// index.
+// index.  tau > 0 (the reduced-precision modes' LSQ systems) adds
+// tau diag(A): the tensor-core Gram's entries carry ~1e-5 of sqrt(A_ii A_jj)
+// of rounding, and when K' is barely above n, S^2 is so small in some
+// directions that this rounding leaves A + lambda S^2 indefinite.
 __device__ __forceinline__ void build_system(const double* __restrict__ A, const double* __restrict__ S2,
                                              const double* __restrict__ s, bool lsq, double Keff, double lam,
-                                             double* __restrict__ Hp, double* __restrict__ L, int n) {
+                                             double tau, double* __restrict__ Hp, double* __restrict__ L, int n) {
   const int np = n * (n + 1) / 2;
 #pragma unroll 4
   for (int u = threadIdx.x; u < np; u += blockDim.x) {
@@ -401,7 +404,7 @@ __device__ __forceinline__ void build_system(const double* __restrict__ A, const
       const double sc = Keff * s[r] * s[r];
       t = (r == c) ? sc * sc : 0.0;
     }
-    const double h = A[i] + lam * t;
+    const double h = A[i] + lam * t + ((r == c && lsq) ? tau * A[i] : 0.0);
     Hp[u] = h;
     L[u] = h;
   }
@@ -441,6 +444,30 @@ __device__ __forceinline__ double srow_dot(const float* S, const double*, const 
 // other instances on the SM keep the FP64 pipe busy through this one's
 // latency-bound steps.  Instances run in the order a.order gives (largest n
 // first).
+// Retry ladder of a failed factorisation.  FP64 products (parity mode), and
+// the printed form: lambda x 10 per retry, as the oracle.  FP32 tensor-core
+// products in LSQ form: first the diagonal shifts tau = 1e-5, 1e-4, 1e-3 of
+// diag(A) at the stated lambda (the Gram's measured entry error is 1.2e-5 to
+// 3e-5 of sqrt(A_ii A_jj)), then lambda x 10 per retry with tau = 1e-3.  A
+// system that factors at once is solved unchanged.
+template <typename TA>
+__device__ __forceinline__ void retry_ladder(int attempt, bool lsq, double lam0, double& lam, double& tau) {
+  if (sizeof(TA) == 4 && lsq) {
+    if (attempt <= 3) {
+      tau = attempt == 0 ? 0.0 : (attempt == 1 ? 1e-5 : (attempt == 2 ? 1e-4 : 1e-3));
+      lam = lam0;
+    } else {
+      tau = 1e-3;
+      lam = lam0;
+      for (int q = 3; q < attempt; ++q) lam *= 10.0;
+    }
+  } else {
+    tau = 0.0;
+    lam = lam0;
+    for (int q = 0; q < attempt; ++q) lam *= 10.0;
+  }
+}
+
 template <typename TA, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) k_solve(SolveArgs a) {
   const int b = a.order[blockIdx.x];
@@ -494,13 +521,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_solve(SolveArgs a) {
     }
     const bool forced = inj && (a.cs.inj_kind == 2 || lsq);
     for (retries = 0; retries <= 6; ++retries) {
-      build_system(A, S2, s, lsq, Keff, lam, Hp, L, n);
+      double tau = 0.0;
+      retry_ladder<TA>(retries, lsq, a.cs.lambda, lam, tau);
+      build_system(A, S2, s, lsq, Keff, lam, tau, Hp, L, n);
       __syncthreads();
       if (chol_factor(L, invd, Y, n, &fail) && !forced) {
         ok = true;
         break;
       }
-      lam *= 10.0;
       __syncthreads();
     }
   }

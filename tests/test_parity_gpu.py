@@ -543,6 +543,41 @@ def test_reduced_precision_iteration_at_sweep_sizes(M, N, K, seed, prec):
     assert e_new <= max(TOLRED, 4.0 * kap * U32)
 
 
+def test_reduced_precision_indefinite_lsq_system_takes_the_diagonal_shift():
+    """The same near-singular draw without injection.  The FP64 mode factors
+    the damped LSQ system at once, like the oracle.  In the reduced modes the
+    tensor-core Gram's rounding (~1e-5 of sqrt(A_ii A_jj)) can leave
+    P^T P + lambda S^2 indefinite when S is this ill-conditioned; the retry
+    then adds tau diag(A) (tau = 1e-5, 1e-4, 1e-3) at the stated lambda
+    before it raises lambda, so the step stays in the LSQ form at lambda =
+    1e-3 and close to the oracle's (the shift perturbs the system by at most
+    1e-3 of its diagonal)."""
+    seed = I.BASE_SEED + 77
+    Ms, Ns, Ks, x0s, tgts = I.uneven_chain_instances(seed, 24)
+    b = 23
+    M, N, K = int(Ms[b]), int(Ns[b]), int(Ks[b])
+    m = O.chain(M=M, N=N)
+    ref = O.iteration(m, O.Options(K=K, lam=1e-3, seed=seed, threads=8), x0s[b], tgts[b], np.zeros(m.n), 0.2,
+                      inst=0, it=0)
+    assert ref.status == 0 and ref.jac_mode_used == 0 and ref.chol_retries == 0
+    for prec in (G.PREC_FP64, G.PREC_FP32, G.PREC_BF16):
+        gp = G.chain_problem(M=M, N=N, K=K, iterations=1, lam=1e-3, sigma0=0.2, seed=seed, precision=prec)
+        s = G.Solver(gp, 1)
+        st, U, rep = s.step(x0s[b], tgts[b], np.zeros(m.n), np.full(m.n, 0.2), 0)
+        s.close()
+        r = rep[0]
+        print(f"\nprec={prec}: retries {r.chol_retries}, lambda {r.lambda_used:.1e}, jac_mode {r.jac_mode_used}, "
+              f"C_new {r.C_new:.9e} vs oracle {ref.C_new:.9e} ({abs(r.C_new - ref.C_new) / ref.C_nom:.2e} of C_nom)")
+        assert st == 0 and r.status == 0 and r.jac_mode_used == 0
+        if prec == G.PREC_FP64:
+            assert r.chol_retries == 0
+            assert r.C_new == pytest.approx(ref.C_new, rel=2e-6)
+        else:
+            assert r.chol_retries <= 3 and r.lambda_used == 1e-3
+            assert r.C_new < r.C_nom
+            assert abs(r.C_new - ref.C_new) <= 1e-3 * ref.C_nom
+
+
 def test_reduced_precision_lsq_breakdown_takes_the_printed_form():
     """K' = 256 pairs barely above n = 246: S is nearly singular (kappa(S)
     ~ 5.6e3), the case the LSQ-breakdown reading of Eq. 9 exists for.  With
