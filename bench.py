@@ -42,7 +42,7 @@ DTYPE = "f32 rollouts, bf16 head+remainder contractions (3 passes, f32 accumulat
 
 # DRAM read + write of one k_samples launch of the default workload (256 instances), from one
 # full-size ncu capture of this command (one-pass metrics); null for other batch sizes.
-K_SAMPLES_TRAFFIC_B256 = 2.2802e9
+K_SAMPLES_TRAFFIC_B256 = 2.4886e9
 
 
 def load_cstar(path=CSTAR):

@@ -65,6 +65,7 @@ struct gnmppi_s {
   double *d_S2 = nullptr, *d_H = nullptr, *d_Cl = nullptr, *d_Cout = nullptr, *d_lin = nullptr, *d_Lg = nullptr;
   int64_t* d_oL = nullptr;
   void *d_dR = nullptr, *d_W = nullptr, *d_P = nullptr, *d_r = nullptr, *d_RL = nullptr;
+  uint32_t* d_W2 = nullptr;  // BF16 mode: W split into BF16 head and remainder (the contraction's B rows)
   int64_t n_x0 = 0, n_xref = 0, n_U = 0, n_dR = 0, n_W = 0, n_C = 0, n_P = 0, n_nn = 0, n_R = 0, n_RL = 0, n_L = 0;
   size_t szT = 8, szS = 8, szA = 8;
   int4* d_tiles[3] = {nullptr, nullptr, nullptr};
@@ -328,6 +329,8 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
     d.o_dR = odR;
     d.o_W = odR + (int64_t)d.nR * d.ldK;
     odR += (int64_t)(d.nR + d.n) * d.ldK;
+    d.o_W2 = oW;  // the BF16 mode's split W copy, [n][ldK] words
+    oW += (int64_t)d.n * d.ldK;
     d.o_C = oC; oC += 2 * (int64_t)d.Kp;
     d.o_P = oP; oP += (int64_t)d.n * d.ldP;
     d.o_nn = onn; onn += (int64_t)d.n * d.n;
@@ -377,6 +380,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   AL(h->d_Cout, 8 * (int64_t)h->batch);
   AL(h->d_dR, h->szS * h->n_dR);
   h->d_W = h->d_dR;
+  if (p.precision == kBF16) AL(h->d_W2, 4 * h->n_W);
   AL(h->d_P, h->szA * h->n_P);
   AL(h->d_r, h->szT * h->n_R);
   AL(h->d_RL, h->szT * h->n_RL);
@@ -481,7 +485,7 @@ static gnmppi_status build(gnmppi_t h, const gnmppi_instance_shape* shapes) {
   // tensor-core contraction (three TF32 passes, or three BF16 passes, over FP32 operands)
   h->use_tc = prec != kFP64;
   if (h->use_tc) {
-    st = tc_plan_create(h->desc, h->d_dR, h->d_P, prec == kBF16 ? 1 : 0, h->stream, &h->tc, h->err);
+    st = tc_plan_create(h->desc, h->d_dR, h->d_W2, h->d_P, prec == kBF16 ? 1 : 0, h->stream, &h->tc, h->err);
     for (void* q : h->tc.allocs) h->allocs.push_back(q);
     if (st != GNMPPI_OK) return st;
   }
@@ -597,6 +601,7 @@ static RollArgs roll_args(gnmppi_t h, uint32_t it) {
   a.r = h->d_r;
   a.dR = h->d_dR;
   a.W = h->d_W;
+  a.W2 = h->d_W2;
   a.C = h->d_C;
   a.e = h->d_e;
   a.RL = h->d_RL;

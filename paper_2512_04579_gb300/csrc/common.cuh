@@ -3,6 +3,7 @@
 // sums, and the dynamics / residual models (Sec. 2, Eq. 1-4 of arXiv
 // 2512.04579).  Internal; not part of the C ABI.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -68,6 +69,7 @@ struct InstDesc {
   int32_t sP;                           // column of S in a [P^T | S] row: nR rounded up to 32 (16-byte aligned)
   int64_t o_x0, o_xref, o_U;            // packed double arrays (x0; xref; U, s, delta, g, ...)
   int64_t o_dR, o_W;                    // dR [nR][ldK], W [n][ldK] (storage type)
+  int64_t o_W2;                         // BF16 mode: W split into BF16 head and remainder, [n][ldK] words
   int64_t o_C;                          // sample costs [Kp][2] (double), e and weights [Kp]
   int64_t o_P;                          // [P^T | S]  [n][ldP] (accumulation type)
   int64_t o_nn;                         // n*n double arrays (A, S2, H)
@@ -199,6 +201,20 @@ struct Acc<float> {
 // One dR / W slot in the storage type (FP64 in the FP64 mode, FP32 otherwise).
 __device__ __forceinline__ void put(double* p, double v) { *p = v; }
 __device__ __forceinline__ void put(float* p, float v) { *p = v; }
+
+// Sample m of row j of the BF16 mode's split copy of W: the BF16 head of w
+// (round to nearest even) and the BF16 rounding of its remainder w - head,
+// laid out per 16 samples as 16 heads then 16 remainders (one 64-byte row of
+// the contraction's BF16 operand for that k-block).  row: the copy's row j,
+// ldK words = 2 ldK BF16 slots.  The same arithmetic as the contraction's
+// in-place split of FP32 W rows.
+__device__ __forceinline__ void put_w2(uint16_t* row, int m, float w) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(w);
+  const __nv_bfloat16 l = __float2bfloat16_rn(w - __bfloat162float(h));
+  const int i = (m >> 4) * 32 + (m & 15);
+  row[i] = __bfloat16_as_ushort(h);
+  row[i + 16] = __bfloat16_as_ushort(l);
+}
 
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(float x) { return (double)x; }

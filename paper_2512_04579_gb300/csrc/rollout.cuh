@@ -28,6 +28,7 @@ struct RollArgs {
   const void* r;      // nominal residual [nR] per instance (scalar type)
   void* dR;           // [nR][ldK] storage type
   void* W;            // [n][ldK]  storage type
+  uint32_t* W2;       // BF16 mode: W's head/remainder copy [n][ldK] words (else null)
   double* C;          // [Kp][2]
   double* e;          // [Kp]
   void* RL;           // [L][nR] scalar type
@@ -43,6 +44,15 @@ struct RollArgs {
   int pre;            // k_line_group: controls staged in dynamic shared memory
                       // (candidates of the CTA x nmax float2), else formed per step
 };
+
+// Sample m of W row j, and in the BF16 mode (W2b not null) its split copy.
+template <typename S, typename V>
+__device__ __forceinline__ void put_w(S* Wm, uint32_t* W2b, int ldK, int j, int m, V w) {
+  put(Wm + (int64_t)j * ldK + m, (S)w);
+  if constexpr (sizeof(S) == 4) {
+    if (W2b) put_w2(reinterpret_cast<uint16_t*>(W2b + (int64_t)j * ldK), m, (float)w);
+  }
+}
 
 // Models that read a per-instance reference (the chain's target positions)
 // get it from a caller-staged copy in the scalar type.
@@ -152,6 +162,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
 
   S* dR = reinterpret_cast<S*>(a.dR) + I.o_dR + m;  // this sample's column
   S* Wm = reinterpret_cast<S*>(a.W) + I.o_W;
+  uint32_t* W2b = a.W2 ? a.W2 + I.o_W2 : nullptr;
   Acc<T> cost, eacc;
   SampleEmit<T, S, ANTI> em{dR, sR, I.ldK, par, 0, I.nR, active, sign, (T)0, (T)0};
   const uint32_t mm = active ? (uint32_t)m : 0u;
@@ -173,7 +184,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
         const int j = k * NU + c;
         const T w = (j == m) ? sS[j] * sqrtn : (T)0;
         u[c] = sU[j] + sign * w;
-        if (active && par == 0 && GNM_IN(j, I.n)) put(Wm + (int64_t)j * I.ldK + m, w);
+        if (active && par == 0 && GNM_IN(j, I.n)) put_w(Wm, W2b, I.ldK, j, m, w);
       }
     } else if (SHARE) {
       if ((k & 1) == 0) {
@@ -194,7 +205,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
         const int j = k * NU + c;
         const T w = sS[j] * (c ? z1 : z0);
         u[c] = sU[j] + sign * w;
-        if (active && par == c && GNM_IN(j, I.n)) put(Wm + (int64_t)j * I.ldK + m, w);
+        if (active && par == c && GNM_IN(j, I.n)) put_w(Wm, W2b, I.ldK, j, m, w);
       }
     } else {
 #pragma unroll
@@ -207,7 +218,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
         }
         const T w = sS[j] * ((j & 1) ? z1 : z0);
         u[c] = sU[j] + sign * w;
-        if (active && par == (ANTI ? (j & 1) : 0) && GNM_IN(j, I.n)) put(Wm + (int64_t)j * I.ldK + m, w);
+        if (active && par == (ANTI ? (j & 1) : 0) && GNM_IN(j, I.n)) put_w(Wm, W2b, I.ldK, j, m, w);
       }
     }
     em.col = dR + k * stage_stride;
@@ -248,7 +259,7 @@ __global__ void __launch_bounds__(128) k_samples(RollArgs a) {
     if (!ok) {  // dropped pair: its columns leave P and S
       const int rows = I.N * Model::RPS + Model::RT;
       for (int row = par; row < rows; row += (ANTI ? 2 : 1)) put(dR + (int64_t)row * I.ldK + m, (T)0);
-      for (int j = par; j < I.n; j += (ANTI ? 2 : 1)) put(Wm + (int64_t)j * I.ldK + m, (T)0);
+      for (int j = par; j < I.n; j += (ANTI ? 2 : 1)) put_w(Wm, W2b, I.ldK, j, m, (T)0);
     }
   }
 }

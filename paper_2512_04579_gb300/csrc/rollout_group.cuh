@@ -365,6 +365,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   }
   S* dR = reinterpret_cast<S*>(a.dR) + I.o_dR;
   S* Wm = reinterpret_cast<S*>(a.W) + I.o_W;
+  uint32_t* W2b = a.W2 ? a.W2 + I.o_W2 : nullptr;
   Acc<T> cost, eacc;
   const uint32_t mm = active ? (uint32_t)m : 0u;
   // Per-row difference emitter: the + group owns row r0 and the - group row
@@ -413,8 +414,8 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
     const T w0 = sS[2 * k] * z0, w1 = sS[2 * k + 1] * z1;
     const T u[2] = {sU[2 * k] + sign * w0, sU[2 * k + 1] + sign * w1};
     if (active && plus && lg == 0 && GNM_IN(2 * k + 1, I.n)) {
-      put(Wm + (int64_t)(2 * k) * I.ldK + m, w0);
-      put(Wm + (int64_t)(2 * k + 1) * I.ldK + m, w1);
+      put_w(Wm, W2b, I.ldK, 2 * k, m, w0);
+      put_w(Wm, W2b, I.ldK, 2 * k + 1, m, w1);
     }
     em.base = k * rps;
     em.r = sR + k * RS;
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(256, 2) k_samples_group(RollArgs a) {
   if (active && plus && !ok) {  // dropped pair: its columns leave P and S
     const int rows = I.N * rps + 2 * I.F;
     for (int row = lg; row < rows; row += G) put(dR + (int64_t)row * I.ldK + m, (T)0);
-    for (int j = lg; j < I.n; j += G) put(Wm + (int64_t)j * I.ldK + m, (T)0);
+    for (int j = lg; j < I.n; j += G) put_w(Wm, W2b, I.ldK, j, m, (T)0);
   }
 }
 

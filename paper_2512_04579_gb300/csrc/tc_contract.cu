@@ -108,14 +108,15 @@ __device__ __forceinline__ void split_row_sw64(unsigned char* p, int row) {
 // D[i][j] = sum_k A[i][k] B[j][k] is stored transposed, into row j and column
 // i of [P^T | S] (columns >= ccut cgap further right): one TMEM lane per
 // output column i, so each warp store writes 32 consecutive columns.  TMA
-// lands FP32 k-blocks of 16 values (64-byte rows, 64-byte swizzle) of up to
-// two 128-row A sub-tiles and 256 B rows; four splitter warps rewrite every
-// landed row in place as a BF16 [head | remainder] row, and each product is
-// formed from three BF16 MMAs of K = 16 (head x head, head x remainder,
-// remainder x head, the remainders 32 bytes into the rows), which keeps
-// FP32-level accuracy (the dropped remainder x remainder term is ~2^-18
-// relative).  192 threads: warp 0 lane 0 TMA, warp 1 lane 0 MMA, warps 2-5
-// split; warps 0-3 read TMEM back.
+// lands k-blocks of 16 values (64-byte rows, 64-byte swizzle): the FP32 rows
+// of up to two 128-row A sub-tiles, which four splitter warps rewrite in
+// place as BF16 [head | remainder] rows, and 256 B rows from the rollouts'
+// BF16 copy of W, which arrive in that layout already (split once per
+// iteration instead of once per tile).  Each product is formed from three
+// BF16 MMAs of K = 16 (head x head, head x remainder, remainder x head, the
+// remainders 32 bytes into the rows), which keeps FP32-level accuracy (the
+// dropped remainder x remainder term is ~2^-18 relative).  192 threads: warp
+// 0 lane 0 TMA, warp 1 lane 0 MMA, warps 2-5 split; warps 0-3 read TMEM back.
 //
 // MT: A sub-tiles per CTA.  MT = 2: 256 A rows, a 6-stage ring of 32 KB, one
 // CTA per SM; MT = 1: 128 A rows, a 4-stage ring of 24 KB (96 KB), two CTAs per
@@ -144,6 +145,7 @@ __global__ void __launch_bounds__(kContractThreads, 3 - MT) k_contract_tc(const 
   if (st[J.inst].status != 0) return;  // uniform over the CTA, before any allocation
   const int nkb = J.nkb;
   const CUtensorMap* map = maps + J.map;
+  const CUtensorMap* map2 = maps + J.map2;
 
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
@@ -180,6 +182,7 @@ __global__ void __launch_bounds__(kContractThreads, 3 - MT) k_contract_tc(const 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map2) : "memory");
     int issued = 0;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES, round = kb / STAGES;
@@ -194,8 +197,9 @@ __global__ void __launch_bounds__(kContractThreads, 3 - MT) k_contract_tc(const 
       const uint32_t b_dst = a_dst + MT * TILE;
       const int x = J.x0 + kb * KBLK;
       for (int q = 0; q < mt; ++q) tma_load(a_dst + q * TILE, map, full, x, J.a_row0 + row_org + q * BM);
-      tma_load(b_dst, map, full, x, J.b_row0 + tl.z * BN);
-      tma_load(b_dst + TILE, map, full, x, J.b_row0 + tl.z * BN + BM);
+      // the B rows land already split (the rollouts' BF16 W copy, rows 0..n)
+      tma_load(b_dst, map2, full, x, tl.z * BN);
+      tma_load(b_dst + TILE, map2, full, x, tl.z * BN + BM);
       ++issued;
     }
     // every copy this thread issued has landed before the CTA may exit
@@ -213,8 +217,6 @@ __global__ void __launch_bounds__(kContractThreads, 3 - MT) k_contract_tc(const 
       }
       unsigned char* sb = base + s * STAGE_BYTES;
       for (int q = 0; q < mt; ++q) split_row_sw64(sb + q * TILE, t);
-      split_row_sw64(sb + MT * TILE, t);       // B row t
-      split_row_sw64(sb + MT * TILE, t + BM);  // B row 128 + t
       // the generic-proxy writes become visible to the tensor core's reads
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bars + STAGES + s)) : "memory");
@@ -573,14 +575,18 @@ static void gram_tiles(int job, int n, std::vector<int4>& out) {
   }
 }
 
-gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void* P, int bf16, cudaStream_t stream,
-                             TcPlan* plan, std::string& err) {
+gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const uint32_t* W2, void* P, int bf16,
+                             cudaStream_t stream, TcPlan* plan, std::string& err) {
   plan->bf16 = bf16;
   auto encode = get_encode(err);
   if (!encode) return GNMPPI_E_CUDA;
   const int kblk = KBLK_F32;
   const int nb = (int)desc.size();
-  std::vector<CUtensorMap> maps(3 * (size_t)nb);
+  if (bf16 && !W2) {
+    err = "the BF16 contraction needs the split W copy";
+    return GNMPPI_E_ARG;
+  }
+  std::vector<CUtensorMap> maps(4 * (size_t)nb);
   std::vector<TcJob> jobs(3 * (size_t)nb);
   std::vector<int4> tc, tc1, tg, ts;
   for (int b = 0; b < nb; ++b) {
@@ -599,10 +605,17 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void*
       err = "cuTensorMapEncodeTiled failed (contraction, instance " + std::to_string(b) + ")";
       return GNMPPI_E_CUDA;
     }
+    // BF16 mode: the B rows come from the rollouts' split W copy
+    if (bf16 && !encode_rows(encode, &maps[3 * nb + b], const_cast<uint32_t*>(W2) + d.o_W2, d.ldK, d.ldK, d.n,
+                             KBLK_BF16)) {
+      err = "cuTensorMapEncodeTiled failed (split W, instance " + std::to_string(b) + ")";
+      return GNMPPI_E_CUDA;
+    }
     TcJob& jc = jobs[b];
     jc = TcJob{};
     jc.inst = b;
     jc.map = b;
+    jc.map2 = 3 * nb + b;
     // BF16 kernel: A side = the [dR; W] rows, B side = the W rows; three-pass
     // TF32 kernel: A side = the W rows, B side = the [dR; W] rows
     jc.a_row0 = bf16 ? 0 : d.nR;

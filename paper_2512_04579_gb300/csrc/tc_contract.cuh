@@ -21,6 +21,7 @@ namespace gnm {
 // stored cgap further right (the S block of [P^T | S] starts aligned).
 struct TcJob {
   int32_t inst, map;
+  int32_t map2, pad0;  // BF16-mode contraction: tensor map of the split W copy (the B rows)
   int32_t a_row0, b_row0;
   int32_t M, Nc, nkb, x0;
   int64_t out_off;
@@ -41,11 +42,13 @@ struct TcPlan {
   std::vector<void*> allocs;
 };
 
-// dRW: the combined per-instance FP32 [nR + n][ldK] operand block; P: the
-// FP32 [P^T | S] array (S from column sP on); bf16 selects the contraction's
-// BF16 passes (otherwise TF32).  Builds tensor maps, jobs and tile lists.
-gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, void* P, int bf16, cudaStream_t stream,
-                             TcPlan* plan, std::string& err);
+// dRW: the combined per-instance FP32 [nR + n][ldK] operand block; W2 (BF16
+// mode): W split into BF16 head and remainder by the rollouts, [n][ldK]
+// words per instance at InstDesc::o_W2; P: the FP32 [P^T | S] array (S from
+// column sP on); bf16 selects the contraction's BF16 passes (otherwise TF32).
+// Builds tensor maps, jobs and tile lists.
+gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const uint32_t* W2, void* P, int bf16,
+                             cudaStream_t stream, TcPlan* plan, std::string& err);
 
 // [P^T | S] = W^T [dR | W] into P (FP32).  inject != 0 (tests only): every
 // CTA's first MMA-side wait is on a barrier that nothing completes, so it
