@@ -5,18 +5,19 @@
 //   S[i][k]   = sum_m W_m[i] W_m[k]
 // with the sample index m as the reduction dimension.  dR and W of an instance
 // are stored as one [nR + n][ldK] block (sample-contiguous rows), so one TMA
-// tensor map per instance covers both operands: the A tile is rows nR + i of
-// the block, the B tile rows j.  Both reduced-precision modes keep FP32-level
-// accuracy (a single TF32 or BF16 pass does not: its operand rounding moves
-// the Gauss-Newton step, and the cost after it, by up to 1e-3 / 1e-2 at
-// 10^4 residual rows):
+// tensor map per instance covers both operands.  Both reduced-precision modes
+// keep FP32-level accuracy (a single TF32 or BF16 pass does not: its operand
+// rounding moves the Gauss-Newton step, and the cost after it, by up to
+// 1e-3 / 1e-2 at 10^4 residual rows):
 //    BF16 mode (k_contract_tc): one CTA computes the products of up to 256
 //      rows of the [dR; W] block (two 128-row sub-tiles, each with its own
 //      256-column TMEM accumulator) with up to 256 W rows, from three
 //      kind::f16 passes per product:
-//        warp 0 lane 0  issues TMA loads of FP32 k-blocks into a 3-stage ring,
-//        warps 2-5      rewrite each landed box in place as a BF16 head tile
-//                       and a BF16 remainder tile,
+//        warp 0 lane 0  issues TMA loads of 16-value k-blocks into a 6-stage
+//                       ring: the FP32 [dR; W] rows, and the W rows from the
+//                       rollouts' BF16 head/remainder copy of W,
+//        warps 2-5      rewrite each landed FP32 row in place as a BF16
+//                       [head | remainder] row (each thread its own rows),
 //        warp 1 lane 0  issues tcgen05.mma (M=128, N = the W rows, K=16) per
 //                       sub-tile,
 //        warps 0-3      read TMEM back (tcgen05.ld 32x32b, one lane per
@@ -55,7 +56,7 @@ constexpr int KBLK_F32 = 32;    // Gram and three-pass TF32 k-block (128-byte ro
 constexpr int KBLK_BF16 = 16;   // BF16-mode contraction k-block (64-byte rows, 64-byte swizzle)
 constexpr int A_BYTES = BM * ROW_BYTES;
 constexpr int B_BYTES = BN * ROW_BYTES;
-constexpr int RING_BYTES = 4 * (A_BYTES + B_BYTES);  // 192 KB of operand ring
+constexpr int RING_BYTES = 4 * (A_BYTES + B_BYTES);  // 192 KB of operand ring (every kernel here)
 constexpr int TMEM_COLS = 256;
 
 // BF16 heads of two adjacent FP32 values (round to nearest even) and the
