@@ -77,10 +77,12 @@ enum {
                            LSQ system that does not factor is retried with 1e-5, 1e-4,
                            1e-3 of diag(P^T P) added before lambda grows (the Gram's
                            rounding can leave it indefinite when K' is close to n)       */
-  GNMPPI_PREC_BF16 = 2  /* as FP32, but the contraction's FP32 operands are split in shared
-                           memory into a BF16 head and a BF16 remainder and contracted by
-                           three BF16 passes (head x head + head x remainder + remainder x
-                           head, FP32 accumulation; 16 significant bits per operand)       */
+  GNMPPI_PREC_BF16 = 2  /* as FP32, but the contraction's FP32 operands are split into a
+                           BF16 head and a BF16 remainder (the [dR; W] rows in shared memory,
+                           the W rows once by the rollouts, which keep a split copy of W)
+                           and contracted by three BF16 passes (head x head + head x
+                           remainder + remainder x head, FP32 accumulation; 16 significant
+                           bits per operand)                                               */
 };
 
 /* Jacobian estimator (Eq. 7).  dR_m = (R(U+W_m) - R(U-W_m))/2 (antithetic) or
