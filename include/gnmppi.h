@@ -77,11 +77,11 @@ enum {
                            LSQ system that does not factor is retried with 1e-5, 1e-4,
                            1e-3 of diag(P^T P) added before lambda grows (the Gram's
                            rounding can leave it indefinite when K' is close to n)       */
-  GNMPPI_PREC_BF16 = 2  /* as FP32, but the contraction's FP32 operands are split into a
-                           BF16 head and a BF16 remainder (the [dR; W] rows in shared memory,
-                           the W rows once by the rollouts, which keep a split copy of W)
-                           and contracted by three BF16 passes (head x head + head x
-                           remainder + remainder x head, FP32 accumulation; 16 significant
+  GNMPPI_PREC_BF16 = 2  /* as FP32, but the contraction's and the Gram's FP32 operands are
+                           split into a BF16 head and a BF16 remainder (in shared memory;
+                           the contraction's W rows once by the rollouts, which keep a split
+                           copy of W) and multiplied by three BF16 passes (head x head + head
+                           x remainder + remainder x head, FP32 accumulation; 16 significant
                            bits per operand)                                               */
 };
 

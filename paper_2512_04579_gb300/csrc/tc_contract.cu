@@ -339,15 +339,22 @@ __device__ __forceinline__ void split_block(unsigned char* p, int delta, int n4,
 // rows b_row0 + j of the instance's FP32 [dR; W] map), FP32 output into out0
 // with the S columns moved to sP; otherwise A = out0 or S2 in FP64.
 constexpr int kGramThreads = 192;
-template <bool CONTRACT>
+// BF (the BF16 mode's Gram, CONTRACT false only): k-blocks of 16 FP32 values
+// (64-byte rows, 64-byte swizzle) split in place row by row into BF16
+// [head | remainder] rows, three kind::f16 passes; B rows and (off the
+// diagonal) A rows only, no separate remainder area, so up to 8 stages.
+template <bool CONTRACT, bool BF = false>
 __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
                                                     const InstState* __restrict__ st, const int4* __restrict__ tiles,
                                                     void* __restrict__ out0, double* __restrict__ S2,
                                                     int* __restrict__ err, int inject) {
   using TO = typename std::conditional<CONTRACT, float, double>::type;
-  constexpr int KBLK = 32, NSUB = 4;  // FP32 elements per k-block, TF32 MMAs (K = 8) per k-block
+  static_assert(!(CONTRACT && BF), "the BF16 contraction is k_contract_tc");
+  // FP32 elements per k-block; MMAs (TF32 K = 8, BF16 K = 16) per k-block
+  constexpr int KBLK = BF ? KBLK_BF16 : 32, NSUB = BF ? 1 : 4;
+  constexpr int RB = BF ? 64 : ROW_BYTES;  // bytes of one landed row of a k-block
   constexpr int SPLITTERS = kGramThreads - 64;  // warps 2-5
-  constexpr int MAXST = 3;
+  constexpr int MAXST = BF ? 8 : 3;
   const int4 tl = tiles[blockIdx.x];
   const TcJob J = jobs[tl.x];
   const int mt = tl.w & 3;
@@ -355,9 +362,12 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
   const int row_org = tl.y, col_org = tl.z;
   const int kept = min(BN, J.Nc - col_org);  // output columns of this tile = B rows
   const int nbox = kept > BM ? 2 : 1;        // 128-row TMA boxes of B
-  const int stage_bytes = diag ? 2 * B_BYTES : 2 * (B_BYTES + A_BYTES);
-  const int stages = RING_BYTES / stage_bytes;  // 3 (diagonal) or 2
-  const uint32_t tx_bytes = (uint32_t)(nbox * BM * ROW_BYTES + (diag ? 0 : A_BYTES));
+  // TF32: B head, B remainder (256 rows each) [, A head, A remainder];
+  // BF16: 256 B rows [, 128 A rows], each split in place
+  const int stage_bytes = BF ? (diag ? BN * RB : (BN + BM) * RB) : (diag ? 2 * B_BYTES : 2 * (B_BYTES + A_BYTES));
+  const int stages = min(MAXST, RING_BYTES / stage_bytes);  // TF32: 3 (diagonal) or 2; BF16: 8
+  const int a_off = BF ? BN * RB : 2 * B_BYTES;              // A rows of an off-diagonal stage
+  const uint32_t tx_bytes = (uint32_t)(nbox * BM * RB + (diag ? 0 : BM * RB));
   const uint32_t tcols = mt == 2 ? 2 * TMEM_COLS : TMEM_COLS;
   if (st[J.inst].status != 0) return;  // uniform over the CTA, before any allocation
   const int nkb = J.nkb;
@@ -410,8 +420,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
       mbar_expect_tx(full, tx_bytes);
       const uint32_t b_dst = su32(base + s * stage_bytes);
       const int x = J.x0 + kb * KBLK;
-      for (int q = 0; q < nbox; ++q) tma_load(b_dst + q * A_BYTES, map, full, x, J.b_row0 + col_org + q * BM);
-      if (!diag) tma_load(b_dst + 2 * B_BYTES, map, full, x, J.a_row0 + row_org);
+      for (int q = 0; q < nbox; ++q) tma_load(b_dst + q * BM * RB, map, full, x, J.b_row0 + col_org + q * BM);
+      if (!diag) tma_load(b_dst + a_off, map, full, x, J.a_row0 + row_org);
       ++issued;
     }
     for (int kb = (issued > stages ? issued - stages : 0); kb < issued; ++kb)
@@ -427,8 +437,13 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
         break;
       }
       unsigned char* sb = base + s * stage_bytes;
-      split_block(sb, B_BYTES, nbox * A_BYTES / 16, t, SPLITTERS);
-      if (!diag) split_block(sb + 2 * B_BYTES, A_BYTES, A_BYTES / 16, t, SPLITTERS);
+      if constexpr (BF) {
+        for (int q = 0; q < nbox; ++q) split_row_sw64(sb, t + q * BM);
+        if (!diag) split_row_sw64(sb + a_off, t);
+      } else {
+        split_block(sb, B_BYTES, nbox * A_BYTES / 16, t, SPLITTERS);
+        if (!diag) split_block(sb + 2 * B_BYTES, A_BYTES, A_BYTES / 16, t, SPLITTERS);
+      }
       // the generic-proxy writes become visible to the tensor core's reads
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bars + MAXST + s)) : "memory");
@@ -438,7 +453,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
     uint32_t id[2];
     for (int q = 0; q < 2; ++q) {
       const int need = diag ? min(kept, BM * (q + 1)) : kept;  // columns up to the diagonal
-      id[q] = idesc<false>(min(BN, (need + 15) / 16 * 16));
+      id[q] = idesc<BF>(min(BN, (need + 15) / 16 * 16));
     }
     if (inject && !mbar_wait(su32(bars + 2 * MAXST), 0, abort, true, INJECT_WAIT_NS)) {
       *abort = 1;
@@ -452,17 +467,30 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
         break;
       }
       tc_fence_after();
-      const uint32_t bh = su32(base + s * stage_bytes), bl = bh + B_BYTES;
-#pragma unroll
-      for (int k = 0; k < NSUB; ++k) {
+      if constexpr (BF) {
+        // [head | remainder] rows: the remainders 32 bytes into each row
+        const uint32_t bh = su32(base + s * stage_bytes), bl = bh + 32;
         for (int q = 0; q < mt; ++q) {
           // diagonal: A sub-tile q is B rows [128 q, 128 q + 128)
-          const uint32_t ah = diag ? bh + q * A_BYTES : bh + 2 * B_BYTES;
-          const uint32_t al = diag ? bl + q * A_BYTES : bh + 2 * B_BYTES + A_BYTES;
+          const uint32_t ah = diag ? bh + q * BM * RB : bh + a_off, al = ah + 32;
           const uint32_t d = tmem + (uint32_t)(q * TMEM_COLS);
-          mma<false>(d, sdesc(ah + k * 32), sdesc(bh + k * 32), id[q], (kb > 0 || k > 0) ? 1u : 0u);
-          mma<false>(d, sdesc(ah + k * 32), sdesc(bl + k * 32), id[q], 1u);
-          mma<false>(d, sdesc(al + k * 32), sdesc(bh + k * 32), id[q], 1u);
+          mma<true>(d, sdesc<true>(ah), sdesc<true>(bh), id[q], kb > 0 ? 1u : 0u);
+          mma<true>(d, sdesc<true>(ah), sdesc<true>(bl), id[q], 1u);
+          mma<true>(d, sdesc<true>(al), sdesc<true>(bh), id[q], 1u);
+        }
+      } else {
+        const uint32_t bh = su32(base + s * stage_bytes), bl = bh + B_BYTES;
+#pragma unroll
+        for (int k = 0; k < NSUB; ++k) {
+          for (int q = 0; q < mt; ++q) {
+            // diagonal: A sub-tile q is B rows [128 q, 128 q + 128)
+            const uint32_t ah = diag ? bh + q * A_BYTES : bh + 2 * B_BYTES;
+            const uint32_t al = diag ? bl + q * A_BYTES : bh + 2 * B_BYTES + A_BYTES;
+            const uint32_t d = tmem + (uint32_t)(q * TMEM_COLS);
+            mma<false>(d, sdesc(ah + k * 32), sdesc(bh + k * 32), id[q], (kb > 0 || k > 0) ? 1u : 0u);
+            mma<false>(d, sdesc(ah + k * 32), sdesc(bl + k * 32), id[q], 1u);
+            mma<false>(d, sdesc(al + k * 32), sdesc(bh + k * 32), id[q], 1u);
+          }
         }
       }
       mma_commit(su32(bars + 2 * MAXST + s));
@@ -646,8 +674,9 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
     }
     // Gram: FP32 maps over the P^T columns (nR) and the S columns (n) of [P^T | S]
     float* Pb = reinterpret_cast<float*>(P) + d.o_P;
-    if (!encode_rows(encode, &maps[nb + b], Pb, d.nR, d.ldP, d.n) ||
-        !encode_rows(encode, &maps[2 * nb + b], Pb + d.sP, d.n, d.ldP, d.n)) {
+    const int gk = bf16 ? KBLK_BF16 : KBLK_F32;  // the BF16 mode's Gram: BF16 passes too
+    if (!encode_rows(encode, &maps[nb + b], Pb, d.nR, d.ldP, d.n, gk) ||
+        !encode_rows(encode, &maps[2 * nb + b], Pb + d.sP, d.n, d.ldP, d.n, gk)) {
       err = "cuTensorMapEncodeTiled failed (Gram, instance " + std::to_string(b) + ")";
       return GNMPPI_E_CUDA;
     }
@@ -657,7 +686,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
     jg.map = nb + b;
     jg.M = d.n;
     jg.Nc = d.n;
-    jg.nkb = (d.nR + KBLK_F32 - 1) / KBLK_F32;
+    jg.nkb = (d.nR + gk - 1) / gk;
     jg.out_off = d.o_nn;
     jg.ldc = d.n;
     jg.ccut = d.n;
@@ -666,7 +695,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
     TcJob& js = jobs[2 * nb + b];
     js = jg;
     js.map = 2 * nb + b;
-    js.nkb = (d.n + KBLK_F32 - 1) / KBLK_F32;
+    js.nkb = (d.n + gk - 1) / gk;
     js.out_sel = 1;
     if (d.lsq) gram_tiles(2 * nb + b, d.n, ts);
   }
@@ -726,7 +755,8 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
   if (e == cudaSuccess && bf16)
     e = cudaFuncSetAttribute(k_contract_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem1);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
+    e = bf16 ? cudaFuncSetAttribute(k_gram_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem)
+             : cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
   if (e != cudaSuccess) {
     err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
     return GNMPPI_E_CUDA;
@@ -751,8 +781,12 @@ cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float*
 
 cudaError_t tc_gram_launch(const TcPlan& plan, const InstState* d_st, double* A, double* S2, cudaStream_t stream) {
   if (plan.ntiles_g == 0) return cudaSuccess;
-  k_gram_tc<false><<<plan.ntiles_g, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
-                                                                        plan.d_tiles_g, A, S2, plan.d_err, 0);
+  if (plan.bf16)
+    k_gram_tc<false, true><<<plan.ntiles_g, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
+                                                                               plan.d_tiles_g, A, S2, plan.d_err, 0);
+  else
+    k_gram_tc<false><<<plan.ntiles_g, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
+                                                                          plan.d_tiles_g, A, S2, plan.d_err, 0);
   return cudaGetLastError();
 }
 

@@ -409,9 +409,10 @@ def test_tensor_core_contraction_matches_oracle(prec, tol):
 @pytest.mark.parametrize("prec", [G.PREC_FP32, G.PREC_BF16])
 @pytest.mark.parametrize("M,N,K", [(6, 75, 1400), (4, 150, 640), (3, 260, 1056)])
 def test_tensor_core_gram_matches_its_definition(prec, M, N, K):
-    """A = P^T P and S2 = S S^T of Eq. 9 from the tcgen05 Gram kernel (TF32
-    head/remainder split in shared memory, three passes, FP32 accumulation)
-    against the same products formed in FP64 from the [P^T | S] the GPU holds,
+    """A = P^T P and S2 = S S^T of Eq. 9 from the tcgen05 Gram kernel (head/
+    remainder split in shared memory: TF32 in the FP32 mode, BF16 in the BF16
+    mode; three passes, FP32 accumulation) against the same products formed
+    in FP64 from the [P^T | S] the GPU holds,
     at n = 150, 300 and 520: one and two 128-row sub-tiles on the diagonal,
     off-diagonal tiles, lower blocks stored transposed, ragged edges.  Every
     entry must be written (a stale or missing block fails the entrywise
@@ -433,19 +434,24 @@ def test_tensor_core_gram_matches_its_definition(prec, M, N, K):
     for got, ref in ((A, Pt @ Pt.T), (S2, S @ S.T)):
         # Each entry is a dot product of two rows: its rounding error is
         # bounded by a multiple of |row_i| |row_j| = sqrt(ref_ii ref_jj)
-        # (Cauchy-Schwarz).  The split itself leaves ~2^-22 per product; the
-        # tensor core's FP32 accumulation over nR = 1206-1566 terms measures
-        # ~2e-5 of that scale here, so 1e-4 bounds it while a stale or missing
-        # block (an O(1) error) fails.
+        # (Cauchy-Schwarz).  The split itself leaves ~2^-22 (TF32) or ~2^-16
+        # (BF16, the dropped remainder x remainder term, of random sign) per
+        # product; the tensor core's FP32 accumulation over nR = 1206-1566
+        # terms measures ~2e-5 of that scale here, so 1e-4 bounds it while a
+        # stale or missing block (an O(1) error) fails.
         d = np.sqrt(np.diag(ref))
         assert rel(got, ref) < 5e-5
         assert np.all(np.abs(got - ref) <= 1e-4 * np.outer(d, d))
     assert np.all(np.abs(A - A.T) <= 1e-4 * np.outer(np.sqrt(np.diag(A)), np.sqrt(np.diag(A))))
     # The remainder passes take effect: the head-only product hi hi^T (hi =
-    # [P^T] rounded to TF32, the one pass a dropped remainder would leave) has
-    # a different, larger error, and the GPU's error is uncorrelated with it.
+    # [P^T] rounded to TF32 or BF16, the one pass a dropped remainder would
+    # leave) has a different, larger error, and the GPU's error is
+    # uncorrelated with it.
     u = Pt.astype(np.float32).view(np.uint32).astype(np.uint64)
-    hi = ((u + 0x1000) & 0xFFFFE000).astype(np.uint32).view(np.float32).astype(np.float64)
+    if prec == G.PREC_BF16:  # round to nearest even on the 16 kept bits
+        hi = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32).view(np.float32).astype(np.float64)
+    else:
+        hi = ((u + 0x1000) & 0xFFFFE000).astype(np.uint32).view(np.float32).astype(np.float64)
     Aref = Pt @ Pt.T
     d = np.sqrt(np.diag(Aref))
     e_gpu = (A - Aref) / np.outer(d, d)
