@@ -108,3 +108,62 @@ def test_contraction_tile_does_not_change_the_bf16_solve():
         assert np.array_equal(U, ref[0])
     finally:
         G.gnmppi_destroy(h)
+
+
+TUNE_CHILD = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+from paper_2512_04579_gb300 import gnmppi as G
+from paper_2512_04579_gb300 import inputs as I
+G.load()
+seed, batch = I.BASE_SEED + 80, 6
+Ms, Ns, Ks, x0s, tgts = I.uneven_chain_instances(seed, batch)
+shapes = [(int(Ns[b]), int(Ms[b]), int(Ks[b])) for b in range(batch)]
+prob = G.chain_problem(M=int(Ms[0]), N=int(Ns[0]), K=int(Ks[0]), iterations=1, lam=1e-3, sigma0=0.2, seed=seed,
+                       precision=G.PREC_BF16)
+h = G.gnmppi_create(prob, batch, shapes)
+nU = int(sum(2 * n for n in Ns))
+rep = G.gnmppi_autotune(h, G.MEM_HOST, np.concatenate(x0s), np.concatenate(tgts), np.zeros(nU))
+G.gnmppi_destroy(h)
+print(json.dumps(rep))
+"""
+
+
+def test_tune_file_persists_the_choice_across_processes(tmp_path):
+    """GNMPPI_TUNE_FILE: the first process times and appends one
+    "signature branches solve_nt contract_mt" line; a second process with the
+    same instance shapes takes the choice from the file without timing.  Lines
+    of the earlier three-field form (no contraction tile) are read as tile 2."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    from paper_2512_04579_gb300 import build as B
+
+    B.build()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    tf = tmp_path / "tune.txt"
+    env = dict(os.environ, GNMPPI_TUNE_FILE=str(tf))
+
+    def child():
+        r = subprocess.run([sys.executable, "-c", TUNE_CHILD, root], env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+    first = child()
+    assert first["source"] == "timed"
+    fields = tf.read_text().split()
+    assert len(fields) == 4 and fields[0] == first["signature"]
+    assert [int(f) for f in fields[1:]] == [first["branches"], first["solve_nt"], first["contract_mt"]]
+    second = child()
+    assert second["source"] == "cache"
+    assert (second["branches"], second["solve_nt"], second["contract_mt"]) == \
+        (first["branches"], first["solve_nt"], first["contract_mt"])
+    # the three-field form of the same entry
+    tf.write_text(f"{first['signature']} 2 512\n")
+    third = child()
+    assert third["source"] == "cache"
+    assert (third["branches"], third["solve_nt"], third["contract_mt"]) == (2, 512, 2)
