@@ -25,12 +25,15 @@
 //                       per warp store (the S columns from column sP on);
 //    FP32 mode: the three-pass TF32 kernel of (2) on the FP32 [dR; W] block.
 //  (2) k_gram_tc: the Gram product A = P^T P of Eq. 9 in FP32-level accuracy
-//      from three TF32 passes, A ~ Ph Ph^T + Ph Pl^T + Pl Ph^T with every FP32
-//      operand x split into a TF32 head h = rna(x) and its remainder x - h
-//      (exact in FP32), and in the same launch S2 = S S^T for the scaled LSQ
-//      system.  TMA streams the FP32 rows of [P^T | S] straight from the
-//      contraction's output; warps 2-5 split each landed stage in shared
-//      memory (head in place, remainder beside it) before the MMAs read it.  A
+//      from three passes, A ~ Ph Ph^T + Ph Pl^T + Pl Ph^T with every FP32
+//      operand x split into a head h and its remainder x - h, and in the same
+//      launch S2 = S S^T for the scaled LSQ system.  FP32 mode: TF32 heads
+//      h = rna(x) (remainder exact in FP32), 32-value k-blocks, the remainder
+//      beside the head.  BF16 mode: BF16 head and remainder written in place
+//      as a [head | remainder] row per 16-value k-block, as in (1).  TMA
+//      streams the FP32 rows of [P^T | S] straight from the contraction's
+//      output; warps 2-5 split each landed stage in shared memory before the
+//      MMAs read it.  A
 //      diagonal tile takes its A sub-tiles from its own B rows (the operand is
 //      the same matrix), each sub-tile's MMAs stop at the diagonal, and the
 //      strictly lower 32 x 32 blocks are also stored transposed, so every
@@ -449,7 +452,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bars + MAXST + s)) : "memory");
     }
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer: three TF32 passes per sub-tile
+    // ---------------- MMA issuer: three passes (TF32 or BF16) per sub-tile
     uint32_t id[2];
     for (int q = 0; q < 2; ++q) {
       const int need = diag ? min(kept, BM * (q + 1)) : kept;  // columns up to the diagonal

@@ -58,7 +58,8 @@ cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float*
                                int mt);
 
 // A = P^T P and, for instances in LSQ mode, S2 = S S^T (FP64 outputs) from
-// three TF32 passes over [P^T | S] split in shared memory, in one launch.
+// three passes over [P^T | S] split in shared memory (BF16 head + remainder
+// in BF16 mode, TF32 otherwise), in one launch.
 cudaError_t tc_gram_launch(const TcPlan& plan, const InstState* d_st, double* A, double* S2, cudaStream_t stream);
 
 }  // namespace gnm
