@@ -310,6 +310,24 @@ __device__ __forceinline__ float tf32_head(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
+// FP32 bit pattern u widened to the FP64 value it encodes, on the integer
+// pipe (GB300's FP64 pipe retires one warp instruction per ~19 cycles per SM,
+// so a conversion per output entry there would dominate the Gram's
+// epilogue).  IEEE 754 binary32 -> binary64: the sign stays, a normal
+// exponent is rebiased by 1023 - 127 = 896, the 23 fraction bits become the
+// top of the 52 (the low 3 of them land in the low word's top 3 bits);
+// zeros, infinities and NaNs keep their class; subnormals (rare here) take
+// the hardware conversion.
+__device__ __forceinline__ double widen_f32(uint32_t u) {
+  const uint32_t a = u & 0x7FFFFFFFu, sgn = u & 0x80000000u;
+  uint32_t hi;
+  if (a >= 0x7F800000u) hi = sgn | 0x7FF00000u | ((a & 0x007FFFFFu) >> 3);
+  else if (a >= 0x00800000u) hi = sgn | ((a >> 3) + (896u << 20));
+  else if (a == 0u) hi = sgn;
+  else return (double)__uint_as_float(u);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 // Splits `n4` float4 of a landed operand block in place: head (TF32) at p,
 // remainder at p + delta bytes.  Same positions in both blocks, so the
 // 128-byte swizzle of the TMA layout carries over.
@@ -345,7 +363,9 @@ constexpr int kGramThreads = 192;
 // BF (the BF16 mode's Gram, CONTRACT false only): k-blocks of 16 FP32 values
 // (64-byte rows, 64-byte swizzle) split in place row by row into BF16
 // [head | remainder] rows, three kind::f16 passes; B rows and (off the
-// diagonal) A rows only, no separate remainder area, so up to 8 stages.
+// diagonal) A rows only, no separate remainder area, so up to 8 stages (12
+// diagonal 16 KB stages would fit the ring but measured slower: 0.92 against
+// 0.84 ms for 64 instances of M = 32).
 template <bool CONTRACT, bool BF = false>
 __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
                                                     const InstState* __restrict__ st, const int4* __restrict__ tiles,
@@ -522,7 +542,10 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
         uint32_t v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sub * TMEM_COLS + c * 32), v);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = (TO)__uint_as_float(v[q]);
+        for (int q = 0; q < 32; ++q) {
+          if constexpr (CONTRACT) stg[lane * 33 + q] = __uint_as_float(v[q]);
+          else stg[lane * 33 + q] = widen_f32(v[q]);
+        }
         __syncwarp();
         const int col = col_org + c * 32 + lane;
         if (col < J.Nc) {

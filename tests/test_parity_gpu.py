@@ -443,6 +443,11 @@ def test_tensor_core_gram_matches_its_definition(prec, M, N, K):
         assert rel(got, ref) < 5e-5
         assert np.all(np.abs(got - ref) <= 1e-4 * np.outer(d, d))
     assert np.all(np.abs(A - A.T) <= 1e-4 * np.outer(np.sqrt(np.diag(A)), np.sqrt(np.diag(A))))
+    # The FP32 accumulators are widened to FP64 exactly (on the integer pipe):
+    # every entry is an FP32 value, so a misplaced fraction bit (which the
+    # 1e-4 bound above cannot see) fails here.
+    for got in (A, S2):
+        assert np.array_equal(got.astype(np.float32).astype(np.float64), got)
     # The remainder passes take effect: the head-only product hi hi^T (hi =
     # [P^T] rounded to TF32 or BF16, the one pass a dropped remainder would
     # leave) has a different, larger error, and the GPU's error is
