@@ -30,7 +30,8 @@
 //      launch S2 = S S^T for the scaled LSQ system.  FP32 mode: TF32 heads
 //      h = rna(x) (remainder exact in FP32), 32-value k-blocks, the remainder
 //      beside the head.  BF16 mode: BF16 head and remainder written in place
-//      as a [head | remainder] row per 16-value k-block, as in (1).  TMA
+//      as a [head | remainder] row per 16-value k-block, as in (1), one
+//      128-row sub-tile per CTA and two CTAs per SM.  TMA
 //      streams the FP32 rows of [P^T | S] straight from the contraction's
 //      output; warps 2-5 split each landed stage in shared memory before the
 //      MMAs read it.  A
@@ -363,11 +364,17 @@ constexpr int kGramThreads = 192;
 // BF (the BF16 mode's Gram, CONTRACT false only): k-blocks of 16 FP32 values
 // (64-byte rows, 64-byte swizzle) split in place row by row into BF16
 // [head | remainder] rows, three kind::f16 passes; B rows and (off the
-// diagonal) A rows only, no separate remainder area, so up to 8 stages (12
-// diagonal 16 KB stages would fit the ring but measured slower: 0.92 against
-// 0.84 ms for 64 instances of M = 32).
+// diagonal) A rows only, no separate remainder area.  Every tile has one
+// 128-row sub-tile (256 TMEM columns) and a 96 KB ring (up to 8 stages), so
+// two CTAs share an SM and each hides the other's pipeline latency: a
+// diagonal tile with two sub-tiles runs as two CTAs (tl.w bit 3 marks the
+// second), the first loading only the 128 B rows its MMAs read.  Same
+// products in the same order per output as one CTA per diagonal tile
+// (0.266 -> 0.215 ms per launch at 256 instances of n = 200).  12 diagonal
+// stages of 16 KB in a 192 KB ring measured slower (0.92 against 0.84 ms for
+// 64 instances of M = 32).
 template <bool CONTRACT, bool BF = false>
-__global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kGramThreads, BF ? 2 : 1) k_gram_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
                                                     const InstState* __restrict__ st, const int4* __restrict__ tiles,
                                                     void* __restrict__ out0, double* __restrict__ S2,
                                                     int* __restrict__ err, int inject) {
@@ -382,13 +389,16 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
   const TcJob J = jobs[tl.x];
   const int mt = tl.w & 3;
   const bool diag = (tl.w & 4) != 0;
+  const int q0 = (tl.w >> 3) & 1;  // BF16: the diagonal tile's second sub-tile alone
   const int row_org = tl.y, col_org = tl.z;
   const int kept = min(BN, J.Nc - col_org);  // output columns of this tile = B rows
-  const int nbox = kept > BM ? 2 : 1;        // 128-row TMA boxes of B
+  const int kept_b = diag ? min(kept, BM * (q0 + mt)) : kept;  // B rows the MMAs read
+  const int nbox = kept_b > BM ? 2 : 1;      // 128-row TMA boxes of B
   // TF32: B head, B remainder (256 rows each) [, A head, A remainder];
   // BF16: 256 B rows [, 128 A rows], each split in place
-  const int stage_bytes = BF ? (diag ? BN * RB : (BN + BM) * RB) : (diag ? 2 * B_BYTES : 2 * (B_BYTES + A_BYTES));
-  const int stages = min(MAXST, RING_BYTES / stage_bytes);  // TF32: 3 (diagonal) or 2; BF16: 8
+  constexpr int RING = BF ? RING_BYTES / 2 : RING_BYTES;  // BF16: two CTAs per SM
+  const int stage_bytes = BF ? (diag ? nbox * BM * RB : (BN + BM) * RB) : (diag ? 2 * B_BYTES : 2 * (B_BYTES + A_BYTES));
+  const int stages = min(MAXST, RING / stage_bytes);  // TF32: 3 (diagonal) or 2; BF16: 8
   const int a_off = BF ? BN * RB : 2 * B_BYTES;              // A rows of an off-diagonal stage
   const uint32_t tx_bytes = (uint32_t)(nbox * BM * RB + (diag ? 0 : BM * RB));
   const uint32_t tcols = mt == 2 ? 2 * TMEM_COLS : TMEM_COLS;
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
 
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + RING_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + RING);
   // bars[0..3): full (TMA landed), [3..6): split (heads and remainders
   // written), [6..9): empty (MMAs done with the stage), [9]: done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * MAXST + 1);
@@ -475,7 +485,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
     // ---------------- MMA issuer: three passes (TF32 or BF16) per sub-tile
     uint32_t id[2];
     for (int q = 0; q < 2; ++q) {
-      const int need = diag ? min(kept, BM * (q + 1)) : kept;  // columns up to the diagonal
+      const int need = diag ? min(kept, BM * (q0 + q + 1)) : kept;  // columns up to the diagonal
       id[q] = idesc<BF>(min(BN, (need + 15) / 16 * 16));
     }
     if (inject && !mbar_wait(su32(bars + 2 * MAXST), 0, abort, true, INJECT_WAIT_NS)) {
@@ -495,7 +505,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
         const uint32_t bh = su32(base + s * stage_bytes), bl = bh + 32;
         for (int q = 0; q < mt; ++q) {
           // diagonal: A sub-tile q is B rows [128 q, 128 q + 128)
-          const uint32_t ah = diag ? bh + q * BM * RB : bh + a_off, al = ah + 32;
+          const uint32_t ah = diag ? bh + (q0 + q) * BM * RB : bh + a_off, al = ah + 32;
           const uint32_t d = tmem + (uint32_t)(q * TMEM_COLS);
           mma<true>(d, sdesc<true>(ah), sdesc<true>(bh), id[q], kb > 0 ? 1u : 0u);
           mma<true>(d, sdesc<true>(ah), sdesc<true>(bl), id[q], 1u);
@@ -535,8 +545,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
                         : reinterpret_cast<TO*>(J.out_sel ? S2 : reinterpret_cast<double*>(out0))) + J.out_off;
 #pragma unroll 1
     for (int sub = 0; sub < mt; ++sub) {
-      const int row0 = row_org + sub * BM + warp * 32;
-      const int cend = diag ? min(kept, BM * (sub + 1)) : kept;
+      const int row0 = row_org + (q0 + sub) * BM + warp * 32;
+      const int cend = diag ? min(kept, BM * (q0 + sub + 1)) : kept;
 #pragma unroll 1
       for (int c = 0; c * 32 < cend; ++c) {  // uniform over the warp
         uint32_t v[32];
@@ -557,7 +567,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram_tc(const CUtensorMap* 
         }
         // strictly lower block of the symmetric Gram: store its transpose too
         // (the contraction's output is rectangular and has no mirror image)
-        if (!CONTRACT && (!diag || c < 4 * sub)) {
+        if (!CONTRACT && (!diag || c < 4 * (q0 + sub))) {
           const int rowt = row0 + lane;
           if (rowt < J.M) {
 #pragma unroll 4
@@ -620,12 +630,18 @@ static bool plan_alloc(TcPlan* plan, P** p, size_t bytes) {
 }
 
 // Gram tiles of an n x n symmetric output: per 256-column block J the
-// diagonal tile (rows = columns, one or two 128-row sub-tiles), then the
-// 128-row off-diagonal tiles below it.
-static void gram_tiles(int job, int n, std::vector<int4>& out) {
+// diagonal tile (rows = columns, one or two 128-row sub-tiles; with split,
+// two one-sub-tile tiles, the second marked by bit 3), then the 128-row
+// off-diagonal tiles below it.
+static void gram_tiles(int job, int n, std::vector<int4>& out, bool split) {
   for (int J = 0; J * BN < n; ++J) {
     const int r0 = J * BN;
-    out.push_back(make_int4(job, r0, r0, (n - r0 > BM ? 2 : 1) | 4));
+    if (split && n - r0 > BM) {
+      out.push_back(make_int4(job, r0, r0, 1 | 4));
+      out.push_back(make_int4(job, r0, r0, 1 | 4 | 8));
+    } else {
+      out.push_back(make_int4(job, r0, r0, (n - r0 > BM ? 2 : 1) | 4));
+    }
     for (int i = r0 + BN; i < n; i += BM) out.push_back(make_int4(job, i, r0, 1));
   }
 }
@@ -716,14 +732,14 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
     jg.out_off = d.o_nn;
     jg.ldc = d.n;
     jg.ccut = d.n;
-    gram_tiles(nb + b, d.n, tg);
+    gram_tiles(nb + b, d.n, tg, bf16 != 0);
     // S2 = S S^T over the S columns (LSQ mode)
     TcJob& js = jobs[2 * nb + b];
     js = jg;
     js.map = 2 * nb + b;
     js.nkb = (d.n + gk - 1) / gk;
     js.out_sel = 1;
-    if (d.lsq) gram_tiles(2 * nb + b, d.n, ts);
+    if (d.lsq) gram_tiles(2 * nb + b, d.n, ts, bf16 != 0);
   }
   // longest first, so that the short tiles (the S2 products, small
   // instances) fill the SMs that the last long ones leave idle.  Gram tiles
@@ -781,7 +797,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
   if (e == cudaSuccess && bf16)
     e = cudaFuncSetAttribute(k_contract_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem1);
   if (e == cudaSuccess)
-    e = bf16 ? cudaFuncSetAttribute(k_gram_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem)
+    e = bf16 ? cudaFuncSetAttribute(k_gram_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem1)
              : cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem);
   if (e != cudaSuccess) {
     err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
@@ -808,7 +824,7 @@ cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float*
 cudaError_t tc_gram_launch(const TcPlan& plan, const InstState* d_st, double* A, double* S2, cudaStream_t stream) {
   if (plan.ntiles_g == 0) return cudaSuccess;
   if (plan.bf16)
-    k_gram_tc<false, true><<<plan.ntiles_g, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
+    k_gram_tc<false, true><<<plan.ntiles_g, kGramThreads, plan.smem1, stream>>>(plan.d_maps, plan.d_jobs, d_st,
                                                                                plan.d_tiles_g, A, S2, plan.d_err, 0);
   else
     k_gram_tc<false><<<plan.ntiles_g, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
