@@ -774,7 +774,7 @@ static gnmppi_status launch_iteration_t(gnmppi_t h, uint32_t it, int shrink, cud
   if (ON(3)) {
     if (h->use_tc) {
       CK(tc_gram_launch(h->tc, h->d_st, h->d_A, h->d_S2, h->stream));
-      h->launches++;
+      h->launches += h->tc.nred > 0 ? 2 : 1;  // the chunk sum is a second launch
     } else {
       ga.tiles = h->d_tiles[1];
       k_gemm_nt<kGram, TA, TC, double><<<h->ntiles[1], 256, 0, h->stream>>>(ga);

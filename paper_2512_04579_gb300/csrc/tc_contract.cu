@@ -377,6 +377,7 @@ template <bool CONTRACT, bool BF = false>
 __global__ void __launch_bounds__(kGramThreads, BF ? 2 : 1) k_gram_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
                                                     const InstState* __restrict__ st, const int4* __restrict__ tiles,
                                                     void* __restrict__ out0, double* __restrict__ S2,
+                                                    double* __restrict__ part,
                                                     int* __restrict__ err, int inject) {
   using TO = typename std::conditional<CONTRACT, float, double>::type;
   static_assert(!(CONTRACT && BF), "the BF16 contraction is k_contract_tc");
@@ -542,7 +543,8 @@ __global__ void __launch_bounds__(kGramThreads, BF ? 2 : 1) k_gram_tc(const CUte
   } else if (__all_sync(0xffffffffu, ok && !*abort)) {
     TO* stg = reinterpret_cast<TO*>(base) + warp * 32 * 33;
     TO* out = (CONTRACT ? reinterpret_cast<TO*>(out0)
-                        : reinterpret_cast<TO*>(J.out_sel ? S2 : reinterpret_cast<double*>(out0))) + J.out_off;
+                        : reinterpret_cast<TO*>(J.out_sel == 2 ? part
+                                                : J.out_sel ? S2 : reinterpret_cast<double*>(out0))) + J.out_off;
 #pragma unroll 1
     for (int sub = 0; sub < mt; ++sub) {
       const int row0 = row_org + (q0 + sub) * BM + warp * 32;
@@ -593,6 +595,23 @@ __global__ void __launch_bounds__(kGramThreads, BF ? 2 : 1) k_gram_tc(const CUte
 }
 
 }  // namespace
+
+// A of the instances whose Gram runs in column chunks: the sum, in FP64 and
+// in chunk order, of the chunks' FP64-widened FP32 tile results (the
+// reduction over nR split so that no FP32 accumulator sums more than
+// kGramChunkCols columns).  Instances whose status is not OK are skipped
+// (their chunk tiles did not run).
+__global__ void __launch_bounds__(256) k_gram_reduce(const GramRed* __restrict__ red, const InstState* __restrict__ st,
+                                                     const double* __restrict__ part, double* __restrict__ A) {
+  const GramRed r = red[blockIdx.y];
+  if (st[r.inst].status != 0) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < r.nn; i += (int64_t)gridDim.x * blockDim.x) {
+    const double* p = part + r.part_off + i;
+    double acc = p[0];
+    for (int c = 1; c < r.chunks; ++c) acc += p[(int64_t)c * r.nn];
+    A[r.out_off + i] = acc;
+  }
+}
 
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode(std::string& err) {
   void* fn = nullptr;
@@ -660,6 +679,9 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
   std::vector<CUtensorMap> maps(4 * (size_t)nb);
   std::vector<TcJob> jobs(3 * (size_t)nb);
   std::vector<int4> tc, tc1, tg, ts;
+  std::vector<TcJob> chunk_jobs;  // appended after the 3 nb fixed jobs
+  std::vector<GramRed> red;
+  int64_t part_elems = 0;
   for (int b = 0; b < nb; ++b) {
     const InstDesc& d = desc[b];
     if (d.ldK % kblk != 0) {
@@ -732,7 +754,26 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
     jg.out_off = d.o_nn;
     jg.ldc = d.n;
     jg.ccut = d.n;
-    gram_tiles(nb + b, d.n, tg, bf16 != 0);
+    // nR beyond kGramChunkCols: one job per column chunk into the FP64 chunk
+    // buffer, added up by k_gram_reduce
+    const int gchunk = kGramChunkCols / gk;
+    const int nchunks = (jg.nkb + gchunk - 1) / gchunk;
+    if (nchunks <= 1) {
+      gram_tiles(nb + b, d.n, tg, bf16 != 0);
+    } else {
+      const int64_t nn = (int64_t)d.n * d.n;
+      for (int c = 0; c < nchunks; ++c) {
+        TcJob jc2 = jg;
+        jc2.x0 = c * gchunk * gk;
+        jc2.nkb = std::min(gchunk, jg.nkb - c * gchunk);
+        jc2.out_sel = 2;
+        jc2.out_off = part_elems + c * nn;
+        chunk_jobs.push_back(jc2);
+        gram_tiles(3 * nb + (int)chunk_jobs.size() - 1, d.n, tg, bf16 != 0);
+      }
+      red.push_back(GramRed{d.o_nn, part_elems, nn, nchunks, b});
+      part_elems += nchunks * nn;
+    }
     // S2 = S S^T over the S columns (LSQ mode)
     TcJob& js = jobs[2 * nb + b];
     js = jg;
@@ -746,6 +787,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
   // by k-blocks x sub-tiles x kept columns; contraction tiles by their
   // instance's k-blocks x sub-tiles only, so that the column tiles of an
   // instance, which share its W rows in L2, stay adjacent.
+  jobs.insert(jobs.end(), chunk_jobs.begin(), chunk_jobs.end());
   tg.insert(tg.end(), ts.begin(), ts.end());
   auto gram_work = [&](const int4& t) {
     const TcJob& j = jobs[t.x];
@@ -762,6 +804,8 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
       !plan_alloc(plan, &plan->d_tiles_c, sizeof(int4) * std::max<size_t>(1, tc.size())) ||
       !plan_alloc(plan, &plan->d_tiles_c1, sizeof(int4) * std::max<size_t>(1, tc1.size())) ||
       !plan_alloc(plan, &plan->d_tiles_g, sizeof(int4) * std::max<size_t>(1, tg.size())) ||
+      (part_elems > 0 && !plan_alloc(plan, &plan->d_part, sizeof(double) * (size_t)part_elems)) ||
+      (!red.empty() && !plan_alloc(plan, &plan->d_red, sizeof(GramRed) * red.size())) ||
       !plan_alloc(plan, &plan->d_err, sizeof(int))) {
     err = "cudaMalloc failed for the tensor-core plan";
     return GNMPPI_E_NOMEM;
@@ -769,6 +813,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
   plan->ntiles_c = (int)tc.size();
   plan->ntiles_c1 = (int)tc1.size();
   plan->ntiles_g = (int)tg.size();
+  plan->nred = (int)red.size();
   bool ok = cudaMemcpyAsync(plan->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
                             stream) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(plan->d_jobs, jobs.data(), sizeof(TcJob) * jobs.size(), cudaMemcpyHostToDevice, stream) ==
@@ -780,6 +825,9 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
                                stream) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(plan->d_tiles_g, tg.data(), sizeof(int4) * tg.size(), cudaMemcpyHostToDevice, stream) ==
                  cudaSuccess;
+  if (!red.empty())
+    ok = ok && cudaMemcpyAsync(plan->d_red, red.data(), sizeof(GramRed) * red.size(), cudaMemcpyHostToDevice,
+                               stream) == cudaSuccess;
   ok = ok && cudaMemsetAsync(plan->d_err, 0, sizeof(int), stream) == cudaSuccess;
   if (!ok) {
     err = "copying the tensor-core plan failed";
@@ -817,19 +865,26 @@ cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float*
                                                                              plan.d_tiles_c, P, plan.d_err, inject);
   else
     k_gram_tc<true><<<plan.ntiles_c, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
-                                                                        plan.d_tiles_c, P, nullptr, plan.d_err, inject);
+                                                                        plan.d_tiles_c, P, nullptr, nullptr, plan.d_err,
+                                                                        inject);
   return cudaGetLastError();
 }
 
 cudaError_t tc_gram_launch(const TcPlan& plan, const InstState* d_st, double* A, double* S2, cudaStream_t stream) {
   if (plan.ntiles_g == 0) return cudaSuccess;
   if (plan.bf16)
-    k_gram_tc<false, true><<<plan.ntiles_g, kGramThreads, plan.smem1, stream>>>(plan.d_maps, plan.d_jobs, d_st,
-                                                                               plan.d_tiles_g, A, S2, plan.d_err, 0);
+    k_gram_tc<false, true><<<plan.ntiles_g, kGramThreads, plan.smem1, stream>>>(
+        plan.d_maps, plan.d_jobs, d_st, plan.d_tiles_g, A, S2, plan.d_part, plan.d_err, 0);
   else
     k_gram_tc<false><<<plan.ntiles_g, kGramThreads, plan.smem, stream>>>(plan.d_maps, plan.d_jobs, d_st,
-                                                                          plan.d_tiles_g, A, S2, plan.d_err, 0);
-  return cudaGetLastError();
+                                                                          plan.d_tiles_g, A, S2, plan.d_part,
+                                                                          plan.d_err, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && plan.nred > 0) {
+    k_gram_reduce<<<dim3(32, plan.nred), 256, 0, stream>>>(plan.d_red, d_st, plan.d_part, A);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 GNM_CHECK_ACCESSOR(check_count_tc)

@@ -29,6 +29,19 @@ struct TcJob {
   int32_t ccut, cgap;
 };
 
+// One instance whose Gram A = P^T P runs in column chunks: A (at out_off,
+// nn = n^2 entries) = sum over the chunks of part[part_off + c nn + i].
+struct GramRed {
+  int64_t out_off, part_off;
+  int64_t nn;
+  int32_t chunks, inst;
+};
+
+// Columns of P^T summed by one FP32 accumulator of the Gram; longer sums are
+// split into chunks whose results are added in FP64 (the tensor core's FP32
+// accumulation error grows with the number of accumulation steps).
+constexpr int kGramChunkCols = 2048;
+
 struct TcPlan {
   CUtensorMap* d_maps = nullptr;  // per instance: contraction [dR; W]; then P^T columns; then S columns
   TcJob* d_jobs = nullptr;        // same order as the maps (contraction, Gram, S2)
@@ -38,6 +51,9 @@ struct TcPlan {
   int ntiles_c = 0, ntiles_c1 = 0, ntiles_g = 0;
   int smem = 0, smem1 = 0;
   int bf16 = 1;
+  double* d_part = nullptr;       // FP64 chunk results of the chunked Grams
+  GramRed* d_red = nullptr;       // one record per chunked instance
+  int nred = 0;
   int* d_err = nullptr;           // set to 1 when a bounded wait ran out
   std::vector<void*> allocs;
 };
@@ -59,7 +75,9 @@ cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float*
 
 // A = P^T P and, for instances in LSQ mode, S2 = S S^T (FP64 outputs) from
 // three passes over [P^T | S] split in shared memory (BF16 head + remainder
-// in BF16 mode, TF32 otherwise), in one launch.
+// in BF16 mode, TF32 otherwise), in one launch; where nR exceeds
+// kGramChunkCols, A is formed per column chunk and a second launch adds the
+// chunks in FP64.
 cudaError_t tc_gram_launch(const TcPlan& plan, const InstState* d_st, double* A, double* S2, cudaStream_t stream);
 
 }  // namespace gnm

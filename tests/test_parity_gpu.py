@@ -407,16 +407,18 @@ def test_tensor_core_contraction_matches_oracle(prec, tol):
 
 
 @pytest.mark.parametrize("prec", [G.PREC_FP32, G.PREC_BF16])
-@pytest.mark.parametrize("M,N,K", [(6, 75, 1400), (4, 150, 640), (3, 260, 1056)])
+@pytest.mark.parametrize("M,N,K", [(6, 75, 1400), (4, 150, 640), (3, 260, 1056), (10, 120, 512), (16, 150, 640)])
 def test_tensor_core_gram_matches_its_definition(prec, M, N, K):
     """A = P^T P and S2 = S S^T of Eq. 9 from the tcgen05 Gram kernel (head/
     remainder split in shared memory: TF32 in the FP32 mode, BF16 in the BF16
     mode; three passes, FP32 accumulation) against the same products formed
     in FP64 from the [P^T | S] the GPU holds,
     at n = 150, 300 and 520: one and two 128-row sub-tiles on the diagonal,
-    off-diagonal tiles, lower blocks stored transposed, ragged edges.  Every
-    entry must be written (a stale or missing block fails the entrywise
-    bound) and A symmetric."""
+    off-diagonal tiles, lower blocks stored transposed, ragged edges; and at
+    nR = 2418 and 4830 (n = 240, 300), where A is summed over 2048-column
+    chunks in FP64 (two and three chunks, the last one ragged).  Every entry
+    must be written (a stale or missing block fails the entrywise bound) and
+    A symmetric."""
     seed = 31
     n = 2 * N
     x0, tgt = I.chain_instances(seed, 1, M)
@@ -444,9 +446,10 @@ def test_tensor_core_gram_matches_its_definition(prec, M, N, K):
         assert np.all(np.abs(got - ref) <= 1e-4 * np.outer(d, d))
     assert np.all(np.abs(A - A.T) <= 1e-4 * np.outer(np.sqrt(np.diag(A)), np.sqrt(np.diag(A))))
     # The FP32 accumulators are widened to FP64 exactly (on the integer pipe):
-    # every entry is an FP32 value, so a misplaced fraction bit (which the
-    # 1e-4 bound above cannot see) fails here.
-    for got in (A, S2):
+    # every entry of an unchunked product is an FP32 value, so a misplaced
+    # fraction bit (which the 1e-4 bound above cannot see) fails here.  A
+    # chunked A is a FP64 sum of such values.
+    for got in ((A, S2) if nR <= 2048 else (S2,)):
         assert np.array_equal(got.astype(np.float32).astype(np.float64), got)
     # The remainder passes take effect: the head-only product hi hi^T (hi =
     # [P^T] rounded to TF32 or BF16, the one pass a dropped remainder would
@@ -461,7 +464,11 @@ def test_tensor_core_gram_matches_its_definition(prec, M, N, K):
     d = np.sqrt(np.diag(Aref))
     e_gpu = (A - Aref) / np.outer(d, d)
     e_head = (hi @ hi.T - Aref) / np.outer(d, d)
-    assert np.sqrt(np.mean(e_gpu ** 2)) < 0.5 * np.sqrt(np.mean(e_head ** 2))
+    # (a TF32 head-only product's random rounding averages down over long
+    # sums, below the FP32 accumulation error, so the size comparison is made
+    # where the head's rounding dominates: BF16, or short sums)
+    if prec == G.PREC_BF16 or nR <= 2048:
+        assert np.sqrt(np.mean(e_gpu ** 2)) < 0.5 * np.sqrt(np.mean(e_head ** 2))
     assert abs(np.sum(e_gpu * e_head)) < 0.3 * np.sqrt(np.sum(e_gpu ** 2) * np.sum(e_head ** 2))
 
 
@@ -528,10 +535,11 @@ def test_reduced_precision_iteration_at_sweep_sizes(M, N, K, seed, prec):
     nx = 124 / 252, N = 200, n = 400, nR = 12862 / 25726, K = 4096; group-per-
     rollout kernels).  Every sample cost and the nominal cost within 1e-4; dR
     within 1e-4 normwise (the FP32 group model keeps positions relative to the
-    initial state); the cost after the step within
-    max(1e-4, 4 kappa(J^T J + lambda I) u_FP32): the Gram's FP32 accumulation
-    over nR rows, amplified by the conditioning, moves the step.  Prints the
-    measured deviations (pytest -s)."""
+    initial state); the cost after the step within 1e-4 as well (the Gram sums
+    P^T P over at most 2048 columns per FP32 accumulator and adds the chunks
+    in FP64: with one accumulator over nR = 12862 rows its rounding moved
+    this step's cost by 2.4e-4 at M = 32).  Prints the measured deviations
+    and, for reference, 4 kappa(J^T J + lambda I) u_FP32 (pytest -s)."""
     m, x0, tgt, it = _sweep_oracle(M, N, K, seed)
     gp = G.chain_problem(M=M, N=N, K=K, iterations=1, lam=1e-3, sigma0=0.2, seed=seed, precision=prec)
     s = G.Solver(gp, 1)
@@ -551,7 +559,7 @@ def test_reduced_precision_iteration_at_sweep_sizes(M, N, K, seed, prec):
           f"{np.max(np.abs(Cs - it.C_samp) / np.abs(it.C_samp)):.2e}, C_new {e_new:.2e}, "
           f"kappa(J^T J + lambda I) {kap:.3e}, bound {max(TOLRED, 4 * kap * U32):.2e}")
     assert rep[0].C_new < rep[0].C_nom and it.C_new < it.C_nom
-    assert e_new <= max(TOLRED, 4.0 * kap * U32)
+    assert e_new <= TOLRED
 
 
 def test_reduced_precision_indefinite_lsq_system_takes_the_diagonal_shift():
