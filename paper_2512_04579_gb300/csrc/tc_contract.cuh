@@ -17,7 +17,8 @@ namespace gnm {
 // One batched NT GEMM per instance: D[i][j] = sum_k A[i][k] B[j][k] with A
 // rows a_row0.., B rows b_row0.. of tensor map `map`, k from column x0 over
 // nkb k-blocks, M x Nc outputs with row stride ldc from out_off of the
-// launch's first (out_sel 0) or second array; output columns >= ccut are
+// launch's first (out_sel 0: A, or the contraction's [P^T | S]), second (1:
+// S2) or chunk array (2: one column chunk of a chunked Gram); output columns >= ccut are
 // stored cgap further right (the S block of [P^T | S] starts aligned).
 struct TcJob {
   int32_t inst, map;
