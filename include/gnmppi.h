@@ -73,7 +73,9 @@ enum {
   GNMPPI_PREC_FP32 = 1, /* FP32 rollouts with compensated cost sums; contraction and Gram
                            on the tensor cores from three TF32 passes over FP32 operands
                            split into head and remainder (FP32-level accuracy, FP32
-                           accumulation); FP64 Cholesky with iterative refinement.  An
+                           accumulation; the Gram's sum over the residual rows in chunks
+                           of 2048, added in FP64); FP64 Cholesky with iterative
+                           refinement.  An
                            LSQ system that does not factor is retried with 1e-5, 1e-4,
                            1e-3 of diag(P^T P) added before lambda grows (the Gram's
                            rounding can leave it indefinite when K' is close to n)       */
