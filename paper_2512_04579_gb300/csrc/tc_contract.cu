@@ -351,6 +351,33 @@ __device__ __forceinline__ void split_block(unsigned char* p, int delta, int n4,
   }
 }
 
+// One warp's store of a staged 32 x 32 block (stg[r * 33 + c], row r of the
+// block in TMEM lane row0 + r, column col_org + 32 c0 + c) into out with row
+// stride ldc: the rows, and with mirror also the transposed block.
+template <typename T>
+__device__ __forceinline__ void store_block(T* out, const T* stg, const TcJob& J, int lane, int row0, int cbase,
+                                            bool mirror) {
+  const int col = cbase + lane;
+  if (col < J.Nc) {
+    const int colw = col < J.ccut ? col : col + J.cgap;
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr)
+      if (row0 + rr < J.M && GNM_IN((int64_t)(row0 + rr) * J.ldc + colw, (int64_t)J.M * J.ldc))
+        out[(int64_t)(row0 + rr) * J.ldc + colw] = stg[rr * 33 + lane];
+  }
+  if (mirror) {
+    const int rowt = row0 + lane;
+    if (rowt < J.M) {
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        const int colt = cbase + rr;
+        if (colt < J.Nc && GNM_IN((int64_t)colt * J.ldc + rowt, (int64_t)J.M * J.ldc))
+          out[(int64_t)colt * J.ldc + rowt] = stg[lane * 33 + rr];
+      }
+    }
+  }
+}
+
 // Gram tile of one job: output rows tl.y.., columns tl.z.. (the B rows),
 // tl.w = sub-tiles (1 or 2) | 4 if the tile sits on the diagonal.  Per stage
 // (one 32-column k-block): B head and remainder (256 rows), and for an
@@ -377,7 +404,7 @@ template <bool CONTRACT, bool BF = false>
 __global__ void __launch_bounds__(kGramThreads, BF ? 2 : 1) k_gram_tc(const CUtensorMap* __restrict__ maps, const TcJob* __restrict__ jobs,
                                                     const InstState* __restrict__ st, const int4* __restrict__ tiles,
                                                     void* __restrict__ out0, double* __restrict__ S2,
-                                                    double* __restrict__ part,
+                                                    float* __restrict__ part,
                                                     int* __restrict__ err, int inject) {
   using TO = typename std::conditional<CONTRACT, float, double>::type;
   static_assert(!(CONTRACT && BF), "the BF16 contraction is k_contract_tc");
@@ -543,8 +570,11 @@ __global__ void __launch_bounds__(kGramThreads, BF ? 2 : 1) k_gram_tc(const CUte
   } else if (__all_sync(0xffffffffu, ok && !*abort)) {
     TO* stg = reinterpret_cast<TO*>(base) + warp * 32 * 33;
     TO* out = (CONTRACT ? reinterpret_cast<TO*>(out0)
-                        : reinterpret_cast<TO*>(J.out_sel == 2 ? part
-                                                : J.out_sel ? S2 : reinterpret_cast<double*>(out0))) + J.out_off;
+                        : reinterpret_cast<TO*>(J.out_sel ? S2 : reinterpret_cast<double*>(out0))) + J.out_off;
+    // a chunk of a chunked Gram keeps its FP32 accumulators as they are
+    const bool fpart = !CONTRACT && J.out_sel == 2;
+    float* stgf = reinterpret_cast<float*>(base) + warp * 32 * 33;
+    float* outf = fpart ? part + J.out_off : nullptr;
 #pragma unroll 1
     for (int sub = 0; sub < mt; ++sub) {
       const int row0 = row_org + (q0 + sub) * BM + warp * 32;
@@ -553,32 +583,22 @@ __global__ void __launch_bounds__(kGramThreads, BF ? 2 : 1) k_gram_tc(const CUte
       for (int c = 0; c * 32 < cend; ++c) {  // uniform over the warp
         uint32_t v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sub * TMEM_COLS + c * 32), v);
+        // strictly lower block of the symmetric Gram: its transpose is stored
+        // too (the contraction's output is rectangular and has no mirror image)
+        const bool mirror = !CONTRACT && (!diag || c < 4 * (q0 + sub));
+        if (fpart) {
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          if constexpr (CONTRACT) stg[lane * 33 + q] = __uint_as_float(v[q]);
-          else stg[lane * 33 + q] = widen_f32(v[q]);
-        }
-        __syncwarp();
-        const int col = col_org + c * 32 + lane;
-        if (col < J.Nc) {
-          const int colw = col < J.ccut ? col : col + J.cgap;
-#pragma unroll 4
-          for (int rr = 0; rr < 32; ++rr)
-            if (row0 + rr < J.M && GNM_IN((int64_t)(row0 + rr) * J.ldc + colw, (int64_t)J.M * J.ldc))
-              out[(int64_t)(row0 + rr) * J.ldc + colw] = stg[rr * 33 + lane];
-        }
-        // strictly lower block of the symmetric Gram: store its transpose too
-        // (the contraction's output is rectangular and has no mirror image)
-        if (!CONTRACT && (!diag || c < 4 * (q0 + sub))) {
-          const int rowt = row0 + lane;
-          if (rowt < J.M) {
-#pragma unroll 4
-            for (int rr = 0; rr < 32; ++rr) {
-              const int colt = col_org + c * 32 + rr;
-              if (colt < J.Nc && GNM_IN((int64_t)colt * J.ldc + rowt, (int64_t)J.M * J.ldc))
-                out[(int64_t)colt * J.ldc + rowt] = stg[lane * 33 + rr];
-            }
+          for (int q = 0; q < 32; ++q) stgf[lane * 33 + q] = __uint_as_float(v[q]);
+          __syncwarp();
+          store_block(outf, stgf, J, lane, row0, col_org + c * 32, mirror);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            if constexpr (CONTRACT) stg[lane * 33 + q] = __uint_as_float(v[q]);
+            else stg[lane * 33 + q] = widen_f32(v[q]);
           }
+          __syncwarp();
+          store_block(out, stg, J, lane, row0, col_org + c * 32, mirror);
         }
         __syncwarp();
       }
@@ -596,20 +616,29 @@ __global__ void __launch_bounds__(kGramThreads, BF ? 2 : 1) k_gram_tc(const CUte
 
 }  // namespace
 
-// A of the instances whose Gram runs in column chunks: the sum, in FP64 and
-// in chunk order, of the chunks' FP64-widened FP32 tile results (the
-// reduction over nR split so that no FP32 accumulator sums more than
-// kGramChunkCols columns).  Instances whose status is not OK are skipped
-// (their chunk tiles did not run).
+// A of the instances whose Gram runs in column chunks: the sum, in chunk
+// order, of the chunks' FP32 tile results (the reduction over nR split so
+// that no FP32 accumulator sums more than kGramChunkCols columns).  The sum
+// runs in FP32 with Knuth's TwoSum collecting every addition's rounding
+// error in a second word, and hi + lo, both widened exactly, is added once
+// in FP64: the result is the chunks' sum to well below an FP32 ulp, with one
+// FP64 instruction per entry (GB300's FP64 pipe is slow).  Instances whose
+// status is not OK are skipped (their chunk tiles did not run).
 __global__ void __launch_bounds__(256) k_gram_reduce(const GramRed* __restrict__ red, const InstState* __restrict__ st,
-                                                     const double* __restrict__ part, double* __restrict__ A) {
+                                                     const float* __restrict__ part, double* __restrict__ A) {
   const GramRed r = red[blockIdx.y];
   if (st[r.inst].status != 0) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < r.nn; i += (int64_t)gridDim.x * blockDim.x) {
-    const double* p = part + r.part_off + i;
-    double acc = p[0];
-    for (int c = 1; c < r.chunks; ++c) acc += p[(int64_t)c * r.nn];
-    A[r.out_off + i] = acc;
+    const float* p = part + r.part_off + i;
+    float hi = p[0], lo = 0.f;
+    for (int c = 1; c < r.chunks; ++c) {
+      const float x = p[(int64_t)c * r.nn];
+      const float t = __fadd_rn(hi, x);
+      const float z = __fsub_rn(t, hi);
+      lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(x, z)));
+      hi = t;
+    }
+    A[r.out_off + i] = widen_f32(__float_as_uint(hi)) + widen_f32(__float_as_uint(lo));
   }
 }
 
@@ -804,7 +833,7 @@ gnmppi_status tc_plan_create(const std::vector<InstDesc>& desc, void* dRW, const
       !plan_alloc(plan, &plan->d_tiles_c, sizeof(int4) * std::max<size_t>(1, tc.size())) ||
       !plan_alloc(plan, &plan->d_tiles_c1, sizeof(int4) * std::max<size_t>(1, tc1.size())) ||
       !plan_alloc(plan, &plan->d_tiles_g, sizeof(int4) * std::max<size_t>(1, tg.size())) ||
-      (part_elems > 0 && !plan_alloc(plan, &plan->d_part, sizeof(double) * (size_t)part_elems)) ||
+      (part_elems > 0 && !plan_alloc(plan, &plan->d_part, sizeof(float) * (size_t)part_elems)) ||
       (!red.empty() && !plan_alloc(plan, &plan->d_red, sizeof(GramRed) * red.size())) ||
       !plan_alloc(plan, &plan->d_err, sizeof(int))) {
     err = "cudaMalloc failed for the tensor-core plan";

@@ -39,8 +39,8 @@ struct GramRed {
 };
 
 // Columns of P^T summed by one FP32 accumulator of the Gram; longer sums are
-// split into chunks whose results are added in FP64 (the tensor core's FP32
-// accumulation error grows with the number of accumulation steps).
+// split into chunks whose FP32 results are added with a compensated sum (the
+// tensor core's FP32 accumulation error grows with the number of steps).
 constexpr int kGramChunkCols = 2048;
 
 struct TcPlan {
@@ -52,7 +52,7 @@ struct TcPlan {
   int ntiles_c = 0, ntiles_c1 = 0, ntiles_g = 0;
   int smem = 0, smem1 = 0;
   int bf16 = 1;
-  double* d_part = nullptr;       // FP64 chunk results of the chunked Grams
+  float* d_part = nullptr;        // FP32 chunk results of the chunked Grams
   GramRed* d_red = nullptr;       // one record per chunked instance
   int nred = 0;
   int* d_err = nullptr;           // set to 1 when a bounded wait ran out
@@ -78,7 +78,7 @@ cudaError_t tc_contract_launch(const TcPlan& plan, const InstState* d_st, float*
 // three passes over [P^T | S] split in shared memory (BF16 head + remainder
 // in BF16 mode, TF32 otherwise), in one launch; where nR exceeds
 // kGramChunkCols, A is formed per column chunk and a second launch adds the
-// chunks in FP64.
+// chunks (compensated, into FP64).
 cudaError_t tc_gram_launch(const TcPlan& plan, const InstState* d_st, double* A, double* S2, cudaStream_t stream);
 
 }  // namespace gnm
